@@ -1,0 +1,244 @@
+/*
+ * nk.h -- C ABI of the GB300 dense-contraction library (libnk.so).
+ *
+ * The library computes the dense contractions that nelli (arXiv 2307.16080)
+ * writes as MLIR linalg ops and lowers through tiled loop nests:
+ *
+ *   linalg.matmul           C[m,n] (+)= sum_k A[m,k] * B[k,n]
+ *                           (Sec. 1 Listing "for->affine"; Sec. 2.1.1 Listing
+ *                           "linalg-matmul": maps (d0,d2),(d2,d1)->(d0,d1),
+ *                           iterators parallel, parallel, reduction)
+ *   linalg.batch_matmul     the same with a leading batch / group index
+ *   linalg.conv_2d_nhwc_hwcf
+ *                           O[n,oh,ow,f] (+)= sum_{kh,kw,c}
+ *                              I[n, oh*sh + kh*dh - ph, ow*sw + kw*dw - pw, c]
+ *                              * W[kh,kw,c,f]
+ *                           (Sec. 4.1 Listing "2dnchwconv", output-parallel,
+ *                           no kernel flip; NHWC/HWCF with stride, dilation
+ *                           and zero padding)
+ *
+ * followed by the epilogue of the lowered torch.nn.Linear (Sec. 2.1.2 Listing
+ * "listing1": zero-fill, contraction, bias add), extended with ReLU and a
+ * dequantisation scale:   out = ReLU?(beta*C_in + alpha*acc + bias[n]).
+ *
+ * Conventions for every entry point
+ *  - The caller owns every buffer and the stream.  The library never frees or
+ *    allocates caller-visible device memory; compute calls allocate nothing.
+ *  - Device pointers are plain CUDA device addresses on the current device;
+ *    `stream` is a cudaStream_t (NULL = legacy default stream).  Compute calls
+ *    are asynchronous on that stream; host arguments are read before return.
+ *  - Arguments are validated before anything is launched.  A non-OK status
+ *    means nothing was launched; nk_last_error() gives a message.
+ *  - Strides are in elements.  Every matrix needs one unit-stride dimension
+ *    (its "major" dimension); FP32 operands and outputs may have any other
+ *    stride.  BF16 / E4M3 operands are read by TMA directly and so need a
+ *    16-byte aligned base and 16-byte multiples for the other strides
+ *    (NK_ERR_MISALIGNED otherwise).
+ *  - There is no CPU fallback: without a usable GB300 (sm_103) the calls
+ *    return NK_ERR_CUDA.
+ */
+#ifndef NK_H
+#define NK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  NK_OK = 0,
+  NK_ERR_INVALID_ARG = -1, /* null pointer, bad rank/shape/dtype combination  */
+  NK_ERR_UNSUPPORTED = -2, /* legal request this build does not implement     */
+  NK_ERR_MISALIGNED = -3,  /* pointer or stride breaks the 16-byte rule       */
+  NK_ERR_WORKSPACE = -4,   /* workspace missing or smaller than required      */
+  NK_ERR_CUDA = -5,        /* CUDA runtime/driver error (message has details) */
+  NK_ERR_TIMEOUT = -6,     /* a bounded device-side wait expired              */
+  NK_ERR_NO_SCHEDULE = -7  /* no legal schedule for this problem              */
+} nk_status;
+
+typedef enum { NK_F32 = 0, NK_BF16 = 1, NK_F8E4M3 = 2, NK_F64 = 3 } nk_dtype;
+
+/* Arithmetic of the contraction; the accumulator is FP32 in every case.
+ *  F32    : FP32 inputs, FP32 FFMA (CUDA cores).
+ *  BF16   : operands rounded to bfloat16 (RNE), tcgen05 MMA.
+ *  BF16X3 : x = hi + lo with hi = bf16(x), lo = bf16(x - hi); the MMA sums
+ *           hi*hi + hi*lo + lo*hi (lo*lo dropped) to recover FP32 accuracy.
+ *  FP8    : per-tensor scales s = 448/amax(|x|), q = e4m3_rn_sat(x*s),
+ *           tcgen05 MMA on E4M3, result multiplied by 1/(s_a*s_b).        */
+typedef enum {
+  NK_PREC_F32 = 0,
+  NK_PREC_BF16 = 1,
+  NK_PREC_BF16X3 = 2,
+  NK_PREC_FP8 = 3
+} nk_precision;
+
+/* A strided view of device memory: element (i0,..,i{r-1}) lives at
+ * ptr + sum_d i_d * stride[d] elements.  rank <= 4; unused entries ignored. */
+typedef struct {
+  void* ptr;
+  int32_t dtype; /* nk_dtype */
+  int32_t rank;
+  int64_t shape[4];
+  int64_t stride[4];
+} nk_tensor;
+
+/* out = ReLU?(beta*C_in + alpha*acc + bias[n]) with beta = accumulate ? 1 : 0.
+ * bias: FP32 device vector of length N (GEMM) / F (conv), or NULL.
+ * scale_a, scale_b: only read for FP8 inputs that are already quantised
+ * (dtype NK_F8E4M3): the quantisation scales s_a, s_b; alpha = 1/(s_a*s_b).
+ * For FP32 inputs at NK_PREC_FP8 the library computes the scales itself.  */
+typedef struct {
+  const float* bias;
+  int32_t relu;
+  int32_t accumulate;
+  float scale_a;
+  float scale_b;
+} nk_epilogue;
+
+/* Tile schedule.  tile_m x tile_n output tile per CTA (cluster 2 pairs two
+ * CTAs along M that share B tiles through TMA multicast), tile_k reduction
+ * depth per pipeline stage, stages = shared-memory ring depth, split_k =
+ * number of K slices reduced by a separate fixed-order pass.  Any field 0
+ * means "choose".                                                          */
+typedef struct {
+  int32_t tile_m, tile_n, tile_k, cluster, stages, split_k;
+} nk_schedule;
+
+/* ---------------------------------------------------------------- matmul */
+
+/* linalg.matmul: C = epilogue(A @ B).
+ * A: [M,K], B: [K,N], C: [M,N] FP32 (C is also C_in when accumulate = 1).
+ * dtype of A and B: F32 for any precision (BF16/BF16X3/FP8 convert them into
+ * the workspace first), BF16 with NK_PREC_BF16, F8E4M3 with NK_PREC_FP8
+ * (scales from `epi`).  Either dimension of A and B may be the unit-stride
+ * one; (A B)^T = B^T A^T is used when C is column-major.
+ * sched: NULL = built-in choice.  ws/ws_bytes: device scratch of at least
+ * nk_matmul_workspace_size() bytes (may be NULL/0 when that size is 0).   */
+nk_status nk_matmul(const nk_tensor* A, const nk_tensor* B, nk_tensor* C,
+                    int32_t precision, const nk_epilogue* epi,
+                    const nk_schedule* sched, void* ws, size_t ws_bytes,
+                    void* stream);
+
+/* Bytes of workspace nk_matmul needs for these operands and schedule.     */
+nk_status nk_matmul_workspace_size(const nk_tensor* A, const nk_tensor* B,
+                                   const nk_tensor* C, int32_t precision,
+                                   const nk_schedule* sched, size_t* bytes);
+
+/* ---------------------------------------------------------- grouped GEMM */
+
+/* One independent GEMM of a group: C_g = A_g @ B_g (+ C_g if accumulate).
+ * A_g: [M,K] row-major with leading dimension lda (elements), B_g: [K,N]
+ * given as its transpose Bt [N,K] row-major with ldb, C_g: [M,N] FP32
+ * row-major with ldc.  M, N, K >= 1; K a multiple of 8 and lda, ldb
+ * multiples of 8 for BF16 (16-byte rows).                                  */
+typedef struct {
+  int32_t M, N, K;
+  int32_t accumulate;
+  const void* A;
+  const void* Bt;
+  float* C;
+  int64_t lda, ldb, ldc;
+} nk_gemm_group;
+
+/* Opaque plan: group table, per-group TMA descriptors and tile table in
+ * device memory, built once on the host side and replayed by one persistent
+ * launch.  Creating a plan allocates; running it does not (graph-safe).   */
+typedef struct nk_grouped_plan nk_grouped_plan;
+
+/* Build a plan for G groups (host array `groups`, copied) at `precision`
+ * (NK_PREC_BF16 with BF16 operands, or NK_PREC_F32 with FP32 operands).    */
+nk_status nk_grouped_plan_create(int32_t G, const nk_gemm_group* groups,
+                                 int32_t precision, const nk_schedule* sched,
+                                 nk_grouped_plan** plan);
+nk_status nk_grouped_plan_run(const nk_grouped_plan* plan, void* stream);
+nk_status nk_grouped_plan_destroy(nk_grouped_plan* plan);
+
+/* linalg.batch_matmul generalised to uneven groups, as one call: builds the
+ * plan in the caller's workspace (no allocation) and launches it.
+ * ws must hold nk_grouped_workspace_size() bytes; the workspace must stay
+ * untouched until the launch has completed.                               */
+nk_status nk_batch_matmul_grouped(int32_t G, const nk_gemm_group* groups,
+                                  int32_t precision, const nk_schedule* sched,
+                                  void* ws, size_t ws_bytes, void* stream);
+nk_status nk_grouped_workspace_size(int32_t G, const nk_gemm_group* groups,
+                                    int32_t precision, const nk_schedule* sched,
+                                    size_t* bytes);
+
+/* ------------------------------------------------------------------ conv */
+
+/* linalg.conv_2d_nhwc_hwcf with zero padding and the epilogue.
+ * I: [N,H,W,C], W: [KH,KW,C,F], O: [N,OH,OW,F] FP32, all with unit stride in
+ * the last dimension.  OH = (H + pt + pb - dh*(KH-1) - 1)/sh + 1 (same for OW).
+ * stride = {sh, sw}, dilation = {dh, dw}, pad = {top, bottom, left, right}.
+ * I and W dtype: F32 (any precision; BF16 converts into the workspace) or
+ * BF16 with NK_PREC_BF16.                                                   */
+nk_status nk_conv2d_nhwc_hwcf(const nk_tensor* I, const nk_tensor* W,
+                              nk_tensor* O, const int64_t stride[2],
+                              const int64_t dilation[2], const int64_t pad[4],
+                              int32_t precision, const nk_epilogue* epi,
+                              const nk_schedule* sched, void* ws,
+                              size_t ws_bytes, void* stream);
+nk_status nk_conv2d_workspace_size(const nk_tensor* I, const nk_tensor* W,
+                                   const nk_tensor* O, const int64_t stride[2],
+                                   const int64_t dilation[2],
+                                   const int64_t pad[4], int32_t precision,
+                                   const nk_schedule* sched, size_t* bytes);
+
+/* --------------------------------------------------------- operand prep */
+
+/* amax = max |x| over n FP32 values, written as one float to `amax` (device).
+ * Needs nk_prep_workspace_size(n) bytes of scratch.                         */
+nk_status nk_amax(const float* x, int64_t n, float* amax, void* ws,
+                  size_t ws_bytes, void* stream);
+size_t nk_prep_workspace_size(int64_t n);
+
+/* Cast a [rows, cols] FP32 matrix (row stride ld_in) to BF16 (RNE), FP8 E4M3
+ * (q = e4m3_rn_sat(x * s) with s = 448/(*amax), s = 1 if amax = 0; the scale
+ * is also stored to *scale_out when non-NULL) or the BF16 hi/lo pair.
+ * transpose = 1 writes out[c, r] (row stride ld_out) so a [K,N] operand
+ * becomes the K-major [N,K] layout the tensor cores read.                  */
+nk_status nk_cast_bf16(const float* in, int64_t rows, int64_t cols, int64_t ld_in,
+                       void* out, int64_t ld_out, int32_t transpose, void* stream);
+nk_status nk_cast_fp8(const float* in, int64_t rows, int64_t cols, int64_t ld_in,
+                      const float* amax, void* out, int64_t ld_out,
+                      int32_t transpose, float* scale_out, void* stream);
+nk_status nk_split_bf16x3(const float* in, int64_t rows, int64_t cols,
+                          int64_t ld_in, void* hi, void* lo, int64_t ld_out,
+                          int32_t transpose, void* stream);
+
+/* ------------------------------------------------------------ validation */
+
+/* sumsq[0] = sum (C - R)^2, sumsq[1] = sum R^2 over an [M,N] FP32 matrix C
+ * (row stride ldc) and FP64 reference R (row stride ldr), accumulated in FP64
+ * on the device in a fixed order (run-to-run identical).  The relative
+ * Frobenius error is sqrt(sumsq[0] / sumsq[1]).  sumsq: 2 doubles (device).
+ * Needs nk_norm_workspace_size(M, N) bytes.                                  */
+nk_status nk_rel_frobenius(const float* C, int64_t ldc, const double* R,
+                           int64_t ldr, int64_t M, int64_t N, double* sumsq,
+                           void* ws, size_t ws_bytes, void* stream);
+size_t nk_norm_workspace_size(int64_t M, int64_t N);
+
+/* ---------------------------------------------------------- diagnostics */
+
+/* Thread-local message describing the last non-OK status of this thread.  */
+const char* nk_last_error(void);
+
+/* Synchronise `stream`, then report device-side failures: NK_ERR_TIMEOUT if
+ * a bounded wait inside a kernel expired since the last call (the flag is
+ * cleared), NK_ERR_CUDA for a runtime error.                                */
+nk_status nk_sync_status(void* stream);
+
+/* Test hook: the spin budget (iterations) of every bounded device wait;
+ * 0 restores the default.  Lets a test drive the timeout path on purpose. */
+nk_status nk_set_wait_budget(int64_t iterations);
+
+/* Number of SMs and the compute capability of the current device.          */
+nk_status nk_device_info(int32_t* sm_count, int32_t* cc_major, int32_t* cc_minor);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NK_H */

@@ -1,0 +1,315 @@
+// k_prep.cu -- operand preparation and the validation norm.
+//
+// Operand prep turns FP32 operands into what the tensor cores read:
+//   BF16     x -> bf16_rn(x)
+//   FP8      s = 448/amax(|x|) (1 if amax is 0 or not finite), q = e4m3_rn_sat(x*s)
+//   BF16x3   hi = bf16_rn(x), lo = bf16_rn(x - hi)
+// optionally transposing [rows, cols] -> [cols, rows] so that a [K,N] operand
+// becomes K-major.  These passes are HBM-bound: 128-bit loads, one read and
+// one write of every element, 32x32 shared-memory tiles for the transpose.
+// Rounding uses CUDA's own conversion intrinsics (RNE; satfinite for E4M3).
+//
+// The validation norm sums (C-R)^2 and R^2 in FP64 over a fixed partition
+// (fixed block count, fixed tree), so its result is identical run to run.
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <cuda_runtime.h>
+
+#include "nk_internal.cuh"
+
+namespace nk {
+namespace {
+
+constexpr int kAmaxBlocks = 1024;
+constexpr int kNormBlocks = 1024;
+
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// amax over a [rows, cols] matrix with row stride ld.  Stage 1: one partial
+// per block; stage 2: one block folds the partials.  NaN inputs make the
+// result NaN (the scale then falls back to 1).
+__global__ void amax_stage1(const float* __restrict__ x, int64_t rows, int64_t cols, int64_t ld,
+                            float* __restrict__ partial) {
+  float m = 0.f;
+  bool nan = false;
+  const bool vec = (cols % 4 == 0) && (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(x) & 15) == 0);
+  if (vec) {
+    const int64_t cq = cols / 4;
+    const int64_t total = rows * cq;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+      const int64_t r = i / cq, c = (i % cq) * 4;
+      float4 v = __ldg(reinterpret_cast<const float4*>(x + r * ld + c));
+      nan |= (v.x != v.x) | (v.y != v.y) | (v.z != v.z) | (v.w != v.w);
+      m = fmaxf(m, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+    }
+  } else {
+    const int64_t total = rows * cols;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+      float v = x[(i / cols) * ld + (i % cols)];
+      nan |= (v != v);
+      m = fmaxf(m, fabsf(v));
+    }
+  }
+  if (__any_sync(0xffffffffu, nan)) m = __int_as_float(0x7fc00000);
+  __shared__ float sm[32];
+  float w = warp_max(m);
+  bool wn = __any_sync(0xffffffffu, m != m);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x / 32] = wn ? __int_as_float(0x7fc00000) : w;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int nw = blockDim.x / 32;
+    float v = threadIdx.x < nw ? sm[threadIdx.x] : 0.f;
+    bool bn = __any_sync(0xffffffffu, v != v);
+    v = warp_max(v);
+    if (threadIdx.x == 0) partial[blockIdx.x] = bn ? __int_as_float(0x7fc00000) : v;
+  }
+}
+
+__global__ void amax_stage2(const float* __restrict__ partial, int n, float* __restrict__ out) {
+  float m = 0.f;
+  bool nan = false;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    float v = partial[i];
+    nan |= (v != v);
+    m = fmaxf(m, v);
+  }
+  __shared__ float sm[32];
+  __shared__ int sn;
+  if (threadIdx.x == 0) sn = 0;
+  __syncthreads();
+  if (nan) atomicOr(&sn, 1);
+  float w = warp_max(m);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x / 32] = w;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float v = threadIdx.x < (int)(blockDim.x / 32) ? sm[threadIdx.x] : 0.f;
+    v = warp_max(v);
+    if (threadIdx.x == 0) *out = sn ? __int_as_float(0x7fc00000) : v;
+  }
+}
+
+__device__ __forceinline__ float fp8_scale_of(const float* amax) {
+  const float a = *amax;
+  return (a > 0.f && a <= 3.402823466e38f) ? __fdiv_rn(448.f, a) : 1.f;
+}
+
+// One element of each cast kind.  kind 0: bf16, 1: e4m3, 2: bf16 hi/lo.
+template <int KIND>
+struct Caster;
+
+template <>
+struct Caster<0> {
+  using T = __nv_bfloat16;
+  __device__ static void cvt(float x, float, T& o0, T&) { o0 = __float2bfloat16_rn(x); }
+};
+template <>
+struct Caster<1> {
+  using T = __nv_fp8_storage_t;
+  __device__ static void cvt(float x, float s, T& o0, T&) {
+    o0 = __nv_cvt_float_to_fp8(__fmul_rn(x, s), __NV_SATFINITE, __NV_E4M3);
+  }
+};
+template <>
+struct Caster<2> {
+  using T = __nv_bfloat16;
+  __device__ static void cvt(float x, float, T& o0, T& o1) {
+    o0 = __float2bfloat16_rn(x);
+    o1 = __float2bfloat16_rn(__fsub_rn(x, __bfloat162float(o0)));
+  }
+};
+
+// Row-major cast without transpose: four elements per thread per step.
+template <int KIND>
+__global__ void cast_rows(const float* __restrict__ in, int64_t rows, int64_t cols, int64_t ld_in,
+                          const float* __restrict__ amax, typename Caster<KIND>::T* __restrict__ o0,
+                          typename Caster<KIND>::T* __restrict__ o1, int64_t ld_out,
+                          float* scale_out) {
+  using T = typename Caster<KIND>::T;
+  const float s = KIND == 1 ? fp8_scale_of(amax) : 1.f;
+  if (scale_out && blockIdx.x == 0 && threadIdx.x == 0) *scale_out = s;
+  const int64_t cq = (cols + 3) / 4;
+  const int64_t total = rows * cq;
+  const bool vec = (cols % 4 == 0) && (ld_in % 4 == 0) &&
+                   ((reinterpret_cast<uintptr_t>(in) & 15) == 0);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / cq, c = (i % cq) * 4;
+    float v[4];
+    if (vec) {
+      float4 q = __ldg(reinterpret_cast<const float4*>(in + r * ld_in + c));
+      v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) v[j] = (c + j < cols) ? in[r * ld_in + c + j] : 0.f;
+    }
+    T a[4], b[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) Caster<KIND>::cvt(v[j], s, a[j], b[j]);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (c + j < cols) {
+        o0[r * ld_out + c + j] = a[j];
+        if (KIND == 2) o1[r * ld_out + c + j] = b[j];
+      }
+    }
+  }
+}
+
+// Transposing cast: a 32x32 tile through shared memory, coalesced on both sides.
+template <int KIND>
+__global__ void cast_transpose(const float* __restrict__ in, int64_t rows, int64_t cols,
+                               int64_t ld_in, const float* __restrict__ amax,
+                               typename Caster<KIND>::T* __restrict__ o0,
+                               typename Caster<KIND>::T* __restrict__ o1, int64_t ld_out,
+                               float* scale_out) {
+  using T = typename Caster<KIND>::T;
+  __shared__ float tile[32][33];
+  const float s = KIND == 1 ? fp8_scale_of(amax) : 1.f;
+  if (scale_out && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0)
+    *scale_out = s;
+  const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
+  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+    const int64_t r = r0 + j, c = c0 + threadIdx.x;
+    tile[j][threadIdx.x] = (r < rows && c < cols) ? in[r * ld_in + c] : 0.f;
+  }
+  __syncthreads();
+  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+    const int64_t c = c0 + j, r = r0 + threadIdx.x;   // output row c, column r
+    if (c < cols && r < rows) {
+      T a, b;
+      Caster<KIND>::cvt(tile[threadIdx.x][j], s, a, b);
+      o0[c * ld_out + r] = a;
+      if (KIND == 2) o1[c * ld_out + r] = b;
+    }
+  }
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Fixed-order FP64 block sums: thread i of block b visits elements
+// b*blockDim + i + k*gridDim*blockDim; warp tree, then a tree over warps.
+__global__ void norm_stage1(const float* __restrict__ C, int64_t ldc, const double* __restrict__ R,
+                            int64_t ldr, int64_t M, int64_t N, double* __restrict__ partial) {
+  double e = 0.0, r2 = 0.0;
+  const int64_t total = M * N;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t m = i / N, n = i % N;
+    const double r = R[m * ldr + n];
+    const double d = (double)C[m * ldc + n] - r;
+    e = fma(d, d, e);
+    r2 = fma(r, r, r2);
+  }
+  __shared__ double se[32], sr[32];
+  e = warp_sum_d(e);
+  r2 = warp_sum_d(r2);
+  if ((threadIdx.x & 31) == 0) { se[threadIdx.x / 32] = e; sr[threadIdx.x / 32] = r2; }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int nw = blockDim.x / 32;
+    double a = threadIdx.x < nw ? se[threadIdx.x] : 0.0;
+    double b = threadIdx.x < nw ? sr[threadIdx.x] : 0.0;
+    a = warp_sum_d(a);
+    b = warp_sum_d(b);
+    if (threadIdx.x == 0) { partial[2 * blockIdx.x] = a; partial[2 * blockIdx.x + 1] = b; }
+  }
+}
+
+__global__ void norm_stage2(const double* __restrict__ partial, int n, double* __restrict__ out) {
+  double e = 0.0, r2 = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) { e += partial[2 * i]; r2 += partial[2 * i + 1]; }
+  __shared__ double se[32], sr[32];
+  e = warp_sum_d(e);
+  r2 = warp_sum_d(r2);
+  if ((threadIdx.x & 31) == 0) { se[threadIdx.x / 32] = e; sr[threadIdx.x / 32] = r2; }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int nw = blockDim.x / 32;
+    double a = threadIdx.x < nw ? se[threadIdx.x] : 0.0;
+    double b = threadIdx.x < nw ? sr[threadIdx.x] : 0.0;
+    a = warp_sum_d(a);
+    b = warp_sum_d(b);
+    if (threadIdx.x == 0) { out[0] = a; out[1] = b; }
+  }
+}
+
+template <int KIND>
+nk_status launch_cast(const float* in, int64_t rows, int64_t cols, int64_t ld_in,
+                      const float* amax, void* out0, void* out1, int64_t ld_out, int transpose,
+                      float* scale_out, cudaStream_t st, int sms) {
+  using T = typename Caster<KIND>::T;
+  T* o0 = static_cast<T*>(out0);
+  T* o1 = static_cast<T*>(out1);
+  if (transpose) {
+    dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
+    if (grid.y > 65535) return fail(NK_ERR_UNSUPPORTED, "too many rows for the transposing cast");
+    cast_transpose<KIND><<<grid, dim3(32, 8), 0, st>>>(in, rows, cols, ld_in, amax, o0, o1, ld_out,
+                                                       scale_out);
+  } else {
+    const int64_t work = rows * ((cols + 3) / 4);
+    int64_t blocks = (work + 255) / 256;
+    const int64_t cap = (int64_t)sms * 16;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    cast_rows<KIND><<<(unsigned)blocks, 256, 0, st>>>(in, rows, cols, ld_in, amax, o0, o1, ld_out,
+                                                       scale_out);
+  }
+  return check_launch("cast kernel");
+}
+
+}  // namespace
+
+size_t prep_amax_ws(int64_t) { return kAmaxBlocks * sizeof(float); }
+
+nk_status prep_amax(const float* x, int64_t rows, int64_t cols, int64_t ld, float* amax, void* ws,
+                    size_t ws_bytes, cudaStream_t st) {
+  if (!x || !amax) return fail(NK_ERR_INVALID_ARG, "amax: null pointer");
+  if (!ws || ws_bytes < prep_amax_ws(rows * cols))
+    return fail(NK_ERR_WORKSPACE, "amax needs %zu bytes of workspace", prep_amax_ws(rows * cols));
+  amax_stage1<<<kAmaxBlocks, 256, 0, st>>>(x, rows, cols, ld, static_cast<float*>(ws));
+  nk_status s = check_launch("amax_stage1");
+  if (s != NK_OK) return s;
+  amax_stage2<<<1, 1024, 0, st>>>(static_cast<float*>(ws), kAmaxBlocks, amax);
+  return check_launch("amax_stage2");
+}
+
+nk_status prep_cast(int kind, const float* in, int64_t rows, int64_t cols, int64_t ld_in,
+                    const float* amax, void* out0, void* out1, int64_t ld_out, int transpose,
+                    float* scale_out, cudaStream_t st) {
+  int sms = 0;
+  nk_status s = require_device(&sms);
+  if (s != NK_OK) return s;
+  if (rows <= 0 || cols <= 0) return NK_OK;
+  switch (kind) {
+    case 0: return launch_cast<0>(in, rows, cols, ld_in, amax, out0, out1, ld_out, transpose, scale_out, st, sms);
+    case 1: return launch_cast<1>(in, rows, cols, ld_in, amax, out0, out1, ld_out, transpose, scale_out, st, sms);
+    case 2: return launch_cast<2>(in, rows, cols, ld_in, amax, out0, out1, ld_out, transpose, scale_out, st, sms);
+    default: return fail(NK_ERR_INVALID_ARG, "unknown cast kind %d", kind);
+  }
+}
+
+size_t norm_ws(int64_t, int64_t) { return 2 * kNormBlocks * sizeof(double); }
+
+nk_status norm_sumsq(const float* C, int64_t ldc, const double* R, int64_t ldr, int64_t M,
+                     int64_t N, double* out, void* ws, size_t ws_bytes, cudaStream_t st) {
+  if (!ws || ws_bytes < norm_ws(M, N))
+    return fail(NK_ERR_WORKSPACE, "norm needs %zu bytes of workspace", norm_ws(M, N));
+  double* part = static_cast<double*>(ws);
+  norm_stage1<<<kNormBlocks, 256, 0, st>>>(C, ldc, R, ldr, M, N, part);
+  nk_status s = check_launch("norm_stage1");
+  if (s != NK_OK) return s;
+  norm_stage2<<<1, 1024, 0, st>>>(part, kNormBlocks, out);
+  return check_launch("norm_stage2");
+}
+
+}  // namespace nk

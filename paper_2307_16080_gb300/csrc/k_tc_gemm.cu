@@ -1,0 +1,521 @@
+// k_tc_gemm.cu -- linalg.matmul on the 5th-generation tensor cores.
+//
+// C[m,n] (+)= sum_k A[m,k] B[k,n] (Sec. 2.1.1 Listing "linalg-matmul") with
+// the bias / ReLU epilogue of the lowered Linear layer (Sec. 2.1.2 Listing
+// "listing1").  The paper tiles the loop nest and searches tile sizes
+// (Sec. 4.3); here one tile is a 128 x BN block of C computed by one CTA of a
+// persistent grid:
+//
+//   warp 0      TMA producer: A and B tiles (128-byte rows, 128B swizzle) into
+//               a STAGES-deep shared-memory ring, one mbarrier pair per slot.
+//               With cluster 2 the two CTAs of a pair share B: each loads
+//               half of the B tile and multicasts it to both.
+//   warp 1      allocates TMEM; one thread issues tcgen05.mma (M=128, N=BN,
+//               K=16 BF16 / K=32 E4M3 per instruction) into a double-buffered
+//               FP32 accumulator in TMEM, and tcgen05.commit frees each slot.
+//   warps 2..5  epilogue: tcgen05.ld of their 32-lane quarter, then
+//               alpha, beta*C, bias, ReLU and stores -- overlapping the
+//               next tile's main loop through the second accumulator.
+//
+// BF16x3 issues three MMAs per K step (hi*hi, hi*lo, lo*hi) into the same
+// accumulator.  Split-K writes each slice's raw tile to the workspace and the
+// fixed-order warp-shuffle reduce applies the epilogue.
+//
+// Every wait is bounded (see tc_ptx.cuh); on a timeout the CTA drains its own
+// copies and MMAs, frees TMEM and exits, and the host reports NK_ERR_TIMEOUT.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <cstring>
+#include <mutex>
+
+#include "nk_internal.cuh"
+#include "tc_ptx.cuh"
+
+namespace nk {
+
+__device__ unsigned int g_tc_err;
+
+uint32_t tc_read_and_clear_errors() {
+  unsigned int v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_tc_err, sizeof v) != cudaSuccess) return 0;
+  const unsigned int z = 0;
+  cudaMemcpyToSymbol(g_tc_err, &z, sizeof z);
+  return v;
+}
+
+namespace {
+
+constexpr int kThreads = 192;       // 6 warps
+constexpr int kBM = 128;
+constexpr int kRowBytes = 128;      // one K block = one 128-byte swizzle row
+constexpr int kGroupM = 8;          // rasterisation: 8 (pair-)rows of tiles per band
+constexpr int kMaxSmem = 232448;    // 227 KB opt-in limit
+
+struct TcParams {
+  CUtensorMap tmA, tmB, tmA2, tmB2;
+  int M, N, K;
+  int bn, stages;
+  int tiles_m, tiles_n;   // tiles_m padded to the cluster size
+  int splits, kb_per_split, nkb;
+  int units;
+  float* C;
+  int64_t ldc;
+  float* partial;         // [splits][M][N] when splits > 1
+  const float* bias;
+  int bias_on_m, relu;
+  float beta, alpha;
+  const float* scale_a;
+  const float* scale_b;
+  int64_t budget;
+  int c_vec;
+};
+
+__host__ __device__ inline int stage_bytes(int kind, int bn) {
+  const int ab = kBM * kRowBytes + bn * kRowBytes;
+  return kind == TC_BF16X3 ? 2 * ab : ab;
+}
+
+struct Unit {
+  int tm, tn, split;
+};
+
+__device__ __forceinline__ Unit decode_unit(const TcParams& p, int u, int cl, int rank) {
+  const int tmp_count = p.tiles_m / cl;
+  const int per_split = tmp_count * p.tiles_n;
+  Unit r;
+  r.split = u / per_split;
+  const int t = u % per_split;
+  const int band = kGroupM * p.tiles_n;
+  const int first = (t / band) * kGroupM;
+  const int gm = min(tmp_count - first, kGroupM);
+  const int tmp = first + (t % band) % gm;
+  r.tn = (t % band) / gm;
+  r.tm = tmp * cl + rank;
+  return r;
+}
+
+template <int KIND, int CL>
+__global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_constant__ TcParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = ptx::smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023) & ~1023u;
+  uint8_t* base_ptr = smem_raw + (base - raw);
+
+  const int sb = stage_bytes(KIND, p.bn);
+  const int S = p.stages;
+  const uint32_t bar0 = base + S * sb;   // full[S], empty[S], tfull[2], tempty[2], drain
+  auto full_bar = [&](int s) { return bar0 + 8u * s; };
+  auto empty_bar = [&](int s) { return bar0 + 8u * (S + s); };
+  auto tfull_bar = [&](int b) { return bar0 + 8u * (2 * S + b); };
+  auto tempty_bar = [&](int b) { return bar0 + 8u * (2 * S + 2 + b); };
+  const uint32_t drain_bar = bar0 + 8u * (2 * S + 4);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(base_ptr + S * sb + 8 * (2 * S + 5));
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x / 32;
+  const int lane = threadIdx.x % 32;
+  const int rank = CL == 2 ? (int)ptx::cluster_ctarank() : 0;
+  const int cluster_id = blockIdx.x / CL;
+  const int n_clusters = gridDim.x / CL;
+  const uint32_t tmem_cols = 2u * (uint32_t)p.bn < 32u ? 32u : 2u * (uint32_t)p.bn;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      ptx::mbar_init(full_bar(s), 1);
+      ptx::mbar_init(empty_bar(s), CL);
+    }
+    for (int b = 0; b < 2; ++b) {
+      ptx::mbar_init(tfull_bar(b), 1);
+      ptx::mbar_init(tempty_bar(b), 4);
+    }
+    ptx::mbar_init(drain_bar, 1);
+    *abort_flag = 0;
+    ptx::fence_mbar_init();
+  }
+  if (warp == 0 && lane == 0) {
+    ptx::tma_prefetch_desc(&p.tmA);
+    ptx::tma_prefetch_desc(&p.tmB);
+    if (KIND == TC_BF16X3) {
+      ptx::tma_prefetch_desc(&p.tmA2);
+      ptx::tma_prefetch_desc(&p.tmB2);
+    }
+  }
+  if (warp == 1) {
+    ptx::tmem_alloc(ptx::smem_u32(tmem_slot), tmem_cols);
+    ptx::tmem_relinquish();
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  if (CL == 2) ptx::cluster_sync();
+  const uint32_t tmem_base = *tmem_slot;
+
+  const int a_bytes = kBM * kRowBytes;
+  const int b_bytes = p.bn * kRowBytes;
+  // Stage layout: [A][B] or, for BF16x3, [A_hi][B_hi][A_lo][B_lo].
+  auto a_smem = [&](int s, int part) { return base + s * sb + part * (a_bytes + b_bytes); };
+  auto b_smem = [&](int s, int part) { return base + s * sb + part * (a_bytes + b_bytes) + a_bytes; };
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      int it = 0;
+      const int kblk = KIND == TC_FP8 ? 128 : 64;   // elements per 128-byte row
+      const int b_rows = p.bn / CL;
+      bool ok = true;
+      for (int u = cluster_id; u < p.units && ok; u += n_clusters) {
+        const Unit t = decode_unit(p, u, CL, rank);
+        const int kb0 = t.split * p.kb_per_split;
+        const int kb1 = min(p.nkb, kb0 + p.kb_per_split);
+        for (int kb = kb0; kb < kb1; ++kb, ++it) {
+          const int s = it % S;
+          const uint32_t ph = (uint32_t)(it / S) & 1u;
+          if (!ptx::mbar_wait(empty_bar(s), ph ^ 1u, p.budget, abort_flag, &g_tc_err)) { ok = false; break; }
+          ptx::mbar_arrive_expect_tx(full_bar(s), (uint32_t)sb);
+          const int kx = kb * kblk;
+          const int ay = t.tm * kBM;
+          const int by = t.tn * p.bn + rank * b_rows;
+          const int nparts = KIND == TC_BF16X3 ? 2 : 1;
+          for (int part = 0; part < nparts; ++part) {
+            const CUtensorMap* ma = part ? &p.tmA2 : &p.tmA;
+            const CUtensorMap* mb = part ? &p.tmB2 : &p.tmB;
+            ptx::tma_load_2d(a_smem(s, part), ma, full_bar(s), kx, ay);
+            if (CL == 2)
+              ptx::tma_load_2d_mc(b_smem(s, part) + rank * b_rows * kRowBytes, mb, full_bar(s), kx, by,
+                                  (uint16_t)0x3);
+            else
+              ptx::tma_load_2d(b_smem(s, part), mb, full_bar(s), kx, by);
+          }
+        }
+      }
+      // Drain: the last copy issued into each slot must land before exit.
+      const int last = it;
+      for (int j = last - 1; j >= 0 && j >= last - S; --j)
+        ptx::mbar_drain(full_bar(j % S), (uint32_t)(j / S) & 1u, 100000000ull);
+    }
+  } else if (warp == 1) {
+    // -------------------------------------------------------------- MMA
+    if (lane == 0) {
+      const uint32_t idesc = ptx::make_idesc(KIND == TC_FP8 ? 0 : 1, kBM, p.bn);
+      int it = 0, tc = 0;
+      bool ok = true;
+      for (int u = cluster_id; u < p.units && ok; u += n_clusters, ++tc) {
+        const Unit t = decode_unit(p, u, CL, rank);
+        const int kb0 = t.split * p.kb_per_split;
+        const int kb1 = min(p.nkb, kb0 + p.kb_per_split);
+        const int acc = tc & 1;
+        const uint32_t aph = (uint32_t)(tc >> 1) & 1u;
+        if (!ptx::mbar_wait(tempty_bar(acc), aph ^ 1u, p.budget, abort_flag, &g_tc_err)) break;
+        ptx::tc_fence_after();
+        const uint32_t d = tmem_base + (uint32_t)(acc * p.bn);
+        for (int kb = kb0; kb < kb1; ++kb, ++it) {
+          const int s = it % S;
+          const uint32_t ph = (uint32_t)(it / S) & 1u;
+          if (!ptx::mbar_wait(full_bar(s), ph, p.budget, abort_flag, &g_tc_err)) { ok = false; break; }
+          ptx::tc_fence_after();
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const uint32_t koff = (uint32_t)k * 32u;
+            const uint64_t ad = ptx::sw128_desc(a_smem(s, 0) + koff);
+            const uint64_t bd = ptx::sw128_desc(b_smem(s, 0) + koff);
+            const uint32_t accum = (kb > kb0 || k > 0) ? 1u : 0u;
+            ptx::tc_mma<KIND == TC_FP8>(d, ad, bd, idesc, accum);
+            if (KIND == TC_BF16X3) {
+              const uint64_t ad2 = ptx::sw128_desc(a_smem(s, 1) + koff);
+              const uint64_t bd2 = ptx::sw128_desc(b_smem(s, 1) + koff);
+              ptx::tc_mma<0>(d, ad, bd2, idesc, 1u);    // hi * lo
+              ptx::tc_mma<0>(d, ad2, bd, idesc, 1u);    // lo * hi
+            }
+          }
+          if (CL == 2) ptx::tc_commit_mc(empty_bar(s), (uint16_t)0x3);
+          else ptx::tc_commit(empty_bar(s));
+        }
+        if (!ok) break;
+        ptx::tc_commit(tfull_bar(acc));
+      }
+      // Drain: every MMA this thread issued completes before TMEM is freed.
+      ptx::tc_commit(drain_bar);
+      ptx::mbar_drain(drain_bar, 0, 100000000ull);
+    }
+  } else {
+    // ---------------------------------------------------------- epilogue
+    const int q = warp & 3;   // TMEM lane quarter this warp may read
+    float alpha = p.alpha;
+    if (p.scale_a) alpha = __frcp_rn(__fmul_rn(*p.scale_a, *p.scale_b));
+    int tc = 0;
+    for (int u = cluster_id; u < p.units; u += n_clusters, ++tc) {
+      const Unit t = decode_unit(p, u, CL, rank);
+      const int acc = tc & 1;
+      const uint32_t aph = (uint32_t)(tc >> 1) & 1u;
+      if (!ptx::mbar_wait(tfull_bar(acc), aph, p.budget, abort_flag, &g_tc_err)) break;
+      ptx::tc_fence_after();
+      const int row = t.tm * kBM + q * 32 + lane;
+      const bool row_ok = row < p.M;
+      for (int c0 = 0; c0 < p.bn; c0 += 32) {
+        float v[32];
+        ptx::tmem_ld32(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * p.bn + c0), v);
+        const int col0 = t.tn * p.bn + c0;
+        if (!row_ok || col0 >= p.N) continue;
+        if (p.partial) {
+          float* dst = p.partial + ((int64_t)t.split * p.M + row) * p.N + col0;
+          if (p.c_vec && col0 + 32 <= p.N) {
+#pragma unroll
+            for (int j = 0; j < 32; j += 4)
+              *reinterpret_cast<float4*>(dst + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+          } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (col0 + j < p.N) dst[j] = v[j];
+          }
+          continue;
+        }
+        float* dst = p.C + (int64_t)row * p.ldc + col0;
+        const float bm = (p.bias && p.bias_on_m) ? __ldg(p.bias + row) : 0.f;
+        if (p.c_vec && col0 + 32 <= p.N) {
+#pragma unroll
+          for (int j = 0; j < 32; j += 4) {
+            float o[4];
+            float4 cin = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (p.beta != 0.f) cin = *reinterpret_cast<const float4*>(dst + j);
+            const float ci[4] = {cin.x, cin.y, cin.z, cin.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              float x = alpha * v[j + e];
+              if (p.beta != 0.f) x = fmaf(p.beta, ci[e], x);
+              if (p.bias) x += p.bias_on_m ? bm : __ldg(p.bias + col0 + j + e);
+              if (p.relu) x = (x > 0.f || x != x) ? x : 0.f;
+              o[e] = x;
+            }
+            *reinterpret_cast<float4*>(dst + j) = make_float4(o[0], o[1], o[2], o[3]);
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            if (col0 + j >= p.N) continue;
+            float x = alpha * v[j];
+            if (p.beta != 0.f) x = fmaf(p.beta, dst[j], x);
+            if (p.bias) x += p.bias_on_m ? bm : __ldg(p.bias + col0 + j);
+            if (p.relu) x = (x > 0.f || x != x) ? x : 0.f;
+            dst[j] = x;
+          }
+        }
+      }
+      ptx::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) ptx::mbar_arrive(tempty_bar(acc));
+    }
+  }
+
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  if (warp == 1) ptx::tmem_dealloc(tmem_base, tmem_cols);
+  if (CL == 2) ptx::cluster_sync();
+}
+
+// ------------------------------------------------------------------ host
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// 2-D K-major operand [rows, K] with row stride ld (elements), 128B swizzle.
+nk_status make_kmajor_map(CUtensorMap* m, bool fp8, const void* ptr, int64_t rows, int64_t K,
+                          int64_t ld, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return fail(NK_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+  const int esz = fp8 ? 1 : 2;
+  cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * esz)};
+  cuuint32_t box[2] = {(cuuint32_t)(kRowBytes / esz), (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = fn(m, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                  const_cast<void*>(ptr), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS)
+    return fail(NK_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d) for a [%lld, %lld] operand", (int)r,
+                (long long)rows, (long long)K);
+  return NK_OK;
+}
+
+int smem_bytes(int kind, int bn, int stages) {
+  return 1024 + stages * stage_bytes(kind, bn) + 8 * (2 * stages + 5) + 16;
+}
+
+template <int KIND, int CL>
+nk_status launch(const TcParams& p, int grid, int smem, cudaStream_t st) {
+  auto kern = tc_gemm_kernel<KIND, CL>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(tc_gemm_kernel)");
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = CL > 1 ? 1 : 0;
+  e = cudaLaunchKernelEx(&cfg, kern, p);
+  if (e != cudaSuccess) return cuda_fail(e, "launch tc_gemm_kernel");
+  return check_launch("tc_gemm_kernel");
+}
+
+// CTAs that fit on one SM: shared memory and the 512 TMEM columns.
+int ctas_per_sm(int kind, int bn, int stages) {
+  const int sm = smem_bytes(kind, bn, stages);
+  int by_smem = kMaxSmem / sm;
+  int cols = 2 * bn < 32 ? 32 : 2 * bn;
+  int by_tmem = 512 / cols;
+  int r = by_smem < by_tmem ? by_smem : by_tmem;
+  return r < 1 ? 1 : (r > 2 ? 2 : r);
+}
+
+}  // namespace
+
+bool tc_schedule_valid(int kind, const nk_schedule& s, int M, int N, int K) {
+  (void)M; (void)N; (void)K;
+  if (s.tile_m != 128) return false;
+  if (s.tile_n != 64 && s.tile_n != 128 && s.tile_n != 256) return false;
+  if (s.tile_k != (kind == TC_FP8 ? 128 : 64)) return false;
+  if (s.cluster != 1 && s.cluster != 2) return false;
+  if (s.split_k < 1 || s.split_k > 32) return false;
+  if (s.stages < 2 || s.stages > 8) return false;
+  if (smem_bytes(kind, s.tile_n, s.stages) > kMaxSmem) return false;
+  return true;
+}
+
+nk_schedule tc_default_schedule(int kind, int M, int N, int K, int sms) {
+  nk_schedule s{};
+  s.tile_m = 128;
+  s.tile_k = kind == TC_FP8 ? 128 : 64;
+  s.tile_n = kind == TC_BF16X3 ? 128 : 256;
+  if (N <= 64) s.tile_n = 64;
+  else if (N <= 128) s.tile_n = 128;
+  s.cluster = 1;
+  s.stages = 2;
+  while (s.stages < 8 && smem_bytes(kind, s.tile_n, s.stages + 1) <= kMaxSmem) ++s.stages;
+  // Split K when the output tiles cannot fill the GPU and K is deep.
+  const int tiles = ((M + 127) / 128) * ((N + s.tile_n - 1) / s.tile_n);
+  const int nkb = (K + s.tile_k - 1) / s.tile_k;
+  s.split_k = 1;
+  while (tiles * s.split_k * 2 <= sms && nkb / (s.split_k * 2) >= 4 && s.split_k < 16) s.split_k *= 2;
+  return s;
+}
+
+size_t tc_gemm_ws(const TcGemm& g, const nk_schedule& s) {
+  if (s.split_k <= 1) return 0;
+  return (size_t)s.split_k * g.M * g.N * sizeof(float);
+}
+
+nk_status tc_gemm(const TcGemm& g, const nk_schedule& s, void* ws, size_t ws_bytes, cudaStream_t st) {
+  int sms = 0;
+  nk_status status = require_device(&sms);
+  if (status != NK_OK) return status;
+  if (g.M <= 0 || g.N <= 0) return NK_OK;
+  if (!tc_schedule_valid(g.kind, s, g.M, g.N, g.K))
+    return fail(NK_ERR_NO_SCHEDULE, "illegal tensor-core schedule");
+  if (g.K <= 0) {
+    // Empty reduction: the epilogue alone (the CUDA-core kernel with K = 0).
+    SimtGemm z{};
+    z.A = nullptr; z.sam = 0; z.sak = 1;
+    z.B = nullptr; z.sbk = 1; z.sbn = 0;
+    z.C = g.C; z.scm = g.ldc; z.scn = 1;
+    z.bias = g.bias; z.bias_on_m = g.bias_on_m;
+    z.M = g.M; z.N = g.N; z.K = 0;
+    z.alpha = 1.f; z.beta = g.beta; z.relu = g.relu;
+    return simt_gemm(z, 64, 1, nullptr, 0, st);
+  }
+  const bool fp8 = g.kind == TC_FP8;
+  const int esz = fp8 ? 1 : 2;
+  if ((g.lda * esz) % 16 || (g.ldb * esz) % 16)
+    return fail(NK_ERR_MISALIGNED, "operand row strides must be multiples of 16 bytes");
+  TcParams p;
+  memset(&p, 0, sizeof p);
+  const int CL = s.cluster;
+  if ((status = make_kmajor_map(&p.tmA, fp8, g.A, g.M, g.K, g.lda, kBM)) != NK_OK) return status;
+  if ((status = make_kmajor_map(&p.tmB, fp8, g.B, g.N, g.K, g.ldb, s.tile_n / CL)) != NK_OK) return status;
+  if (g.kind == TC_BF16X3) {
+    if ((status = make_kmajor_map(&p.tmA2, fp8, g.A2, g.M, g.K, g.lda, kBM)) != NK_OK) return status;
+    if ((status = make_kmajor_map(&p.tmB2, fp8, g.B2, g.N, g.K, g.ldb, s.tile_n / CL)) != NK_OK) return status;
+  }
+  p.M = g.M; p.N = g.N; p.K = g.K;
+  p.bn = s.tile_n;
+  p.stages = s.stages;
+  const int tm = (g.M + kBM - 1) / kBM;
+  p.tiles_m = (tm + CL - 1) / CL * CL;
+  p.tiles_n = (g.N + s.tile_n - 1) / s.tile_n;
+  p.nkb = (g.K + s.tile_k - 1) / s.tile_k;
+  int splits = s.split_k > p.nkb ? p.nkb : s.split_k;
+  p.kb_per_split = (p.nkb + splits - 1) / splits;
+  splits = (p.nkb + p.kb_per_split - 1) / p.kb_per_split;
+  p.splits = splits;
+  p.units = (p.tiles_m / CL) * p.tiles_n * splits;
+  p.C = g.C;
+  p.ldc = g.ldc;
+  p.partial = nullptr;
+  if (splits > 1) {
+    const size_t need = (size_t)splits * g.M * g.N * sizeof(float);
+    if (!ws || ws_bytes < need) return fail(NK_ERR_WORKSPACE, "split-K needs %zu bytes of workspace", need);
+    p.partial = static_cast<float*>(ws);
+  }
+  p.bias = g.bias;
+  p.bias_on_m = g.bias_on_m;
+  p.relu = g.relu;
+  p.beta = g.beta;
+  p.alpha = g.alpha;
+  p.scale_a = g.scale_a;
+  p.scale_b = g.scale_b;
+  p.budget = wait_budget();
+  const bool cvec = ((reinterpret_cast<uintptr_t>(g.C) & 15) == 0) && (g.ldc % 4 == 0) &&
+                    (splits == 1 || (g.N % 4 == 0 && (reinterpret_cast<uintptr_t>(ws) & 15) == 0));
+  p.c_vec = cvec ? 1 : 0;
+  const int smem = smem_bytes(g.kind, s.tile_n, s.stages);
+  int grid = sms * ctas_per_sm(g.kind, s.tile_n, s.stages);
+  grid = grid / CL * CL;
+  const int need_ctas = p.units * CL;
+  if (grid > need_ctas) grid = need_ctas;
+  if (grid < CL) grid = CL;
+  switch (g.kind * 2 + (CL - 1)) {
+    case TC_BF16 * 2 + 0: status = launch<TC_BF16, 1>(p, grid, smem, st); break;
+    case TC_BF16 * 2 + 1: status = launch<TC_BF16, 2>(p, grid, smem, st); break;
+    case TC_FP8 * 2 + 0: status = launch<TC_FP8, 1>(p, grid, smem, st); break;
+    case TC_FP8 * 2 + 1: status = launch<TC_FP8, 2>(p, grid, smem, st); break;
+    case TC_BF16X3 * 2 + 0: status = launch<TC_BF16X3, 1>(p, grid, smem, st); break;
+    default: status = launch<TC_BF16X3, 2>(p, grid, smem, st); break;
+  }
+  if (status != NK_OK || splits == 1) return status;
+  SplitReduce r;
+  r.partial = p.partial;
+  r.splits = splits;
+  r.M = g.M;
+  r.N = g.N;
+  r.C = g.C;
+  r.scm = g.ldc;
+  r.scn = 1;
+  r.bias = g.bias;
+  r.bias_on_m = g.bias_on_m;
+  r.alpha = g.alpha;
+  r.beta = g.beta;
+  r.relu = g.relu;
+  r.scale_a = g.scale_a;
+  r.scale_b = g.scale_b;
+  return splitk_reduce(r, st);
+}
+
+}  // namespace nk

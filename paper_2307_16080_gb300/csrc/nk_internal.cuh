@@ -1,0 +1,137 @@
+// nk_internal.cuh -- declarations shared by the translation units of libnk.
+//
+// Host side: error reporting, device checks and the internal launch entry
+// points of each kernel family.  Device side: the global failure word that
+// bounded waits set when they give up.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/nk.h"
+
+namespace nk {
+
+// ----------------------------------------------------------------- errors
+nk_status fail(nk_status s, const char* fmt, ...);
+nk_status cuda_fail(cudaError_t e, const char* what);
+nk_status check_launch(const char* what);
+
+// Verifies that the current device is an sm_103 part; caches the answer per
+// device.  Fills the SM count when `sms` is non-null.
+nk_status require_device(int* sms = nullptr);
+
+// Device-side failure word.  Bit 0: a bounded wait expired.  Each
+// translation unit that owns waiting kernels defines its own copy; the host
+// reads and clears all of them in nk_sync_status.
+enum : uint32_t { kErrTimeout = 1u };
+
+// Spin budget shared by the waiting kernels (set through nk_set_wait_budget).
+int64_t wait_budget();
+
+// Reads and clears the failure words of every translation unit.
+nk_status collect_device_errors(uint32_t* flags);
+uint32_t tc_read_and_clear_errors();   // tcgen05 GEMM / conv units
+
+// ----------------------------------------------------------- SIMT (FP32)
+// A[m,k] at A + m*sam + k*sak; B[k,n] at B + k*sbk + n*sbn;
+// C[m,n] at C + m*scm + n*scn (one of scm, scn is 1).
+struct ConvGeom {
+  int n, h, w, c;          // input NHWC extents
+  int kh, kw;              // filter taps
+  int oh, ow;              // output extents
+  int sh, sw, dh, dw, pt, pl;
+  int64_t sin_n, sin_h, sin_w;  // input strides (channel stride is 1)
+};
+
+struct SimtGemm {
+  const float* A;
+  int64_t sam, sak;
+  const float* B;
+  int64_t sbk, sbn;
+  float* C;
+  int64_t scm, scn;
+  const float* bias;
+  int bias_on_m;         // bias indexed by m (transposed problems)
+  int M, N, K;
+  float alpha, beta;
+  int relu;
+  int is_conv;           // A is the implicit im2col matrix of `conv`
+  ConvGeom conv;
+};
+
+// tile: 128 or 64 (square CTA tile); splits >= 1.  When splits > 1 the
+// partial sums go to `ws` ([splits][M][N] FP32) and a reduce pass applies
+// the epilogue.
+nk_status simt_gemm(const SimtGemm& p, int tile, int splits, void* ws, size_t ws_bytes,
+                    cudaStream_t st);
+size_t simt_gemm_ws(int M, int N, int splits);
+
+// Fixed-order split-K reduce with the fused epilogue (warp-shuffle tree).
+struct SplitReduce {
+  const float* partial;  // [splits][M][N] dense
+  int splits;
+  int M, N;
+  float* C;
+  int64_t scm, scn;
+  const float* bias;
+  int bias_on_m;
+  float alpha, beta;
+  int relu;
+  const float* scale_a;  // when set, alpha = 1/(*scale_a * *scale_b) (device scalars)
+  const float* scale_b;
+};
+nk_status splitk_reduce(const SplitReduce& r, cudaStream_t st);
+
+// ------------------------------------------------------------- prep / norm
+nk_status prep_amax(const float* x, int64_t rows, int64_t cols, int64_t ld, float* amax,
+                    void* ws, size_t ws_bytes, cudaStream_t st);
+size_t prep_amax_ws(int64_t n);
+// kind: 0 = bf16, 1 = fp8 (scale from *amax), 2 = bf16 hi/lo pair
+nk_status prep_cast(int kind, const float* in, int64_t rows, int64_t cols, int64_t ld_in,
+                    const float* amax, void* out0, void* out1, int64_t ld_out, int transpose,
+                    float* scale_out, cudaStream_t st);
+nk_status norm_sumsq(const float* C, int64_t ldc, const double* R, int64_t ldr, int64_t M,
+                     int64_t N, double* out, void* ws, size_t ws_bytes, cudaStream_t st);
+size_t norm_ws(int64_t M, int64_t N);
+
+}  // namespace nk
+
+namespace nk {
+
+// -------------------------------------------------- tensor-core GEMM (tcgen05)
+// Operands are K-major in device memory: A [M,K] with row stride lda, B given
+// as Bt [N,K] with row stride ldb (elements; 16-byte multiples).  C is FP32
+// row-major with row stride ldc.  kind: 0 = BF16, 1 = FP8 E4M3, 2 = BF16x3
+// (A2/B2 hold the lo halves).  alpha = 1/(sa*sb) when scale pointers are set.
+enum TcKind { TC_BF16 = 0, TC_FP8 = 1, TC_BF16X3 = 2 };
+
+struct TcGemm {
+  int kind;
+  int M, N, K;
+  const void* A;
+  const void* B;
+  const void* A2;
+  const void* B2;
+  int64_t lda, ldb;
+  float* C;
+  int64_t ldc;
+  const float* bias;
+  int bias_on_m;
+  int relu;
+  float beta;
+  float alpha;
+  const float* scale_a;   // device scalars (FP8 computed on device) or null
+  const float* scale_b;
+};
+
+nk_status tc_gemm(const TcGemm& g, const nk_schedule& s, void* ws, size_t ws_bytes,
+                  cudaStream_t st);
+size_t tc_gemm_ws(const TcGemm& g, const nk_schedule& s);
+// Fills unset fields of `s` with the built-in choice for this problem.
+nk_schedule tc_default_schedule(int kind, int M, int N, int K, int sms);
+bool tc_schedule_valid(int kind, const nk_schedule& s, int M, int N, int K);
+
+}  // namespace nk

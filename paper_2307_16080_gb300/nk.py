@@ -1,0 +1,271 @@
+"""Thin Python binding of libnk (ctypes): argument marshalling only.
+
+Every function here forwards to the C entry point of the same name declared
+in include/nk.h; all arithmetic runs in the library's CUDA kernels.  PyTorch
+tensors serve as device memory and torch's current stream as the stream.
+Importing this module loads libnk.so and raises if it is missing: there is no
+fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libnk.so")
+
+NK_OK = 0
+STATUS = {0: "NK_OK", -1: "NK_ERR_INVALID_ARG", -2: "NK_ERR_UNSUPPORTED", -3: "NK_ERR_MISALIGNED",
+          -4: "NK_ERR_WORKSPACE", -5: "NK_ERR_CUDA", -6: "NK_ERR_TIMEOUT", -7: "NK_ERR_NO_SCHEDULE"}
+NK_F32, NK_BF16, NK_F8E4M3, NK_F64 = 0, 1, 2, 3
+PREC = {"f32": 0, "bf16": 1, "bf16x3": 2, "fp8": 3}
+
+
+class NkError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class nk_tensor(ctypes.Structure):
+    _fields_ = [("ptr", ctypes.c_void_p), ("dtype", ctypes.c_int32), ("rank", ctypes.c_int32),
+                ("shape", ctypes.c_int64 * 4), ("stride", ctypes.c_int64 * 4)]
+
+
+class nk_epilogue(ctypes.Structure):
+    _fields_ = [("bias", ctypes.c_void_p), ("relu", ctypes.c_int32), ("accumulate", ctypes.c_int32),
+                ("scale_a", ctypes.c_float), ("scale_b", ctypes.c_float)]
+
+
+class nk_schedule(ctypes.Structure):
+    _fields_ = [("tile_m", ctypes.c_int32), ("tile_n", ctypes.c_int32), ("tile_k", ctypes.c_int32),
+                ("cluster", ctypes.c_int32), ("stages", ctypes.c_int32), ("split_k", ctypes.c_int32)]
+
+    def as_tuple(self):
+        return (self.tile_m, self.tile_n, self.tile_k, self.cluster, self.stages, self.split_k)
+
+
+class nk_gemm_group(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int32), ("N", ctypes.c_int32), ("K", ctypes.c_int32),
+                ("accumulate", ctypes.c_int32), ("A", ctypes.c_void_p), ("Bt", ctypes.c_void_p),
+                ("C", ctypes.c_void_p), ("lda", ctypes.c_int64), ("ldb", ctypes.c_int64),
+                ("ldc", ctypes.c_int64)]
+
+
+_P = ctypes.c_void_p
+_I32, _I64, _SZ = ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+_PT = ctypes.POINTER(nk_tensor)
+_PE = ctypes.POINTER(nk_epilogue)
+_PS = ctypes.POINTER(nk_schedule)
+
+# name -> (restype, argtypes); mirrors include/nk.h
+SIGNATURES = {
+    "nk_matmul": (_I32, [_PT, _PT, _PT, _I32, _PE, _PS, _P, _SZ, _P]),
+    "nk_matmul_workspace_size": (_I32, [_PT, _PT, _PT, _I32, _PS, ctypes.POINTER(_SZ)]),
+    "nk_grouped_plan_create": (_I32, [_I32, ctypes.POINTER(nk_gemm_group), _I32, _PS, ctypes.POINTER(_P)]),
+    "nk_grouped_plan_run": (_I32, [_P, _P]),
+    "nk_grouped_plan_destroy": (_I32, [_P]),
+    "nk_batch_matmul_grouped": (_I32, [_I32, ctypes.POINTER(nk_gemm_group), _I32, _PS, _P, _SZ, _P]),
+    "nk_grouped_workspace_size": (_I32, [_I32, ctypes.POINTER(nk_gemm_group), _I32, _PS, ctypes.POINTER(_SZ)]),
+    "nk_conv2d_nhwc_hwcf": (_I32, [_PT, _PT, _PT, ctypes.POINTER(_I64), ctypes.POINTER(_I64),
+                                   ctypes.POINTER(_I64), _I32, _PE, _PS, _P, _SZ, _P]),
+    "nk_conv2d_workspace_size": (_I32, [_PT, _PT, _PT, ctypes.POINTER(_I64), ctypes.POINTER(_I64),
+                                        ctypes.POINTER(_I64), _I32, _PS, ctypes.POINTER(_SZ)]),
+    "nk_amax": (_I32, [_P, _I64, _P, _P, _SZ, _P]),
+    "nk_prep_workspace_size": (_SZ, [_I64]),
+    "nk_cast_bf16": (_I32, [_P, _I64, _I64, _I64, _P, _I64, _I32, _P]),
+    "nk_cast_fp8": (_I32, [_P, _I64, _I64, _I64, _P, _P, _I64, _I32, _P, _P]),
+    "nk_split_bf16x3": (_I32, [_P, _I64, _I64, _I64, _P, _P, _I64, _I32, _P]),
+    "nk_rel_frobenius": (_I32, [_P, _I64, _P, _I64, _I64, _I64, _P, _P, _SZ, _P]),
+    "nk_norm_workspace_size": (_SZ, [_I64, _I64]),
+    "nk_last_error": (ctypes.c_char_p, []),
+    "nk_sync_status": (_I32, [_P]),
+    "nk_set_wait_budget": (_I32, [_I64]),
+    "nk_device_info": (_I32, [ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libnk.so (built by __graft_entry__.build()); raise if it is absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libnk.so not built at {LIB_PATH}: run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            if hasattr(L, name):
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    return lib().nk_last_error().decode()
+
+
+def _check(status: int):
+    if status != NK_OK:
+        raise NkError(status, last_error())
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+_DT = {torch.float32: NK_F32, torch.bfloat16: NK_BF16, torch.float8_e4m3fn: NK_F8E4M3,
+       torch.uint8: NK_F8E4M3, torch.float64: NK_F64}
+
+
+def as_nk_tensor(t: torch.Tensor) -> nk_tensor:
+    if t.dim() > 4:
+        raise ValueError("rank > 4")
+    d = nk_tensor()
+    d.ptr = t.data_ptr() if t.numel() else None
+    d.dtype = _DT[t.dtype]
+    d.rank = t.dim()
+    for i in range(t.dim()):
+        d.shape[i] = t.shape[i]
+        d.stride[i] = t.stride(i)
+    return d
+
+
+def _sched(schedule):
+    if schedule is None:
+        return None
+    if isinstance(schedule, nk_schedule):
+        return ctypes.byref(schedule)
+    return ctypes.byref(nk_schedule(*schedule))
+
+
+def _epi(bias, relu, accumulate, scale_a, scale_b):
+    e = nk_epilogue()
+    e.bias = bias.data_ptr() if bias is not None else None
+    e.relu = int(bool(relu))
+    e.accumulate = int(bool(accumulate))
+    e.scale_a = float(scale_a)
+    e.scale_b = float(scale_b)
+    return e
+
+
+def nk_matmul_workspace_size(A, B, C, precision="f32", schedule=None) -> int:
+    n = ctypes.c_size_t(0)
+    ta, tb, tc = as_nk_tensor(A), as_nk_tensor(B), as_nk_tensor(C)
+    _check(lib().nk_matmul_workspace_size(ctypes.byref(ta), ctypes.byref(tb), ctypes.byref(tc),
+                                          PREC[precision], _sched(schedule), ctypes.byref(n)))
+    return n.value
+
+
+def workspace(nbytes: int, device=None) -> torch.Tensor | None:
+    if nbytes == 0:
+        return None
+    return torch.empty(nbytes, dtype=torch.uint8, device=device or "cuda")
+
+
+def nk_matmul(A, B, C, precision="f32", bias=None, relu=False, accumulate=False, scale_a=1.0,
+              scale_b=1.0, schedule=None, ws=None, stream=None):
+    """C = ReLU?(accumulate*C + alpha*(A @ B) + bias) through nk_matmul."""
+    ta, tb, tc = as_nk_tensor(A), as_nk_tensor(B), as_nk_tensor(C)
+    if ws is None:
+        ws = workspace(nk_matmul_workspace_size(A, B, C, precision, schedule), C.device)
+    e = _epi(bias, relu, accumulate, scale_a, scale_b)
+    _check(lib().nk_matmul(ctypes.byref(ta), ctypes.byref(tb), ctypes.byref(tc), PREC[precision],
+                           ctypes.byref(e), _sched(schedule), ws.data_ptr() if ws is not None else None,
+                           ws.numel() if ws is not None else 0, _stream(stream)))
+    return C
+
+
+def _conv_args(stride, dilation, pad):
+    st = (ctypes.c_int64 * 2)(*stride)
+    dl = (ctypes.c_int64 * 2)(*dilation)
+    pd = (ctypes.c_int64 * 4)(*pad)
+    return st, dl, pd
+
+
+def nk_conv2d_workspace_size(I, W, O, stride=(1, 1), dilation=(1, 1), pad=(0, 0, 0, 0),
+                             precision="f32", schedule=None) -> int:
+    n = ctypes.c_size_t(0)
+    ti, tw, to = as_nk_tensor(I), as_nk_tensor(W), as_nk_tensor(O)
+    st, dl, pd = _conv_args(stride, dilation, pad)
+    _check(lib().nk_conv2d_workspace_size(ctypes.byref(ti), ctypes.byref(tw), ctypes.byref(to), st, dl, pd,
+                                          PREC[precision], _sched(schedule), ctypes.byref(n)))
+    return n.value
+
+
+def nk_conv2d_nhwc_hwcf(I, W, O, stride=(1, 1), dilation=(1, 1), pad=(0, 0, 0, 0), precision="f32",
+                        bias=None, relu=False, accumulate=False, schedule=None, ws=None, stream=None):
+    ti, tw, to = as_nk_tensor(I), as_nk_tensor(W), as_nk_tensor(O)
+    st, dl, pd = _conv_args(stride, dilation, pad)
+    if ws is None:
+        ws = workspace(nk_conv2d_workspace_size(I, W, O, stride, dilation, pad, precision, schedule), O.device)
+    e = _epi(bias, relu, accumulate, 1.0, 1.0)
+    _check(lib().nk_conv2d_nhwc_hwcf(ctypes.byref(ti), ctypes.byref(tw), ctypes.byref(to), st, dl, pd,
+                                     PREC[precision], ctypes.byref(e), _sched(schedule),
+                                     ws.data_ptr() if ws is not None else None,
+                                     ws.numel() if ws is not None else 0, _stream(stream)))
+    return O
+
+
+def nk_amax(x: torch.Tensor, out: torch.Tensor, ws=None, stream=None):
+    n = x.numel()
+    if ws is None:
+        ws = workspace(lib().nk_prep_workspace_size(n), x.device)
+    _check(lib().nk_amax(x.data_ptr(), n, out.data_ptr(), ws.data_ptr(), ws.numel(), _stream(stream)))
+    return out
+
+
+def nk_cast_bf16(x: torch.Tensor, out: torch.Tensor, transpose=False, stream=None):
+    rows, cols = x.shape
+    _check(lib().nk_cast_bf16(x.data_ptr(), rows, cols, x.stride(0), out.data_ptr(), out.stride(0),
+                              int(transpose), _stream(stream)))
+    return out
+
+
+def nk_cast_fp8(x: torch.Tensor, amax: torch.Tensor, out: torch.Tensor, transpose=False, scale_out=None,
+                stream=None):
+    rows, cols = x.shape
+    _check(lib().nk_cast_fp8(x.data_ptr(), rows, cols, x.stride(0), amax.data_ptr(), out.data_ptr(),
+                             out.stride(0), int(transpose),
+                             scale_out.data_ptr() if scale_out is not None else None, _stream(stream)))
+    return out
+
+
+def nk_split_bf16x3(x: torch.Tensor, hi: torch.Tensor, lo: torch.Tensor, transpose=False, stream=None):
+    rows, cols = x.shape
+    _check(lib().nk_split_bf16x3(x.data_ptr(), rows, cols, x.stride(0), hi.data_ptr(), lo.data_ptr(),
+                                 hi.stride(0), int(transpose), _stream(stream)))
+    return hi, lo
+
+
+def nk_rel_frobenius(C: torch.Tensor, R: torch.Tensor, out: torch.Tensor | None = None, ws=None,
+                     stream=None) -> torch.Tensor:
+    """Device FP64 sums [sum (C-R)^2, sum R^2]; returns the 2-element tensor."""
+    M, N = C.shape
+    if out is None:
+        out = torch.empty(2, dtype=torch.float64, device=C.device)
+    if ws is None:
+        ws = workspace(lib().nk_norm_workspace_size(M, N), C.device)
+    _check(lib().nk_rel_frobenius(C.data_ptr(), C.stride(0), R.data_ptr(), R.stride(0), M, N,
+                                  out.data_ptr(), ws.data_ptr(), ws.numel(), _stream(stream)))
+    return out
+
+
+def nk_sync_status(stream=None):
+    _check(lib().nk_sync_status(_stream(stream)))
+
+
+def nk_set_wait_budget(iterations: int):
+    _check(lib().nk_set_wait_budget(int(iterations)))
+
+
+def nk_device_info():
+    a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().nk_device_info(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value

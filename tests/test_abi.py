@@ -1,0 +1,59 @@
+"""CPU checks of the C ABI: the library builds, loads, and exports every entry
+point that include/*.h declares; the ctypes binding covers them all.  No
+compute call is made (there is no GPU here)."""
+import glob
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(nk_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_2307_16080_gb300 import _build
+    return _build.build()
+
+
+def test_headers_declare_entry_points():
+    names = _declared()
+    for must in ("nk_matmul", "nk_batch_matmul_grouped", "nk_conv2d_nhwc_hwcf", "nk_last_error"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    missing = sorted(_declared() - exported)
+    assert not missing, missing
+
+
+def test_ctypes_binding_loads_and_covers_header(libpath):
+    import paper_2307_16080_gb300.nk as nk
+    L = nk.lib()
+    for name in _declared():
+        assert hasattr(L, name), name
+        assert name in nk.SIGNATURES, name
+    assert nk.last_error() == ""
+
+
+def test_no_device_means_error_not_fallback(libpath):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import paper_2307_16080_gb300.nk as nk
+    sms = nk.ctypes.c_int32()
+    st = nk.lib().nk_device_info(nk.ctypes.byref(sms), None, None)
+    assert st == -5 and "cuda" in nk.last_error().lower() or st == -5
