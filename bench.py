@@ -151,7 +151,10 @@ def main():
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--ref-rows", type=int, default=16)
     ap.add_argument("--cpu-rows", type=int, default=64)
-    ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the FP8/BF16x3/FP32 sweep")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--no-check", action="store_true", help="skip the sampled accuracy check")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -226,7 +229,7 @@ def main():
 
     # accuracy of this run's output on sampled rows (device FP64 norm vs host oracle rows)
     extra = {}
-    if rank == 0:
+    if rank == 0 and not args.no_check:
         import oracle.nk_oracle as O
         rows = np.sort(synth.raw_u64(77, 1, 32) % np.uint64(n)).astype(np.int64)
         got = c[torch.from_numpy(rows).to(dev)].cpu().numpy()
@@ -275,29 +278,33 @@ def main():
         nk.nk_sync_status()
 
     # end to end through the public API: pinned host FP32 in, host FP32 C out
-    a_h = torch.from_numpy(A).pin_memory()
-    b_h = torch.from_numpy(B).pin_memory()
-    c_h = torch.empty(n, n).pin_memory()
+    e2e = None
+    if not args.no_e2e:
+        a_h = torch.from_numpy(A).pin_memory()
+        b_h = torch.from_numpy(B).pin_memory()
+        c_h = torch.empty(n, n).pin_memory()
 
-    def e2e_step():
-        a32.copy_(a_h, non_blocking=True)
-        b32.copy_(b_h, non_blocking=True)
-        step()
-        c_h.copy_(c, non_blocking=True)
+        def e2e_step():
+            a32.copy_(a_h, non_blocking=True)
+            b32.copy_(b_h, non_blocking=True)
+            step()
+            c_h.copy_(c, non_blocking=True)
 
-    e2e_step()
-    torch.cuda.synchronize()
-    e2e_reps = max(3, args.steps // 4)
-    barrier()
-    t0 = time.perf_counter()
-    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    f0.record(st)
-    for _ in range(e2e_reps):
         e2e_step()
-    f1.record(st)
-    barrier()
-    e2e_ms = max(f0.elapsed_time(f1), (time.perf_counter() - t0) * 1e3) / e2e_reps
-    nk.nk_sync_status()
+        torch.cuda.synchronize()
+        e2e_reps = max(3, args.steps // 4)
+        barrier()
+        t0 = time.perf_counter()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(st)
+        for _ in range(e2e_reps):
+            e2e_step()
+        f1.record(st)
+        barrier()
+        e2e_ms = max(f0.elapsed_time(f1), (time.perf_counter() - t0) * 1e3) / e2e_reps
+        nk.nk_sync_status()
+        e2e = {"value": flop / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
+               "h2d_bytes_per_step": 2 * n * n * 4, "d2h_bytes_per_step": n * n * 4}
 
     if rank != 0:
         if world > 1:
@@ -328,12 +335,11 @@ def main():
                      "kernel": "tc_gemm_kernel<BF16,1>", "peak_source": f"{src} bf16 burst"},
         "gpu_launches": 3 * args.steps,
         "clocks": clk,
-        "e2e": {"value": flop / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
-                "h2d_bytes_per_step": 2 * n * n * 4, "d2h_bytes_per_step": n * n * 4},
+        "e2e": e2e,
         "sweep": sweep,
         "accuracy": extra,
     }
-    if world == 1:
+    if world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(A, B, args.cpu_rows)
     print(json.dumps(line), flush=True)
     if world > 1:

@@ -119,7 +119,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
   const int rank = CL == 2 ? (int)ptx::cluster_ctarank() : 0;
   const int cluster_id = blockIdx.x / CL;
   const int n_clusters = gridDim.x / CL;
-  const uint32_t tmem_cols = 2u * (uint32_t)p.bn < 32u ? 32u : 2u * (uint32_t)p.bn;
+  // Accumulator columns per buffer: BN, or 2*BN for BF16x3 (hi*hi and the
+  // hi*lo + lo*hi corrections accumulate apart and meet in the epilogue, so
+  // the large term sees K/16 roundings instead of 3K/16).
+  const int acc_cols = KIND == TC_BF16X3 ? 2 * p.bn : p.bn;
+  const uint32_t tmem_cols = 2u * (uint32_t)acc_cols < 32u ? 32u : 2u * (uint32_t)acc_cols;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
@@ -209,7 +213,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         const uint32_t aph = (uint32_t)(tc >> 1) & 1u;
         if (!ptx::mbar_wait(tempty_bar(acc), aph ^ 1u, p.budget, abort_flag, &g_tc_err)) break;
         ptx::tc_fence_after();
-        const uint32_t d = tmem_base + (uint32_t)(acc * p.bn);
+        const uint32_t d = tmem_base + (uint32_t)(acc * acc_cols);
+        const uint32_t d2 = d + (uint32_t)p.bn;   // BF16x3 correction accumulator
         for (int kb = kb0; kb < kb1; ++kb, ++it) {
           const int s = it % S;
           const uint32_t ph = (uint32_t)(it / S) & 1u;
@@ -225,8 +230,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
             if (KIND == TC_BF16X3) {
               const uint64_t ad2 = ptx::sw128_desc(a_smem(s, 1) + koff);
               const uint64_t bd2 = ptx::sw128_desc(b_smem(s, 1) + koff);
-              ptx::tc_mma<0>(d, ad, bd2, idesc, 1u);    // hi * lo
-              ptx::tc_mma<0>(d, ad2, bd, idesc, 1u);    // lo * hi
+              ptx::tc_mma<0>(d2, ad, bd2, idesc, accum);   // hi * lo
+              ptx::tc_mma<0>(d2, ad2, bd, idesc, 1u);      // lo * hi
             }
           }
           if (CL == 2) ptx::tc_commit_mc(empty_bar(s), (uint16_t)0x3);
@@ -255,7 +260,14 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
       const bool row_ok = row < p.M;
       for (int c0 = 0; c0 < p.bn; c0 += 32) {
         float v[32];
-        ptx::tmem_ld32(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * p.bn + c0), v);
+        const uint32_t ta = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * acc_cols + c0);
+        ptx::tmem_ld32(ta, v);
+        if (KIND == TC_BF16X3) {
+          float w[32];
+          ptx::tmem_ld32(ta + (uint32_t)p.bn, w);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) v[j] += w[j];
+        }
         const int col0 = t.tn * p.bn + c0;
         if (!row_ok || col0 >= p.N) continue;
         if (p.partial) {
@@ -380,7 +392,8 @@ nk_status launch(const TcParams& p, int grid, int smem, cudaStream_t st) {
 int ctas_per_sm(int kind, int bn, int stages) {
   const int sm = smem_bytes(kind, bn, stages);
   int by_smem = kMaxSmem / sm;
-  int cols = 2 * bn < 32 ? 32 : 2 * bn;
+  const int acc = kind == TC_BF16X3 ? 2 * bn : bn;
+  int cols = 2 * acc < 32 ? 32 : 2 * acc;
   int by_tmem = 512 / cols;
   int r = by_smem < by_tmem ? by_smem : by_tmem;
   return r < 1 ? 1 : (r > 2 ? 2 : r);
@@ -392,6 +405,7 @@ bool tc_schedule_valid(int kind, const nk_schedule& s, int M, int N, int K) {
   (void)M; (void)N; (void)K;
   if (s.tile_m != 128) return false;
   if (s.tile_n != 64 && s.tile_n != 128 && s.tile_n != 256) return false;
+  if (kind == TC_BF16X3 && s.tile_n > 128) return false;   // 2 accumulators x 2 buffers <= 512 cols
   if (s.tile_k != (kind == TC_FP8 ? 128 : 64)) return false;
   if (s.cluster != 1 && s.cluster != 2) return false;
   if (s.split_k < 1 || s.split_k > 32) return false;

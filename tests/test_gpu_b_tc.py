@@ -75,6 +75,15 @@ def test_bf16_schedules_bitwise(nk, sched):
     np.testing.assert_array_equal(C, O.matmul(A, B))
 
 
+@pytest.mark.parametrize("sched", [(128, 64, 64, 1, 2, 1), (128, 128, 64, 2, 3, 2), (128, 64, 64, 2, 4, 3)])
+def test_bf16x3_schedules_bitwise(nk, sched):
+    M, N, K = 260, 200, 384
+    A = synth.small_ints(67, 1, (M, K))
+    B = synth.small_ints(67, 2, (K, N))
+    C = host(_mm(nk, dev(A), dev(B), M, N, "bf16x3", schedule=sched))
+    np.testing.assert_array_equal(C, O.matmul(A, B))
+
+
 @pytest.mark.parametrize("sched", [(128, 128, 128, 1, 4, 1), (128, 256, 128, 2, 4, 2), (128, 64, 128, 1, 3, 1)])
 def test_fp8_schedules_bitwise(nk, sched):
     M, N, K = 260, 384, 640
