@@ -27,8 +27,10 @@
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "nk_internal.cuh"
 #include "tc_ptx.cuh"
@@ -70,6 +72,19 @@ struct TcParams {
   const float* scale_b;
   int64_t budget;
   int c_vec;
+  // grouped launches: per-group shapes, outputs and TMA descriptors in device memory
+  const struct GroupDesc* groups;
+  const int* tile_start;        // [G+1] prefix sums of tiles per group
+  const CUtensorMap* gmaps;     // [G][2]: A_g, Bt_g
+  int G;
+};
+
+struct GroupDesc {
+  int M, N, K, tiles_n;
+  float* C;
+  int64_t ldc;
+  float beta;
+  int pad;
 };
 
 __host__ __device__ inline int stage_bytes(int kind, int bn) {
@@ -79,6 +94,16 @@ __host__ __device__ inline int stage_bytes(int kind, int bn) {
 
 struct Unit {
   int tm, tn, split;
+};
+
+// Everything one role needs to know about a unit of work.
+struct UnitView {
+  int tm, tn, split, kb0, kb1, M, N;
+  const CUtensorMap* ma;
+  const CUtensorMap* mb;
+  float* C;
+  int64_t ldc;
+  float beta;
 };
 
 __device__ __forceinline__ Unit decode_unit(const TcParams& p, int u, int cl, int rank) {
@@ -96,7 +121,50 @@ __device__ __forceinline__ Unit decode_unit(const TcParams& p, int u, int cl, in
   return r;
 }
 
-template <int KIND, int CL>
+template <bool GROUPED>
+__device__ __forceinline__ UnitView view_unit(const TcParams& p, int u, int cl, int rank) {
+  UnitView v;
+  if constexpr (GROUPED) {
+    // group g with tile_start[g] <= u < tile_start[g+1] (binary search)
+    int lo = 0, hi = p.G;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (__ldg(p.tile_start + mid) <= u) lo = mid;
+      else hi = mid;
+    }
+    const GroupDesc& g = p.groups[lo];
+    const int t = u - __ldg(p.tile_start + lo);
+    v.tm = t / g.tiles_n;
+    v.tn = t % g.tiles_n;
+    v.split = 0;
+    v.kb0 = 0;
+    v.kb1 = (g.K + 63) / 64;
+    v.M = g.M;
+    v.N = g.N;
+    v.ma = p.gmaps + 2 * lo;
+    v.mb = p.gmaps + 2 * lo + 1;
+    v.C = g.C;
+    v.ldc = g.ldc;
+    v.beta = g.beta;
+  } else {
+    const Unit t = decode_unit(p, u, cl, rank);
+    v.tm = t.tm;
+    v.tn = t.tn;
+    v.split = t.split;
+    v.kb0 = t.split * p.kb_per_split;
+    v.kb1 = min(p.nkb, v.kb0 + p.kb_per_split);
+    v.M = p.M;
+    v.N = p.N;
+    v.ma = &p.tmA;
+    v.mb = &p.tmB;
+    v.C = p.C;
+    v.ldc = p.ldc;
+    v.beta = p.beta;
+  }
+  return v;
+}
+
+template <int KIND, int CL, bool GROUPED>
 __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_constant__ TcParams p) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = ptx::smem_u32(smem_raw);
@@ -138,7 +206,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     *abort_flag = 0;
     ptx::fence_mbar_init();
   }
-  if (warp == 0 && lane == 0) {
+  if (warp == 0 && lane == 0 && !GROUPED) {
     ptx::tma_prefetch_desc(&p.tmA);
     ptx::tma_prefetch_desc(&p.tmB);
     if (KIND == TC_BF16X3) {
@@ -170,9 +238,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
       const int b_rows = p.bn / CL;
       bool ok = true;
       for (int u = cluster_id; u < p.units && ok; u += n_clusters) {
-        const Unit t = decode_unit(p, u, CL, rank);
-        const int kb0 = t.split * p.kb_per_split;
-        const int kb1 = min(p.nkb, kb0 + p.kb_per_split);
+        const UnitView t = view_unit<GROUPED>(p, u, CL, rank);
+        const int kb0 = t.kb0;
+        const int kb1 = t.kb1;
         for (int kb = kb0; kb < kb1; ++kb, ++it) {
           const int s = it % S;
           const uint32_t ph = (uint32_t)(it / S) & 1u;
@@ -183,8 +251,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
           const int by = t.tn * p.bn + rank * b_rows;
           const int nparts = KIND == TC_BF16X3 ? 2 : 1;
           for (int part = 0; part < nparts; ++part) {
-            const CUtensorMap* ma = part ? &p.tmA2 : &p.tmA;
-            const CUtensorMap* mb = part ? &p.tmB2 : &p.tmB;
+            const CUtensorMap* ma = part ? &p.tmA2 : t.ma;
+            const CUtensorMap* mb = part ? &p.tmB2 : t.mb;
             ptx::tma_load_2d(a_smem(s, part), ma, full_bar(s), kx, ay);
             if (CL == 2)
               ptx::tma_load_2d_mc(b_smem(s, part) + rank * b_rows * kRowBytes, mb, full_bar(s), kx, by,
@@ -206,9 +274,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
       int it = 0, tc = 0;
       bool ok = true;
       for (int u = cluster_id; u < p.units && ok; u += n_clusters, ++tc) {
-        const Unit t = decode_unit(p, u, CL, rank);
-        const int kb0 = t.split * p.kb_per_split;
-        const int kb1 = min(p.nkb, kb0 + p.kb_per_split);
+        const UnitView t = view_unit<GROUPED>(p, u, CL, rank);
+        const int kb0 = t.kb0;
+        const int kb1 = t.kb1;
         const int acc = tc & 1;
         const uint32_t aph = (uint32_t)(tc >> 1) & 1u;
         if (!ptx::mbar_wait(tempty_bar(acc), aph ^ 1u, p.budget, abort_flag, &g_tc_err)) break;
@@ -251,13 +319,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     if (p.scale_a) alpha = __frcp_rn(__fmul_rn(*p.scale_a, *p.scale_b));
     int tc = 0;
     for (int u = cluster_id; u < p.units; u += n_clusters, ++tc) {
-      const Unit t = decode_unit(p, u, CL, rank);
+      const UnitView t = view_unit<GROUPED>(p, u, CL, rank);
       const int acc = tc & 1;
       const uint32_t aph = (uint32_t)(tc >> 1) & 1u;
       if (!ptx::mbar_wait(tfull_bar(acc), aph, p.budget, abort_flag, &g_tc_err)) break;
       ptx::tc_fence_after();
       const int row = t.tm * kBM + q * 32 + lane;
-      const bool row_ok = row < p.M;
+      const bool row_ok = row < t.M;
       for (int c0 = 0; c0 < p.bn; c0 += 32) {
         float v[32];
         const uint32_t ta = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * acc_cols + c0);
@@ -269,7 +337,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
           for (int j = 0; j < 32; ++j) v[j] += w[j];
         }
         const int col0 = t.tn * p.bn + c0;
-        if (!row_ok || col0 >= p.N) continue;
+        if (!row_ok || col0 >= t.N) continue;
         if (p.partial) {
           float* dst = p.partial + ((int64_t)t.split * p.M + row) * p.N + col0;
           if (p.c_vec && col0 + 32 <= p.N) {
@@ -283,19 +351,20 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
           }
           continue;
         }
-        float* dst = p.C + (int64_t)row * p.ldc + col0;
+        float* dst = t.C + (int64_t)row * t.ldc + col0;
         const float bm = (p.bias && p.bias_on_m) ? __ldg(p.bias + row) : 0.f;
-        if (p.c_vec && col0 + 32 <= p.N) {
+        const float beta = t.beta;
+        if (p.c_vec && col0 + 32 <= t.N) {
 #pragma unroll
           for (int j = 0; j < 32; j += 4) {
             float o[4];
             float4 cin = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (p.beta != 0.f) cin = *reinterpret_cast<const float4*>(dst + j);
+            if (beta != 0.f) cin = *reinterpret_cast<const float4*>(dst + j);
             const float ci[4] = {cin.x, cin.y, cin.z, cin.w};
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
               float x = alpha * v[j + e];
-              if (p.beta != 0.f) x = fmaf(p.beta, ci[e], x);
+              if (beta != 0.f) x = fmaf(beta, ci[e], x);
               if (p.bias) x += p.bias_on_m ? bm : __ldg(p.bias + col0 + j + e);
               if (p.relu) x = (x > 0.f || x != x) ? x : 0.f;
               o[e] = x;
@@ -305,9 +374,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         } else {
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
-            if (col0 + j >= p.N) continue;
+            if (col0 + j >= t.N) continue;
             float x = alpha * v[j];
-            if (p.beta != 0.f) x = fmaf(p.beta, dst[j], x);
+            if (beta != 0.f) x = fmaf(beta, dst[j], x);
             if (p.bias) x += p.bias_on_m ? bm : __ldg(p.bias + col0 + j);
             if (p.relu) x = (x > 0.f || x != x) ? x : 0.f;
             dst[j] = x;
@@ -366,9 +435,9 @@ int smem_bytes(int kind, int bn, int stages) {
   return 1024 + stages * stage_bytes(kind, bn) + 8 * (2 * stages + 5) + 16;
 }
 
-template <int KIND, int CL>
+template <int KIND, int CL, bool GROUPED = false>
 nk_status launch(const TcParams& p, int grid, int smem, cudaStream_t st) {
-  auto kern = tc_gemm_kernel<KIND, CL>;
+  auto kern = tc_gemm_kernel<KIND, CL, GROUPED>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(tc_gemm_kernel)");
   cudaLaunchConfig_t cfg = {};
@@ -533,3 +602,188 @@ nk_status tc_gemm(const TcGemm& g, const nk_schedule& s, void* ws, size_t ws_byt
 }
 
 }  // namespace nk
+
+// ====================================================================== grouped
+// linalg.batch_matmul generalised to G independent GEMMs of uneven shapes, all
+// in one persistent launch: a device table holds each group's shape, output
+// and TMA descriptors, and a prefix sum of tiles per group lets every CTA map
+// its running unit index to (group, tile) with a binary search.  Groups are
+// ordered by decreasing K so the longest tiles start first.
+struct nk_grouped_plan {
+  void* dev = nullptr;     // device table (owned when built by nk_grouped_plan_create)
+  bool owned = false;
+  int units = 0;
+  int grid = 0;
+  int smem = 0;
+  nk::TcParams p;
+};
+
+namespace nk {
+namespace {
+
+size_t grouped_bytes(int G) {
+  size_t maps = (size_t)G * 2 * sizeof(CUtensorMap);
+  size_t descs = (size_t)G * sizeof(GroupDesc);
+  size_t starts = (size_t)(G + 1) * sizeof(int);
+  return maps + ((descs + 127) / 128 * 128) + ((starts + 127) / 128 * 128);
+}
+
+nk_schedule grouped_schedule(const nk_schedule* user) {
+  nk_schedule s{128, 128, 64, 1, 0, 1};
+  if (user) {
+    if (user->tile_n) s.tile_n = user->tile_n;
+    if (user->stages) s.stages = user->stages;
+    if (user->cluster) s.cluster = user->cluster;
+    if (user->split_k) s.split_k = user->split_k;
+    if (user->tile_m) s.tile_m = user->tile_m;
+    if (user->tile_k) s.tile_k = user->tile_k;
+  }
+  if (s.stages == 0) {
+    s.stages = 2;
+    while (s.stages < 8 && smem_bytes(TC_BF16, s.tile_n, s.stages + 1) <= kMaxSmem) ++s.stages;
+  }
+  return s;
+}
+
+// Fills `host` (grouped_bytes(G) bytes) with the table for a device buffer at
+// `dev_base`, and the launch parameters.
+nk_status build_grouped(int G, const nk_gemm_group* groups, int precision, const nk_schedule* user,
+                        void* dev_base, std::vector<uint8_t>& host, nk_grouped_plan& plan) {
+  if (G < 0) return fail(NK_ERR_INVALID_ARG, "negative group count");
+  if (G > 0 && !groups) return fail(NK_ERR_INVALID_ARG, "groups is NULL");
+  if (precision != NK_PREC_BF16)
+    return fail(NK_ERR_UNSUPPORTED, "grouped GEMM runs BF16 operands (NK_PREC_BF16) only");
+  const nk_schedule s = grouped_schedule(user);
+  if (s.cluster != 1 || s.split_k != 1 || !tc_schedule_valid(TC_BF16, s, 1, 1, 1))
+    return fail(NK_ERR_NO_SCHEDULE, "grouped schedule needs cluster 1, split_k 1 and a legal tile");
+  int sms = 0;
+  nk_status st = require_device(&sms);
+  if (st != NK_OK) return st;
+  for (int g = 0; g < G; ++g) {
+    const nk_gemm_group& q = groups[g];
+    if (q.M < 1 || q.N < 1 || q.K < 1) return fail(NK_ERR_INVALID_ARG, "group %d has an empty extent", g);
+    if (!q.A || !q.Bt || !q.C) return fail(NK_ERR_INVALID_ARG, "group %d has a NULL pointer", g);
+    if (q.lda < q.K || q.ldb < q.K || q.ldc < q.N)
+      return fail(NK_ERR_INVALID_ARG, "group %d: leading dimension smaller than the row", g);
+    if ((q.lda * 2) % 16 || (q.ldb * 2) % 16 || (reinterpret_cast<uintptr_t>(q.A) & 15) ||
+        (reinterpret_cast<uintptr_t>(q.Bt) & 15))
+      return fail(NK_ERR_MISALIGNED, "group %d: BF16 operands need 16-byte aligned rows", g);
+  }
+  std::vector<int> order(G);
+  for (int g = 0; g < G; ++g) order[g] = g;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return groups[a].K > groups[b].K; });
+  host.assign(grouped_bytes(G), 0);
+  CUtensorMap* maps = reinterpret_cast<CUtensorMap*>(host.data());
+  const size_t off_desc = (size_t)G * 2 * sizeof(CUtensorMap);
+  const size_t off_start = off_desc + ((size_t)G * sizeof(GroupDesc) + 127) / 128 * 128;
+  GroupDesc* descs = reinterpret_cast<GroupDesc*>(host.data() + off_desc);
+  int* starts = reinterpret_cast<int*>(host.data() + off_start);
+  bool cvec = true;
+  int64_t total = 0;
+  for (int i = 0; i < G; ++i) {
+    const nk_gemm_group& q = groups[order[i]];
+    if ((st = make_kmajor_map(&maps[2 * i], false, q.A, q.M, q.K, q.lda, kBM)) != NK_OK) return st;
+    if ((st = make_kmajor_map(&maps[2 * i + 1], false, q.Bt, q.N, q.K, q.ldb, s.tile_n)) != NK_OK) return st;
+    GroupDesc& d = descs[i];
+    d.M = q.M; d.N = q.N; d.K = q.K;
+    d.tiles_n = (q.N + s.tile_n - 1) / s.tile_n;
+    d.C = q.C;
+    d.ldc = q.ldc;
+    d.beta = q.accumulate ? 1.f : 0.f;
+    starts[i] = (int)total;
+    total += (int64_t)((q.M + kBM - 1) / kBM) * d.tiles_n;
+    if (total > INT32_MAX) return fail(NK_ERR_UNSUPPORTED, "too many tiles");
+    cvec = cvec && ((reinterpret_cast<uintptr_t>(q.C) & 15) == 0) && (q.ldc % 4 == 0);
+  }
+  starts[G] = (int)total;
+  TcParams& p = plan.p;
+  memset(&p, 0, sizeof p);
+  p.bn = s.tile_n;
+  p.stages = s.stages;
+  p.units = (int)total;
+  p.splits = 1;
+  p.alpha = 1.f;
+  p.budget = wait_budget();
+  p.c_vec = cvec ? 1 : 0;
+  p.G = G;
+  uint8_t* db = static_cast<uint8_t*>(dev_base);
+  p.gmaps = reinterpret_cast<const CUtensorMap*>(db);
+  p.groups = reinterpret_cast<const GroupDesc*>(db + off_desc);
+  p.tile_start = reinterpret_cast<const int*>(db + off_start);
+  plan.units = (int)total;
+  plan.smem = smem_bytes(TC_BF16, s.tile_n, s.stages);
+  int grid = sms * ctas_per_sm(TC_BF16, s.tile_n, s.stages);
+  plan.grid = grid < plan.units ? grid : plan.units;
+  return NK_OK;
+}
+
+}  // namespace
+}  // namespace nk
+
+using namespace nk;
+
+extern "C" {
+
+nk_status nk_grouped_workspace_size(int32_t G, const nk_gemm_group* groups, int32_t precision,
+                                    const nk_schedule* sched, size_t* bytes) {
+  (void)groups; (void)precision; (void)sched;
+  if (!bytes) return fail(NK_ERR_INVALID_ARG, "bytes is NULL");
+  if (G < 0) return fail(NK_ERR_INVALID_ARG, "negative group count");
+  *bytes = grouped_bytes(G);
+  return NK_OK;
+}
+
+nk_status nk_grouped_plan_create(int32_t G, const nk_gemm_group* groups, int32_t precision,
+                                 const nk_schedule* sched, nk_grouped_plan** out) {
+  if (!out) return fail(NK_ERR_INVALID_ARG, "plan is NULL");
+  *out = nullptr;
+  auto* plan = new nk_grouped_plan();
+  void* dev = nullptr;
+  const size_t bytes = grouped_bytes(G);
+  cudaError_t e = cudaMalloc(&dev, bytes > 0 ? bytes : 1);
+  if (e != cudaSuccess) { delete plan; return cuda_fail(e, "cudaMalloc(grouped plan)"); }
+  std::vector<uint8_t> host;
+  nk_status s = build_grouped(G, groups, precision, sched, dev, host, *plan);
+  if (s == NK_OK && bytes) {
+    e = cudaMemcpy(dev, host.data(), bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) s = cuda_fail(e, "cudaMemcpy(grouped plan)");
+  }
+  if (s != NK_OK) { cudaFree(dev); delete plan; return s; }
+  plan->dev = dev;
+  plan->owned = true;
+  *out = plan;
+  return NK_OK;
+}
+
+nk_status nk_grouped_plan_run(const nk_grouped_plan* plan, void* stream) {
+  if (!plan) return fail(NK_ERR_INVALID_ARG, "plan is NULL");
+  if (plan->units == 0) return NK_OK;
+  return launch<TC_BF16, 1, true>(plan->p, plan->grid, plan->smem, static_cast<cudaStream_t>(stream));
+}
+
+nk_status nk_grouped_plan_destroy(nk_grouped_plan* plan) {
+  if (!plan) return NK_OK;
+  if (plan->owned && plan->dev) cudaFree(plan->dev);
+  delete plan;
+  return NK_OK;
+}
+
+nk_status nk_batch_matmul_grouped(int32_t G, const nk_gemm_group* groups, int32_t precision,
+                                  const nk_schedule* sched, void* ws, size_t ws_bytes, void* stream) {
+  const size_t bytes = grouped_bytes(G);
+  if (G > 0 && (!ws || ws_bytes < bytes))
+    return fail(NK_ERR_WORKSPACE, "grouped GEMM needs %zu bytes of workspace", bytes);
+  if (ws && (reinterpret_cast<uintptr_t>(ws) & 127))
+    return fail(NK_ERR_MISALIGNED, "grouped workspace must be 128-byte aligned");
+  nk_grouped_plan plan;
+  std::vector<uint8_t> host;
+  nk_status s = build_grouped(G, groups, precision, sched, ws, host, plan);
+  if (s != NK_OK || plan.units == 0) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(ws, host.data(), bytes, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(grouped table)");
+  // a pageable source is staged before cudaMemcpyAsync returns, so `host` may go
+  return launch<TC_BF16, 1, true>(plan.p, plan.grid, plan.smem, st);
+}
+
+}  // extern "C"

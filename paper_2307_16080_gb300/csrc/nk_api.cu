@@ -521,26 +521,3 @@ nk_status nk_rel_frobenius(const float* C, int64_t ldc, const double* R, int64_t
 
 }  // extern "C"
 
-// ------------------------------------------------------------ grouped GEMM
-// (implemented in k_tc_grouped.cu once available)
-extern "C" {
-struct nk_grouped_plan {
-  int dummy;
-};
-nk_status nk_grouped_plan_create(int32_t, const nk_gemm_group*, int32_t, const nk_schedule*,
-                                 nk_grouped_plan**) {
-  return fail(NK_ERR_UNSUPPORTED, "grouped GEMM not built");
-}
-nk_status nk_grouped_plan_run(const nk_grouped_plan*, void*) {
-  return fail(NK_ERR_UNSUPPORTED, "grouped GEMM not built");
-}
-nk_status nk_grouped_plan_destroy(nk_grouped_plan*) { return NK_OK; }
-nk_status nk_batch_matmul_grouped(int32_t, const nk_gemm_group*, int32_t, const nk_schedule*, void*,
-                                  size_t, void*) {
-  return fail(NK_ERR_UNSUPPORTED, "grouped GEMM not built");
-}
-nk_status nk_grouped_workspace_size(int32_t, const nk_gemm_group*, int32_t, const nk_schedule*,
-                                    size_t*) {
-  return fail(NK_ERR_UNSUPPORTED, "grouped GEMM not built");
-}
-}

@@ -269,3 +269,47 @@ def nk_device_info():
     a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
     _check(lib().nk_device_info(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
     return a.value, b.value, c.value
+
+
+# ------------------------------------------------------------------ grouped GEMM
+def make_groups(As, Bts, Cs, accumulate=False):
+    """nk_gemm_group array for BF16 A_g [M,K], Bt_g [N,K] (row-major) and FP32 C_g [M,N]."""
+    G = len(As)
+    arr = (nk_gemm_group * max(G, 1))()
+    for g, (a, bt, c) in enumerate(zip(As, Bts, Cs)):
+        q = arr[g]
+        q.M, q.K = a.shape
+        q.N = bt.shape[0]
+        q.accumulate = int(bool(accumulate))
+        q.A, q.Bt, q.C = a.data_ptr(), bt.data_ptr(), c.data_ptr()
+        q.lda, q.ldb, q.ldc = a.stride(0), bt.stride(0), c.stride(0)
+    return arr, G
+
+
+def nk_grouped_workspace_size(G: int) -> int:
+    n = ctypes.c_size_t(0)
+    _check(lib().nk_grouped_workspace_size(G, None, PREC["bf16"], None, ctypes.byref(n)))
+    return n.value
+
+
+def nk_grouped_plan_create(groups, G, precision="bf16", schedule=None):
+    h = ctypes.c_void_p()
+    _check(lib().nk_grouped_plan_create(G, groups, PREC[precision], _sched(schedule), ctypes.byref(h)))
+    return h
+
+
+def nk_grouped_plan_run(plan, stream=None):
+    _check(lib().nk_grouped_plan_run(plan, _stream(stream)))
+
+
+def nk_grouped_plan_destroy(plan):
+    _check(lib().nk_grouped_plan_destroy(plan))
+
+
+def nk_batch_matmul_grouped(groups, G, precision="bf16", schedule=None, ws=None, stream=None):
+    if ws is None:
+        ws = workspace(nk_grouped_workspace_size(G))
+    _check(lib().nk_batch_matmul_grouped(G, groups, PREC[precision], _sched(schedule),
+                                         ws.data_ptr() if ws is not None else None,
+                                         ws.numel() if ws is not None else 0, _stream(stream)))
+    return ws
