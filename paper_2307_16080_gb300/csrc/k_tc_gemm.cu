@@ -28,6 +28,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <climits>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -55,6 +56,16 @@ constexpr int kRowBytes = 128;      // one K block = one 128-byte swizzle row
 constexpr int kGroupM = 8;          // rasterisation: 8 (pair-)rows of tiles per band
 constexpr int kMaxSmem = 232448;    // 227 KB opt-in limit
 
+// Output tile of the convolution: NB images x R output rows x Q output
+// columns (NB*R*Q <= 128 GEMM rows), and the input walk for each filter tap.
+struct ConvTile {
+  int Q, R, NB;
+  int tiles_w, tiles_h;
+  int N, OH, OW;
+  int sh, sw, dh, dw, pt, pl;
+  int KW, cblocks;
+};
+
 struct TcParams {
   CUtensorMap tmA, tmB, tmA2, tmB2;
   int M, N, K;
@@ -77,6 +88,9 @@ struct TcParams {
   const int* tile_start;        // [G+1] prefix sums of tiles per group
   const CUtensorMap* gmaps;     // [G][2]: A_g, Bt_g
   int G;
+  // implicit-GEMM convolution (tmA: 4-D NHWC input map, tmB: 3-D [F][taps][C] map)
+  ConvTile cv;
+  uint32_t a_box_bytes;         // bytes TMA writes per A stage (16 KB unless a conv tile is short)
 };
 
 struct GroupDesc {
@@ -164,7 +178,19 @@ __device__ __forceinline__ UnitView view_unit(const TcParams& p, int u, int cl, 
   return v;
 }
 
-template <int KIND, int CL, bool GROUPED>
+// Output row of GEMM row r (0..127) of conv tile tm, or -1 if it is padding.
+__device__ __forceinline__ int conv_row(const ConvTile& c, int tm, int r) {
+  if (r >= c.Q * c.R * c.NB) return -1;
+  const int tw = tm % c.tiles_w;
+  const int th = (tm / c.tiles_w) % c.tiles_h;
+  const int tb = tm / (c.tiles_w * c.tiles_h);
+  const int q = r % c.Q, rr = (r / c.Q) % c.R, b = r / (c.Q * c.R);
+  const int n = tb * c.NB + b, oh = th * c.R + rr, ow = tw * c.Q + q;
+  if (n >= c.N || oh >= c.OH || ow >= c.OW) return -1;
+  return (n * c.OH + oh) * c.OW + ow;
+}
+
+template <int KIND, int CL, bool GROUPED, bool CONV = false>
 __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_constant__ TcParams p) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = ptx::smem_u32(smem_raw);
@@ -245,6 +271,25 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
           const int s = it % S;
           const uint32_t ph = (uint32_t)(it / S) & 1u;
           if (!ptx::mbar_wait(empty_bar(s), ph ^ 1u, p.budget, abort_flag, &g_tc_err)) { ok = false; break; }
+          if constexpr (CONV) {
+            // K block kb = (filter tap, 64-channel block); the A box is the
+            // input window that tap sees, shifted and strided by TMA.
+            const ConvTile& c = p.cv;
+            ptx::mbar_arrive_expect_tx(full_bar(s), p.a_box_bytes + (uint32_t)b_bytes);
+            const int tap = kb / c.cblocks, c0 = (kb % c.cblocks) * 64;
+            const int kh = tap / c.KW, kw = tap % c.KW;
+            const int tw = t.tm % c.tiles_w, th = (t.tm / c.tiles_w) % c.tiles_h;
+            const int tb = t.tm / (c.tiles_w * c.tiles_h);
+            ptx::tma_load_4d(a_smem(s, 0), &p.tmA, full_bar(s), c0, tw * c.Q * c.sw + kw * c.dw - c.pl,
+                             th * c.R * c.sh + kh * c.dh - c.pt, tb * c.NB);
+            const int fy = t.tn * p.bn + rank * b_rows;
+            if (CL == 2)
+              ptx::tma_load_3d_mc(b_smem(s, 0) + rank * b_rows * kRowBytes, &p.tmB, full_bar(s), c0, tap,
+                                  fy, (uint16_t)0x3);
+            else
+              ptx::tma_load_3d(b_smem(s, 0), &p.tmB, full_bar(s), c0, tap, fy);
+            continue;
+          }
           ptx::mbar_arrive_expect_tx(full_bar(s), (uint32_t)sb);
           const int kx = kb * kblk;
           const int ay = t.tm * kBM;
@@ -324,8 +369,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
       const uint32_t aph = (uint32_t)(tc >> 1) & 1u;
       if (!ptx::mbar_wait(tfull_bar(acc), aph, p.budget, abort_flag, &g_tc_err)) break;
       ptx::tc_fence_after();
-      const int row = t.tm * kBM + q * 32 + lane;
-      const bool row_ok = row < t.M;
+      const int row = CONV ? conv_row(p.cv, t.tm, q * 32 + lane) : t.tm * kBM + q * 32 + lane;
+      const bool row_ok = CONV ? row >= 0 : row < t.M;
       for (int c0 = 0; c0 < p.bn; c0 += 32) {
         float v[32];
         const uint32_t ta = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * acc_cols + c0);
@@ -435,9 +480,9 @@ int smem_bytes(int kind, int bn, int stages) {
   return 1024 + stages * stage_bytes(kind, bn) + 8 * (2 * stages + 5) + 16;
 }
 
-template <int KIND, int CL, bool GROUPED = false>
+template <int KIND, int CL, bool GROUPED = false, bool CONV = false>
 nk_status launch(const TcParams& p, int grid, int smem, cudaStream_t st) {
-  auto kern = tc_gemm_kernel<KIND, CL, GROUPED>;
+  auto kern = tc_gemm_kernel<KIND, CL, GROUPED, CONV>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(tc_gemm_kernel)");
   cudaLaunchConfig_t cfg = {};
@@ -603,6 +648,157 @@ nk_status tc_gemm(const TcGemm& g, const nk_schedule& s, void* ws, size_t ws_byt
 
 }  // namespace nk
 
+// ===================================================================== conv
+namespace nk {
+namespace {
+
+// Output tile (Q columns x R rows x NB images, <= 128 GEMM rows) with the
+// fewest tiles; ties go to the widest rows.
+ConvTile choose_conv_tile(const ConvGeom& g) {
+  ConvTile best{};
+  int64_t best_tiles = INT64_MAX;
+  for (int Q = 1; Q <= 128 && Q <= g.ow; ++Q) {
+    if (Q * g.sw > 256) break;
+    for (int R = 1; Q * R <= 128 && R <= g.oh; ++R) {
+      if (R * g.sh > 256) break;
+      const int NB = std::max(1, std::min(g.n, 128 / (Q * R)));
+      const int64_t tiles = (int64_t)((g.n + NB - 1) / NB) * ((g.oh + R - 1) / R) * ((g.ow + Q - 1) / Q);
+      if (tiles < best_tiles || (tiles == best_tiles && Q > best.Q)) {
+        best_tiles = tiles;
+        best.Q = Q; best.R = R; best.NB = NB;
+      }
+    }
+  }
+  best.tiles_w = (g.ow + best.Q - 1) / best.Q;
+  best.tiles_h = (g.oh + best.R - 1) / best.R;
+  best.N = g.n; best.OH = g.oh; best.OW = g.ow;
+  best.sh = g.sh; best.sw = g.sw; best.dh = g.dh; best.dw = g.dw; best.pt = g.pt; best.pl = g.pl;
+  best.KW = g.kw;
+  best.cblocks = (g.c + 63) / 64;
+  return best;
+}
+
+nk_status make_conv_maps(TcParams& p, const TcConv& c, const ConvTile& t, int bn_box) {
+  auto fn = encode_fn();
+  if (!fn) return fail(NK_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+  const ConvGeom& g = c.g;
+  {
+    cuuint64_t dims[4] = {(cuuint64_t)g.c, (cuuint64_t)g.w, (cuuint64_t)g.h, (cuuint64_t)g.n};
+    cuuint64_t strides[3] = {(cuuint64_t)c.sI_w * 2, (cuuint64_t)c.sI_h * 2, (cuuint64_t)c.sI_n * 2};
+    cuuint32_t box[4] = {64, (cuuint32_t)(t.Q * g.sw), (cuuint32_t)(t.R * g.sh), (cuuint32_t)t.NB};
+    cuuint32_t es[4] = {1, (cuuint32_t)g.sw, (cuuint32_t)g.sh, 1};
+    CUresult r = fn(&p.tmA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(c.I), dims, strides, box,
+                    es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(NK_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d) for the conv input", (int)r);
+  }
+  {
+    const int taps = g.kh * g.kw;
+    cuuint64_t dims[3] = {(cuuint64_t)g.c, (cuuint64_t)taps, (cuuint64_t)c.F};
+    cuuint64_t strides[2] = {(cuuint64_t)c.ldw * 2, (cuuint64_t)c.ldw * taps * 2};
+    cuuint32_t box[3] = {64, 1, (cuuint32_t)bn_box};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = fn(&p.tmB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(c.Wt), dims, strides, box,
+                    es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(NK_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d) for the conv weights", (int)r);
+  }
+  return NK_OK;
+}
+
+}  // namespace
+
+nk_schedule tc_conv_default_schedule(const ConvGeom& g, int F, int sms) {
+  nk_schedule s{};
+  s.tile_m = 128;
+  s.tile_k = 64;
+  s.tile_n = F <= 64 ? 64 : F <= 128 ? 128 : 256;
+  s.cluster = 1;
+  s.stages = 2;
+  while (s.stages < 8 && smem_bytes(TC_BF16, s.tile_n, s.stages + 1) <= kMaxSmem) ++s.stages;
+  const ConvTile t = choose_conv_tile(g);
+  const int tiles = t.tiles_w * t.tiles_h * ((g.n + t.NB - 1) / t.NB) * ((F + s.tile_n - 1) / s.tile_n);
+  const int nkb = g.kh * g.kw * t.cblocks;
+  s.split_k = 1;
+  while (tiles * s.split_k * 2 <= sms && nkb / (s.split_k * 2) >= 4 && s.split_k < 16) s.split_k *= 2;
+  return s;
+}
+
+size_t tc_conv_ws(const TcConv& c, const nk_schedule& s) {
+  if (s.split_k <= 1) return 0;
+  return (size_t)s.split_k * c.g.n * c.g.oh * c.g.ow * c.F * sizeof(float);
+}
+
+nk_status tc_conv(const TcConv& c, const nk_schedule& s, void* ws, size_t ws_bytes, cudaStream_t st) {
+  int sms = 0;
+  nk_status status = require_device(&sms);
+  if (status != NK_OK) return status;
+  const ConvGeom& g = c.g;
+  const int M = g.n * g.oh * g.ow;
+  if (!tc_schedule_valid(TC_BF16, s, M, c.F, g.kh * g.kw * g.c))
+    return fail(NK_ERR_NO_SCHEDULE, "illegal tensor-core schedule for conv");
+  if ((c.sI_w * 2) % 16 || (c.sI_h * 2) % 16 || (c.sI_n * 2) % 16 || (c.ldw * 2) % 16 ||
+      (reinterpret_cast<uintptr_t>(c.I) & 15) || (reinterpret_cast<uintptr_t>(c.Wt) & 15))
+    return fail(NK_ERR_MISALIGNED, "conv operands need 16-byte aligned bases and strides");
+  const ConvTile t = choose_conv_tile(g);
+  if (g.sw > 8 || g.sh > 8) return fail(NK_ERR_UNSUPPORTED, "conv stride above 8");
+  TcParams p;
+  memset(&p, 0, sizeof p);
+  const int CL = s.cluster;
+  if ((status = make_conv_maps(p, c, t, s.tile_n / CL)) != NK_OK) return status;
+  p.cv = t;
+  p.a_box_bytes = (uint32_t)(t.Q * t.R * t.NB * kRowBytes);
+  p.M = M; p.N = c.F; p.K = g.kh * g.kw * g.c;
+  p.bn = s.tile_n;
+  p.stages = s.stages;
+  const int tm = t.tiles_w * t.tiles_h * ((g.n + t.NB - 1) / t.NB);
+  p.tiles_m = (tm + CL - 1) / CL * CL;
+  p.tiles_n = (c.F + s.tile_n - 1) / s.tile_n;
+  p.nkb = g.kh * g.kw * t.cblocks;
+  int splits = s.split_k > p.nkb ? p.nkb : s.split_k;
+  p.kb_per_split = (p.nkb + splits - 1) / splits;
+  splits = (p.nkb + p.kb_per_split - 1) / p.kb_per_split;
+  p.splits = splits;
+  p.units = (p.tiles_m / CL) * p.tiles_n * splits;
+  p.C = c.O;
+  p.ldc = c.F;
+  if (splits > 1) {
+    const size_t need = (size_t)splits * M * c.F * sizeof(float);
+    if (!ws || ws_bytes < need) return fail(NK_ERR_WORKSPACE, "split-K needs %zu bytes of workspace", need);
+    p.partial = static_cast<float*>(ws);
+  }
+  p.bias = c.bias;
+  p.relu = c.relu;
+  p.beta = c.beta;
+  p.alpha = 1.f;
+  p.budget = wait_budget();
+  p.c_vec = ((reinterpret_cast<uintptr_t>(c.O) & 15) == 0 && c.F % 4 == 0 &&
+             (splits == 1 || (reinterpret_cast<uintptr_t>(ws) & 15) == 0)) ? 1 : 0;
+  const int smem = smem_bytes(TC_BF16, s.tile_n, s.stages);
+  int grid = sms * ctas_per_sm(TC_BF16, s.tile_n, s.stages);
+  grid = grid / CL * CL;
+  if (grid > p.units * CL) grid = p.units * CL;
+  if (grid < CL) grid = CL;
+  status = CL == 2 ? launch<TC_BF16, 2, false, true>(p, grid, smem, st)
+                   : launch<TC_BF16, 1, false, true>(p, grid, smem, st);
+  if (status != NK_OK || splits == 1) return status;
+  SplitReduce r{};
+  r.partial = p.partial;
+  r.splits = splits;
+  r.M = M;
+  r.N = c.F;
+  r.C = c.O;
+  r.scm = c.F;
+  r.scn = 1;
+  r.bias = c.bias;
+  r.alpha = 1.f;
+  r.beta = c.beta;
+  r.relu = c.relu;
+  return splitk_reduce(r, st);
+}
+
+}  // namespace nk
+
 // ====================================================================== grouped
 // linalg.batch_matmul generalised to G independent GEMMs of uneven shapes, all
 // in one persistent launch: a device table holds each group's shape, output
@@ -659,8 +855,14 @@ nk_status build_grouped(int G, const nk_gemm_group* groups, int precision, const
   int sms = 0;
   nk_status st = require_device(&sms);
   if (st != NK_OK) return st;
+  // A single-row operand's leading dimension is never stepped over; give TMA
+  // a legal one (row padded to 16 bytes) whatever the caller passed.
+  auto ld_a = [](const nk_gemm_group& q) { return q.M == 1 ? (int64_t)(q.K + 7) / 8 * 8 : q.lda; };
+  auto ld_b = [](const nk_gemm_group& q) { return q.N == 1 ? (int64_t)(q.K + 7) / 8 * 8 : q.ldb; };
+  auto ld_c = [](const nk_gemm_group& q) { return q.M == 1 ? (int64_t)(q.N + 3) / 4 * 4 : q.ldc; };
   for (int g = 0; g < G; ++g) {
-    const nk_gemm_group& q = groups[g];
+    nk_gemm_group q = groups[g];
+    q.lda = ld_a(q); q.ldb = ld_b(q); q.ldc = ld_c(q);
     if (q.M < 1 || q.N < 1 || q.K < 1) return fail(NK_ERR_INVALID_ARG, "group %d has an empty extent", g);
     if (!q.A || !q.Bt || !q.C) return fail(NK_ERR_INVALID_ARG, "group %d has a NULL pointer", g);
     if (q.lda < q.K || q.ldb < q.K || q.ldc < q.N)
@@ -681,7 +883,8 @@ nk_status build_grouped(int G, const nk_gemm_group* groups, int precision, const
   bool cvec = true;
   int64_t total = 0;
   for (int i = 0; i < G; ++i) {
-    const nk_gemm_group& q = groups[order[i]];
+    nk_gemm_group q = groups[order[i]];
+    q.lda = ld_a(q); q.ldb = ld_b(q); q.ldc = ld_c(q);
     if ((st = make_kmajor_map(&maps[2 * i], false, q.A, q.M, q.K, q.lda, kBM)) != NK_OK) return st;
     if ((st = make_kmajor_map(&maps[2 * i + 1], false, q.Bt, q.N, q.K, q.ldb, s.tile_n)) != NK_OK) return st;
     GroupDesc& d = descs[i];

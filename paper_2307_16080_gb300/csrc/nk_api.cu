@@ -388,7 +388,8 @@ static nk_status plan_conv(const nk_tensor* I, const nk_tensor* W, const nk_tens
   if (I->stride[3] != 1 || W->stride[3] != 1 || O->stride[3] != 1)
     return fail(NK_ERR_UNSUPPORTED, "the last dimension of I, W and O must have unit stride");
   if (O->dtype != NK_F32) return fail(NK_ERR_UNSUPPORTED, "O must be FP32");
-  if (I->dtype != W->dtype) return fail(NK_ERR_INVALID_ARG, "I and W must share a dtype");
+  if (I->dtype != W->dtype && !(I->dtype == NK_BF16 && W->dtype == NK_F32))
+    return fail(NK_ERR_INVALID_ARG, "I and W must share a dtype (or BF16 I with FP32 W)");
   for (int i = 0; i < 2; ++i)
     if (stride[i] < 1 || dilation[i] < 1) return fail(NK_ERR_INVALID_ARG, "stride and dilation must be >= 1");
   for (int i = 0; i < 4; ++i)
@@ -413,6 +414,51 @@ static nk_status plan_conv(const nk_tensor* I, const nk_tensor* W, const nk_tens
   return NK_OK;
 }
 
+// Workspace layout of a tensor-core convolution: BF16 copies of I (when given
+// in FP32, channels padded to a multiple of 8) and of W transposed to
+// [F][taps][Cp], then the split-K partials.
+struct ConvPlan {
+  nk_schedule sched{};
+  int Cp = 0;
+  bool cast_i = false;
+  size_t off_i = 0, off_w = 0, off_k = 0, kern = 0, total = 0;
+};
+
+static nk_status plan_tc_conv(const nk_tensor* I, const nk_tensor* W, const nk_tensor* O, const ConvGeom& g,
+                              const nk_schedule* user, ConvPlan& P) {
+  if (W->dtype != NK_F32) return fail(NK_ERR_UNSUPPORTED, "tensor-core conv takes FP32 HWCF weights");
+  if (I->dtype != NK_F32 && I->dtype != NK_BF16) return fail(NK_ERR_UNSUPPORTED, "conv input must be FP32 or BF16");
+  int sms = 152, dev = 0, v = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess &&
+      cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+    sms = v;
+  const int F = (int)W->shape[3];
+  nk_schedule d = tc_conv_default_schedule(g, F, sms);
+  nk_schedule S = user ? *user : nk_schedule{0, 0, 0, 0, 0, 0};
+  if (S.tile_m == 0) S.tile_m = d.tile_m;
+  if (S.tile_n == 0) S.tile_n = d.tile_n;
+  if (S.tile_k == 0) S.tile_k = d.tile_k;
+  if (S.cluster == 0) S.cluster = d.cluster;
+  if (S.stages == 0) S.stages = d.stages;
+  if (S.split_k == 0) S.split_k = d.split_k;
+  if (!tc_schedule_valid(TC_BF16, S, g.n * g.oh * g.ow, F, g.kh * g.kw * g.c))
+    return fail(NK_ERR_NO_SCHEDULE, "illegal conv schedule");
+  P.sched = S;
+  P.Cp = (g.c + 7) / 8 * 8;
+  P.cast_i = I->dtype == NK_F32;
+  if (P.cast_i && !(g.sin_w == g.c && g.sin_h == (int64_t)g.w * g.c && g.sin_n == (int64_t)g.h * g.w * g.c))
+    return fail(NK_ERR_UNSUPPORTED, "an FP32 conv input must be contiguous NHWC for the BF16 path");
+  size_t off = 0;
+  if (P.cast_i) { P.off_i = off; off += align_up((size_t)g.n * g.h * g.w * P.Cp * 2); }
+  P.off_w = off; off += align_up((size_t)F * g.kh * g.kw * P.Cp * 2);
+  TcConv c{};
+  c.g = g; c.F = F;
+  P.kern = tc_conv_ws(c, S);
+  P.off_k = off; off += align_up(P.kern);
+  P.total = off;
+  return NK_OK;
+}
+
 static bool o_dense(const nk_tensor* O) {
   return O->stride[2] == O->shape[3] && O->stride[1] == O->shape[2] * O->stride[2] &&
          O->stride[0] == O->shape[1] * O->stride[1];
@@ -426,8 +472,14 @@ nk_status nk_conv2d_workspace_size(const nk_tensor* I, const nk_tensor* W, const
   ConvGeom g;
   nk_status s = plan_conv(I, W, O, stride, dilation, pad, g);
   if (s != NK_OK) return s;
-  if (precision != NK_PREC_F32) return fail(NK_ERR_UNSUPPORTED, "conv precision %d not available", precision);
   const int M = g.n * g.oh * g.ow, N = (int)W->shape[3];
+  if (precision == NK_PREC_BF16) {
+    ConvPlan P;
+    if ((s = plan_tc_conv(I, W, O, g, sched, P)) != NK_OK) return s;
+    *bytes = P.total;
+    return NK_OK;
+  }
+  if (precision != NK_PREC_F32) return fail(NK_ERR_UNSUPPORTED, "conv precision %d not available", precision);
   const int split = sched && sched->split_k > 0 ? sched->split_k : 1;
   *bytes = simt_gemm_ws(M, N, split);
   return NK_OK;
@@ -443,9 +495,50 @@ nk_status nk_conv2d_nhwc_hwcf(const nk_tensor* I, const nk_tensor* W, nk_tensor*
   if ((s = require_device()) != NK_OK) return s;
   const nk_epilogue e0{nullptr, 0, 0, 1.f, 1.f};
   const nk_epilogue& E = epi ? *epi : e0;
+  if (!o_dense(O)) return fail(NK_ERR_UNSUPPORTED, "O must be contiguous NHWC");
+  if (precision == NK_PREC_BF16) {
+    ConvPlan P;
+    if ((s = plan_tc_conv(I, W, O, g, sched, P)) != NK_OK) return s;
+    if (P.total > 0 && (!ws || ws_bytes < P.total))
+      return fail(NK_ERR_WORKSPACE, "conv needs %zu bytes of workspace (got %zu)", P.total, ws_bytes);
+    if (ws && !aligned16(ws)) return fail(NK_ERR_MISALIGNED, "workspace must be 16-byte aligned");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    char* w = static_cast<char*>(ws);
+    const int F = (int)W->shape[3], taps = g.kh * g.kw;
+    TcConv c{};
+    c.g = g; c.F = F;
+    if (P.cast_i) {
+      s = prep_cast(0, static_cast<const float*>(I->ptr), (int64_t)g.n * g.h * g.w, g.c, g.c, nullptr,
+                    w + P.off_i, nullptr, P.Cp, 0, nullptr, st);
+      if (s != NK_OK) return s;
+      c.I = w + P.off_i;
+      c.sI_w = P.Cp; c.sI_h = (int64_t)g.w * P.Cp; c.sI_n = (int64_t)g.h * g.w * P.Cp;
+    } else {
+      c.I = I->ptr;
+      c.sI_w = g.sin_w; c.sI_h = g.sin_h; c.sI_n = g.sin_n;
+    }
+    const float* Wf = static_cast<const float*>(W->ptr);
+    char* wt = w + P.off_w;
+    if (P.Cp == g.c) {   // [taps*C, F] -> [F, taps*C] in one transposing cast
+      s = prep_cast(0, Wf, (int64_t)taps * g.c, F, F, nullptr, wt, nullptr, (int64_t)taps * g.c, 1, nullptr, st);
+      if (s != NK_OK) return s;
+    } else {             // one tap at a time into rows padded to Cp channels
+      for (int tap = 0; tap < taps; ++tap) {
+        s = prep_cast(0, Wf + (int64_t)tap * g.c * F, g.c, F, F, nullptr, wt + (size_t)tap * P.Cp * 2, nullptr,
+                      (int64_t)taps * P.Cp, 1, nullptr, st);
+        if (s != NK_OK) return s;
+      }
+    }
+    c.Wt = wt;
+    c.ldw = P.Cp;
+    c.O = static_cast<float*>(O->ptr);
+    c.bias = E.bias;
+    c.relu = E.relu;
+    c.beta = E.accumulate ? 1.f : 0.f;
+    return tc_conv(c, P.sched, w + P.off_k, P.kern, st);
+  }
   if (precision != NK_PREC_F32 || I->dtype != NK_F32)
     return fail(NK_ERR_UNSUPPORTED, "conv precision %d / dtype %d not available", precision, I->dtype);
-  if (!o_dense(O)) return fail(NK_ERR_UNSUPPORTED, "O must be contiguous NHWC");
   SimtGemm p{};
   p.A = static_cast<const float*>(I->ptr);
   p.B = static_cast<const float*>(W->ptr);

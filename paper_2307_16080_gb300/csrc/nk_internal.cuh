@@ -129,6 +129,26 @@ struct TcGemm {
 
 nk_status tc_gemm(const TcGemm& g, const nk_schedule& s, void* ws, size_t ws_bytes,
                   cudaStream_t st);
+
+// Implicit-GEMM convolution on the tensor cores (BF16 operands).
+// I: NHWC BF16 with channel stride 1 and element strides sI_n, sI_h, sI_w
+// (16-byte multiples); Wt: BF16 [F][KH*KW][ldw] (K-major per filter tap);
+// O: FP32 [N*OH*OW, F] row-major.
+struct TcConv {
+  const void* I;
+  int64_t sI_n, sI_h, sI_w;
+  const void* Wt;
+  int64_t ldw;
+  ConvGeom g;
+  int F;
+  float* O;
+  const float* bias;
+  int relu;
+  float beta;
+};
+nk_status tc_conv(const TcConv& c, const nk_schedule& s, void* ws, size_t ws_bytes, cudaStream_t st);
+size_t tc_conv_ws(const TcConv& c, const nk_schedule& s);
+nk_schedule tc_conv_default_schedule(const ConvGeom& g, int F, int sms);
 size_t tc_gemm_ws(const TcGemm& g, const nk_schedule& s);
 // Fills unset fields of `s` with the built-in choice for this problem.
 nk_schedule tc_default_schedule(int kind, int M, int N, int K, int sms);

@@ -1,0 +1,97 @@
+"""GPU parity of the BF16 tensor-core implicit-GEMM convolution
+(linalg.conv_2d_nhwc_hwcf) against the FP64 oracle, through the C ABI."""
+import numpy as np
+import pytest
+import torch
+
+import oracle.nk_oracle as O
+from paper_2307_16080_gb300 import synth
+from tests.gpu_util import DEV, dev, host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nk():
+    import paper_2307_16080_gb300.nk as m
+    m.lib()
+    return m
+
+
+def _conv(nk, I, W, st, dl, pad, **kw):
+    N, H, Wd, C = I.shape
+    KH, KW, _, F = W.shape
+    OH = O.conv_out_size(H, KH, st[0], dl[0], pad[0], pad[1])
+    OW = O.conv_out_size(Wd, KW, st[1], dl[1], pad[2], pad[3])
+    out = torch.empty(N, OH, OW, F, device=DEV)
+    i = kw.pop("i_dev", None)
+    nk.nk_conv2d_nhwc_hwcf(dev(I) if i is None else i, dev(W), out, stride=st, dilation=dl, pad=pad,
+                           precision="bf16", **kw)
+    nk.nk_sync_status()
+    return host(out)
+
+
+def test_bf16_conv_resnet_block(nk):
+    I, W, bias = synth.conv_resnet_block()
+    got = _conv(nk, I, W, (1, 1), (1, 1), (1, 1, 1, 1), bias=dev(bias), relu=True)
+    R16 = O.epilogue(O.conv2d_nhwc_hwcf(O.bf16_rn(I), O.bf16_rn(W), pad=(1, 1, 1, 1)), bias=bias, relu=True)
+    R32 = O.epilogue(O.conv2d_nhwc_hwcf(I, W, pad=(1, 1, 1, 1)), bias=bias, relu=True)
+    assert O.rel_frobenius(got, R16) <= 1e-5
+    assert O.rel_frobenius(got, R32) <= 8e-3
+
+
+CASES = [
+    # N, H, W, C, F, KH, KW, stride, dilation, pad
+    (1, 8, 8, 64, 64, 3, 3, (1, 1), (1, 1), (1, 1, 1, 1)),
+    (2, 13, 11, 16, 24, 3, 3, (2, 1), (1, 2), (1, 0, 2, 1)),
+    (1, 12, 12, 5, 7, 3, 3, (1, 1), (1, 1), (0, 0, 0, 0)),      # C not a multiple of 8
+    (2, 9, 9, 200, 72, 3, 3, (2, 2), (1, 1), (1, 1, 1, 1)),     # partial channel block
+    (3, 7, 7, 128, 96, 1, 1, (1, 1), (1, 1), (0, 0, 0, 0)),     # several images per tile
+    (1, 20, 18, 32, 300, 5, 3, (1, 2), (2, 1), (2, 2, 1, 1)),
+    (4, 14, 14, 64, 128, 3, 3, (2, 2), (1, 1), (1, 1, 1, 1)),
+]
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_bf16_conv_small_ints_bitwise(nk, case):
+    N, H, Wd, C, F, KH, KW, st, dl, pad = case
+    I = synth.small_ints(81, H * 100 + C, (N, H, Wd, C))
+    W = synth.small_ints(81, F * 100 + KH, (KH, KW, C, F))
+    np.testing.assert_array_equal(_conv(nk, I, W, st, dl, pad), O.conv2d_nhwc_hwcf(I, W, st, dl, pad))
+
+
+@pytest.mark.parametrize("sched", [(128, 64, 64, 1, 4, 1), (128, 128, 64, 2, 3, 1), (128, 64, 64, 2, 5, 3),
+                                   (128, 256, 64, 1, 4, 2)])
+def test_bf16_conv_schedules_bitwise(nk, sched):
+    N, H, Wd, C, F, KH, KW = 2, 15, 17, 96, 160, 3, 3
+    I = synth.small_ints(82, 1, (N, H, Wd, C))
+    W = synth.small_ints(82, 2, (KH, KW, C, F))
+    got = _conv(nk, I, W, (1, 1), (1, 1), (1, 1, 1, 1), schedule=sched)
+    np.testing.assert_array_equal(got, O.conv2d_nhwc_hwcf(I, W, pad=(1, 1, 1, 1)))
+
+
+def test_bf16_conv_bf16_input_and_accumulate(nk):
+    N, H, Wd, C, F = 2, 10, 10, 64, 64
+    I = synth.normal(83, 0, (N, H, Wd, C))
+    W = synth.normal(83, 1, (3, 3, C, F), sigma=0.06)
+    C0 = synth.uniform(83, 2, (N, H, Wd, F))
+    out = dev(C0)
+    nk.nk_conv2d_nhwc_hwcf(dev(I).to(torch.bfloat16), dev(W), out, pad=(1, 1, 1, 1), precision="bf16",
+                           accumulate=True)
+    nk.nk_sync_status()
+    R = O.epilogue(O.conv2d_nhwc_hwcf(O.bf16_rn(I), O.bf16_rn(W), pad=(1, 1, 1, 1)), c_in=C0, beta=1.0)
+    assert O.rel_frobenius(host(out), R) <= 1e-5
+
+
+@pytest.mark.parametrize("batch", [1, 8])
+def test_bf16_resnet_stack_layers(nk, batch):
+    for li, L in enumerate(synth.resnet_stack(batch)):
+        if li % 3:      # a third of the layers keeps the oracle quick
+            continue
+        I = synth.half_normal(84, li, (L["N"], L["H"], L["W"], L["C"]))
+        W = synth.normal(84, 100 + li, (L["KH"], L["KW"], L["C"], L["F"]),
+                         sigma=float(np.sqrt(2.0 / (L["KH"] * L["KW"] * L["C"]))))
+        st, pad = (L["stride"],) * 2, (L["pad"],) * 4
+        got = _conv(nk, I, W, st, (1, 1), pad)
+        R = O.conv2d_nhwc_hwcf(O.bf16_rn(I), O.bf16_rn(W), st, (1, 1), pad)
+        assert O.rel_frobenius(got, R) <= 1e-5, (li, L)
