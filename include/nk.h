@@ -220,6 +220,29 @@ nk_status nk_rel_frobenius(const float* C, int64_t ldc, const double* R,
                            void* ws, size_t ws_bytes, void* stream);
 size_t nk_norm_workspace_size(int64_t M, int64_t N);
 
+/* ------------------------------------------------ split-K, no allocation */
+
+/* C = A @ B in FP32 on the CUDA cores with split-K, for callers that cannot
+ * allocate device memory (code running inside an allocator callback, under a
+ * runtime that owns the whole memory pool, or with no device memory budget
+ * left): the split_k partial sums live in a fixed 16 MiB array inside the
+ * library instead of a caller workspace.  The paper has no counterpart; this
+ * is a deployment convenience around the split-K path of nk_matmul.
+ * A: [M,K] row-major (row stride lda), B: [K,N] row-major (ldb), C: [M,N]
+ * row-major FP32 (ldc), all device pointers; split_k in [1, 32].
+ * Limit: split_k * M * N <= 4194304 floats, else NK_ERR_WORKSPACE (nothing is
+ * launched).  Allocates nothing: no cudaMalloc, no cudaFree.
+ * The array is shared by every call on a device and keeps the last call's
+ * partials; each call overwrites all it reads, so no clearing is needed, but
+ * calls whose kernels overlap on the same GPU (for example on two streams)
+ * race on it -- serialise them.
+ * The first call on each device looks up the array's device address with
+ * that device current; make that first call before any stream capture.   */
+nk_status nk_matmul_f32_splitk_noalloc(const float* A, int64_t lda,
+                                       const float* B, int64_t ldb, float* C,
+                                       int64_t ldc, int32_t M, int32_t N,
+                                       int32_t K, int32_t split_k, void* stream);
+
 /* ---------------------------------------------------------- diagnostics */
 
 /* Thread-local message describing the last non-OK status of this thread.  */

@@ -13,6 +13,8 @@
 // slices in a fixed order with a warp-shuffle tree, then applies the epilogue.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "nk_internal.cuh"
 
 namespace nk {
@@ -433,3 +435,67 @@ nk_status splitk_reduce(const SplitReduce& r, cudaStream_t st) {
 }
 
 }  // namespace nk
+
+// ------------------------------------------------- split-K without allocation
+// For callers that cannot allocate device memory at all: code running where
+// cudaMalloc is unavailable or forbidden (inside a custom allocator's
+// callbacks, while another runtime owns the memory pool, or in a process
+// whose device memory budget is already spoken for).  The split-K partial
+// sums go to this fixed, file-scope device array instead of a caller
+// workspace; every GPU that loads the library keeps it until exit.
+namespace nk {
+namespace {
+
+constexpr size_t kStaticScratchFloats = size_t(4) << 20;   // 16 MiB of FP32 partials
+__device__ __align__(256) float g_splitk_scratch[kStaticScratchFloats];
+
+std::mutex g_scratch_mu;
+float* g_scratch_addr[64];   // device address of g_splitk_scratch, per device
+
+}  // namespace
+}  // namespace nk
+
+extern "C" nk_status nk_matmul_f32_splitk_noalloc(const float* A, int64_t lda, const float* B,
+                                                  int64_t ldb, float* C, int64_t ldc, int32_t M,
+                                                  int32_t N, int32_t K, int32_t split_k,
+                                                  void* stream) {
+  using namespace nk;
+  nk_status s = require_device();
+  if (s != NK_OK) return s;
+  if (M < 0 || N < 0 || K < 0) return fail(NK_ERR_INVALID_ARG, "negative extent");
+  if (split_k < 1 || split_k > 32) return fail(NK_ERR_INVALID_ARG, "split_k must be in [1, 32]");
+  if (M == 0 || N == 0) return NK_OK;
+  if (!A || !B || !C) return fail(NK_ERR_INVALID_ARG, "null pointer");
+  if (lda < K || ldb < N || ldc < N) return fail(NK_ERR_INVALID_ARG, "leading dimension too small");
+  if ((size_t)split_k * (size_t)M * (size_t)N > kStaticScratchFloats)
+    return fail(NK_ERR_WORKSPACE,
+                "split_k*M*N = %zu exceeds the static scratch of %zu floats (16 MiB)",
+                (size_t)split_k * M * N, kStaticScratchFloats);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  float* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
+      // Host code only sees a host-side stand-in for the array; the device
+      // address comes from the runtime, once per device, with it current.
+      void* p = nullptr;
+      e = cudaGetSymbolAddress(&p, g_splitk_scratch);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_splitk_scratch)");
+      g_scratch_addr[dev] = static_cast<float*>(p);
+    }
+    scratch = g_scratch_addr[dev];
+  }
+  SimtGemm p{};
+  p.A = A; p.sam = lda; p.sak = 1;
+  p.B = B; p.sbk = ldb; p.sbn = 1;
+  p.C = C; p.scm = ldc; p.scn = 1;
+  p.M = M; p.N = N; p.K = K;
+  p.alpha = 1.f; p.beta = 0.f;
+  const int tile = (int64_t)((M + 127) / 128) * ((N + 127) / 128) < 152 ? 64 : 128;
+  // Every slice overwrites its whole [M,N] partial tile, so the scratch needs
+  // no clearing between calls.
+  return simt_gemm(p, tile, split_k, scratch, kStaticScratchFloats * sizeof(float),
+                   static_cast<cudaStream_t>(stream));
+}

@@ -80,6 +80,7 @@ SIGNATURES = {
     "nk_split_bf16x3": (_I32, [_P, _I64, _I64, _I64, _P, _P, _I64, _I32, _P]),
     "nk_rel_frobenius": (_I32, [_P, _I64, _P, _I64, _I64, _I64, _P, _P, _SZ, _P]),
     "nk_norm_workspace_size": (_SZ, [_I64, _I64]),
+    "nk_matmul_f32_splitk_noalloc": (_I32, [_P, _I64, _P, _I64, _P, _I64, _I32, _I32, _I32, _I32, _P]),
     "nk_last_error": (ctypes.c_char_p, []),
     "nk_sync_status": (_I32, [_P]),
     "nk_set_wait_budget": (_I32, [_I64]),
@@ -313,3 +314,13 @@ def nk_batch_matmul_grouped(groups, G, precision="bf16", schedule=None, ws=None,
                                          ws.data_ptr() if ws is not None else None,
                                          ws.numel() if ws is not None else 0, _stream(stream)))
     return ws
+
+
+def nk_matmul_f32_splitk_noalloc(A, B, C, split_k, stream=None):
+    """C = A @ B (FP32, row-major) with split-K partials in the library's static scratch."""
+    M, K = A.shape
+    N = B.shape[1]
+    _check(lib().nk_matmul_f32_splitk_noalloc(A.data_ptr(), A.stride(0), B.data_ptr(), B.stride(0),
+                                              C.data_ptr(), C.stride(0), M, N, K, int(split_k),
+                                              _stream(stream)))
+    return C
