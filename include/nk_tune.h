@@ -1,0 +1,102 @@
+/*
+ * nk_tune.h -- schedule search and the learned tile-cost model of libnk.
+ *
+ * The paper tunes its tiled loop nest by black-box search over tile sizes and
+ * unroll factors (Sec. 4.3, Figure "nevergrad": the tiling pass and an unroll
+ * op, parameterised, timed on the device, fed back to the optimiser).  Here
+ * the search space is the tensor-core schedule (tile_n, cluster, stages,
+ * split_k); candidates are timed on the GPU with CUDA events, and a small MLP
+ * (16 -> 128 -> 128 -> 1, GELU) trained on those timings ranks the candidates
+ * so only the top few need timing.
+ */
+#ifndef NK_TUNE_H
+#define NK_TUNE_H
+
+#include "nk.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { NK_OP_MATMUL = 0, NK_OP_CONV2D = 1 } nk_op;
+typedef enum { NK_TUNE_EXHAUSTIVE = 0, NK_TUNE_MODEL_TOPK = 1 } nk_tune_mode;
+
+/* A tensor-core problem: matmul (M, N, K) or conv (n, h, w, c -> f with a
+ * kh x kw filter, equal stride and padding on both axes, dilation 1).
+ * precision: NK_PREC_BF16 / NK_PREC_FP8 / NK_PREC_BF16X3 (matmul),
+ * NK_PREC_BF16 (conv).                                                     */
+typedef struct {
+  int32_t op;
+  int32_t precision;
+  int32_t M, N, K;
+  int32_t n, h, w, c, f, kh, kw, stride, pad;
+} nk_problem;
+
+typedef struct {
+  int32_t candidates; /* legal schedules enumerated                        */
+  int32_t timed;      /* schedules timed on the GPU                        */
+  float best_ms;      /* median time of the returned schedule              */
+  float default_ms;   /* median time of the built-in default schedule      */
+} nk_tune_report;
+
+/* Number of model features per (problem, schedule) pair.                   */
+#define NK_TUNE_FEATURES 16
+
+/* Legal schedules of a problem in a fixed order (the tie-break order of the
+ * search).  Writes at most `cap` to `out` (host) and the total to *count.  */
+nk_status nk_enumerate_schedules(const nk_problem* p, nk_schedule* out, int32_t cap,
+                                 int32_t* count);
+
+/* The built-in schedule (used when nk_matmul / nk_conv2d get sched = NULL). */
+nk_status nk_default_schedule(const nk_problem* p, nk_schedule* out);
+
+/* Model features of `count` schedules for one problem, host array
+ * [count][NK_TUNE_FEATURES]: log2 M, N, K; is_conv; taps; stride; precision
+ * one-hot (BF16, FP8, BF16x3); log2 tile_m, tile_n, tile_k; cluster; stages;
+ * log2 split_k; log2(work units / SMs) -- each scaled to about [0, 1].     */
+nk_status nk_schedule_features(const nk_problem* p, const nk_schedule* s, int32_t count,
+                               float* features);
+
+/* Median over `reps` timed launches (after two warm-ups) of one schedule on
+ * synthetic operands of the problem's shape, in milliseconds.  Synchronises
+ * `stream`; allocates and keeps library-owned scratch operands (grown on
+ * demand, released by nk_tune_release).                                    */
+nk_status nk_time_schedule(const nk_problem* p, const nk_schedule* s, int32_t reps,
+                           float* median_ms, void* stream);
+nk_status nk_tune_release(void);
+
+/* Pick a schedule.  EXHAUSTIVE times every legal candidate; MODEL_TOPK runs
+ * the cost model (`mlp_params`: device FP32 parameters, see nk_mlp_*) over
+ * all candidates on the GPU and times only the `topk` best-predicted ones.
+ * Ties in median time go to the earlier candidate.  `rep` may be NULL.      */
+nk_status nk_tune(const nk_problem* p, int32_t mode, int32_t topk, const float* mlp_params,
+                  int32_t reps, nk_schedule* best, nk_tune_report* rep, void* stream);
+
+/* ------------------------------------------------------- the cost model */
+/* Parameters: one FP32 device buffer of nk_mlp_param_count() values laid out
+ * W1 [128][16], b1 [128], W2 [128][128], b2 [128], W3 [128], b3 [1].
+ * y = W3 g(W2 g(W1 x + b1) + b2) + b3, g(z) = z Phi(z) (exact GELU).       */
+size_t nk_mlp_param_count(void);
+
+/* y[i] for the B rows of X [B][16] (device).                                 */
+nk_status nk_mlp_forward(const float* params, const float* X, int64_t B, float* y,
+                         void* stream);
+
+/* Gradient of L = mean_i (y_i - t_i)^2 with respect to every parameter into
+ * grad (device, nk_mlp_param_count() floats) and L into *loss (device, may be
+ * NULL).  Per-block partial sums are added in a fixed order, so the result is
+ * identical run to run.  Needs nk_mlp_workspace_size(B) bytes.             */
+size_t nk_mlp_workspace_size(int64_t B);
+nk_status nk_mlp_grad(const float* params, const float* X, const float* t, int64_t B,
+                      float* grad, float* loss, void* ws, size_t ws_bytes, void* stream);
+
+/* One Adam step (Kingma & Ba 2015, Algorithm 1) at step t >= 1 on all
+ * parameters: m, v are device moment buffers of the same length.            */
+nk_status nk_mlp_adam(float* params, const float* grad, float* m, float* v, int32_t t,
+                      float lr, float beta1, float beta2, float eps, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NK_TUNE_H */

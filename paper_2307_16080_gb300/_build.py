@@ -13,7 +13,7 @@ CSRC = os.path.join(PKG, "csrc")
 ROOT = os.path.dirname(PKG)
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libnk.so")
-SOURCES = ["nk_api.cu", "k_simt.cu", "k_prep.cu", "k_tc_gemm.cu"]
+SOURCES = ["nk_api.cu", "k_simt.cu", "k_prep.cu", "k_tc_gemm.cu", "k_mlp.cu", "tune.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]
@@ -31,7 +31,7 @@ def _stale(obj: str, src: str) -> bool:
         return True
     t = os.path.getmtime(obj)
     deps = [src] + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")]
-    deps.append(os.path.join(ROOT, "include", "nk.h"))
+    deps += [os.path.join(ROOT, "include", h) for h in ("nk.h", "nk_tune.h")]
     return any(os.path.getmtime(d) > t for d in deps)
 
 

@@ -1,0 +1,372 @@
+// tune.cu -- schedule search for the tensor-core kernels.
+//
+// The paper searches tile sizes and unroll factors of its loop nest with a
+// black-box optimiser that compiles, runs and times each point (Sec. 4.3).
+// Here the points are tensor-core schedules (tile_n, cluster, stages,
+// split_k): they are enumerated in a fixed order, timed on the GPU with
+// CUDA events on synthetic operands of the problem's shape, and -- in model
+// mode -- first ranked by the learned cost model (k_mlp.cu) so only the top
+// few are timed.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <mutex>
+#include <vector>
+
+#include "../../include/nk_tune.h"
+#include "nk_internal.cuh"
+
+namespace nk {
+namespace {
+
+std::mutex g_mu;
+void* g_scratch = nullptr;
+size_t g_scratch_bytes = 0;
+size_t g_filled = 0;
+
+// Deterministic operand bits: BF16 values in [-1, 1); E4M3 codes without NaN.
+__global__ void fill_kernel(uint16_t* p, size_t n16) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += (size_t)gridDim.x * blockDim.x) {
+    uint32_t h = (uint32_t)(i * 2654435761u) ^ (uint32_t)(i >> 29);
+    h ^= h >> 15;
+    h *= 0x2c1b3c6du;
+    h ^= h >> 12;
+    const float f = (float)(h & 0xFFFF) / 32768.f - 1.f;
+    __nv_bfloat16 b = __float2bfloat16_rn(f);
+    p[i] = *reinterpret_cast<uint16_t*>(&b) & 0xF7F7u;  // as E4M3 pairs: exponent <= 14, no NaN
+  }
+}
+
+nk_status scratch(size_t bytes, void** out) {
+  if (bytes > g_scratch_bytes) {
+    if (g_scratch) cudaFree(g_scratch);
+    g_scratch = nullptr;
+    g_scratch_bytes = 0;
+    g_filled = 0;
+    cudaError_t e = cudaMalloc(&g_scratch, bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(tune scratch)");
+    g_scratch_bytes = bytes;
+  }
+  *out = g_scratch;
+  return NK_OK;
+}
+
+nk_status fill(size_t bytes) {
+  if (bytes <= g_filled) return NK_OK;
+  fill_kernel<<<1024, 256>>>(static_cast<uint16_t*>(g_scratch), bytes / 2);
+  nk_status s = check_launch("fill_kernel");
+  if (s == NK_OK) g_filled = bytes;
+  return s;
+}
+
+int kind_of(int prec) {
+  return prec == NK_PREC_FP8 ? TC_FP8 : prec == NK_PREC_BF16X3 ? TC_BF16X3 : TC_BF16;
+}
+
+nk_status check_problem(const nk_problem* p) {
+  if (!p) return fail(NK_ERR_INVALID_ARG, "problem is NULL");
+  if (p->op == NK_OP_MATMUL) {
+    if (p->M < 1 || p->N < 1 || p->K < 1) return fail(NK_ERR_INVALID_ARG, "matmul extents must be positive");
+    if (p->precision != NK_PREC_BF16 && p->precision != NK_PREC_FP8 && p->precision != NK_PREC_BF16X3)
+      return fail(NK_ERR_UNSUPPORTED, "tuning covers the tensor-core precisions");
+    return NK_OK;
+  }
+  if (p->op == NK_OP_CONV2D) {
+    if (p->n < 1 || p->h < 1 || p->w < 1 || p->c < 1 || p->f < 1 || p->kh < 1 || p->kw < 1 || p->stride < 1 ||
+        p->pad < 0)
+      return fail(NK_ERR_INVALID_ARG, "conv extents must be positive");
+    if (p->precision != NK_PREC_BF16) return fail(NK_ERR_UNSUPPORTED, "conv tuning covers BF16");
+    if ((p->h + 2 * p->pad - p->kh) / p->stride + 1 < 1 || (p->w + 2 * p->pad - p->kw) / p->stride + 1 < 1)
+      return fail(NK_ERR_INVALID_ARG, "empty conv output");
+    return NK_OK;
+  }
+  return fail(NK_ERR_INVALID_ARG, "unknown op %d", p->op);
+}
+
+ConvGeom geom_of(const nk_problem* p) {
+  ConvGeom g{};
+  g.n = p->n; g.h = p->h; g.w = p->w; g.c = p->c;
+  g.kh = p->kh; g.kw = p->kw;
+  g.sh = g.sw = p->stride;
+  g.dh = g.dw = 1;
+  g.pt = g.pl = p->pad;
+  g.oh = (p->h + 2 * p->pad - p->kh) / p->stride + 1;
+  g.ow = (p->w + 2 * p->pad - p->kw) / p->stride + 1;
+  const int cp = (p->c + 7) / 8 * 8;
+  g.sin_w = cp; g.sin_h = (int64_t)p->w * cp; g.sin_n = (int64_t)p->h * p->w * cp;
+  return g;
+}
+
+// GEMM view (M, N, K) of a problem.
+void gemm_view(const nk_problem* p, int64_t& M, int64_t& N, int64_t& K) {
+  if (p->op == NK_OP_MATMUL) { M = p->M; N = p->N; K = p->K; return; }
+  const ConvGeom g = geom_of(p);
+  M = (int64_t)g.n * g.oh * g.ow; N = p->f; K = (int64_t)g.kh * g.kw * g.c;
+}
+
+std::vector<nk_schedule> enumerate(const nk_problem* p) {
+  std::vector<nk_schedule> out;
+  const int kind = kind_of(p->precision);
+  int64_t M, N, K;
+  gemm_view(p, M, N, K);
+  const int tk = kind == TC_FP8 ? 128 : 64;
+  const int64_t nkb = p->op == NK_OP_CONV2D ? (int64_t)p->kh * p->kw * ((p->c + 63) / 64) : (K + tk - 1) / tk;
+  for (int tn : {64, 128, 256})
+    for (int cl : {1, 2})
+      for (int split : {1, 2, 4, 8, 16})
+        for (int st = 2; st <= 8; ++st) {
+          nk_schedule s{128, tn, tk, cl, st, split};
+          if (split > nkb) continue;
+          if (!tc_schedule_valid(kind, s, (int)M, (int)N, (int)K)) continue;
+          out.push_back(s);
+        }
+  return out;
+}
+
+nk_schedule default_of(const nk_problem* p, int sms) {
+  if (p->op == NK_OP_CONV2D) return tc_conv_default_schedule(geom_of(p), p->f, sms);
+  return tc_default_schedule(kind_of(p->precision), p->M, p->N, p->K, sms);
+}
+
+void features(const nk_problem* p, const nk_schedule& s, int sms, float* f) {
+  int64_t M, N, K;
+  gemm_view(p, M, N, K);
+  const int kind = kind_of(p->precision);
+  const int64_t tiles = ((M + 127) / 128) * ((N + s.tile_n - 1) / s.tile_n);
+  f[0] = (float)(std::log2((double)M) / 16.0);
+  f[1] = (float)(std::log2((double)N) / 16.0);
+  f[2] = (float)(std::log2((double)K) / 16.0);
+  f[3] = p->op == NK_OP_CONV2D ? 1.f : 0.f;
+  f[4] = p->op == NK_OP_CONV2D ? (float)(p->kh * p->kw) / 9.f : 0.f;
+  f[5] = p->op == NK_OP_CONV2D ? (float)p->stride / 2.f : 0.f;
+  f[6] = kind == TC_BF16 ? 1.f : 0.f;
+  f[7] = kind == TC_FP8 ? 1.f : 0.f;
+  f[8] = kind == TC_BF16X3 ? 1.f : 0.f;
+  f[9] = (float)(std::log2((double)s.tile_m) / 8.0);
+  f[10] = (float)(std::log2((double)s.tile_n) / 8.0);
+  f[11] = (float)(std::log2((double)s.tile_k) / 8.0);
+  f[12] = (float)s.cluster / 2.f;
+  f[13] = (float)s.stages / 8.f;
+  f[14] = (float)(std::log2((double)s.split_k) / 4.0);
+  f[15] = (float)(std::log2((double)(tiles * s.split_k) / (double)sms) / 4.0);
+}
+
+int sm_count() {
+  int sms = 152, dev = 0, v = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+      v > 0)
+    sms = v;
+  return sms;
+}
+
+// Launches one schedule on the scratch operands.
+struct Runner {
+  const nk_problem* p;
+  char* base = nullptr;
+  size_t op_bytes = 0, total = 0;
+  TcGemm g{};
+  TcConv c{};
+
+  explicit Runner(const nk_problem* pp, const nk_schedule& s) : p(pp) {
+    int64_t M, N, K;
+    gemm_view(p, M, N, K);
+    const size_t split_bytes = s.split_k > 1 ? (size_t)s.split_k * M * N * 4 : 0;
+    if (p->op == NK_OP_MATMUL) {
+      const int kind = kind_of(p->precision);
+      const int esz = kind == TC_FP8 ? 1 : 2;
+      const int64_t ld = (K + 15) / 16 * 16;
+      const size_t a = (size_t)M * ld * esz, b = (size_t)N * ld * esz;
+      const size_t parts = kind == TC_BF16X3 ? 2 : 1;
+      op_bytes = parts * (a + b);
+      total = op_bytes + (size_t)M * N * 4 + split_bytes + 4096;
+      g.kind = kind; g.M = (int)M; g.N = (int)N; g.K = (int)K;
+      g.lda = ld; g.ldb = ld; g.ldc = N; g.alpha = 1.f;
+    } else {
+      const ConvGeom geo = geom_of(p);
+      const int64_t cp = (p->c + 7) / 8 * 8;
+      const size_t ib = (size_t)p->n * p->h * p->w * cp * 2;
+      const size_t wb = (size_t)p->f * p->kh * p->kw * cp * 2;
+      op_bytes = ib + wb;
+      total = op_bytes + (size_t)M * N * 4 + split_bytes + 4096;
+      c.g = geo; c.F = p->f; c.ldw = cp;
+      c.sI_w = geo.sin_w; c.sI_h = geo.sin_h; c.sI_n = geo.sin_n;
+    }
+  }
+  void bind(char* b) {
+    base = b;
+    auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+    if (p->op == NK_OP_MATMUL) {
+      const int esz = g.kind == TC_FP8 ? 1 : 2;
+      const size_t a = al((size_t)g.M * g.lda * esz), bb = al((size_t)g.N * g.ldb * esz);
+      g.A = b; g.B = b + a;
+      if (g.kind == TC_BF16X3) { g.A2 = b + a + bb; g.B2 = b + 2 * a + bb; }
+      g.C = reinterpret_cast<float*>(b + (g.kind == TC_BF16X3 ? 2 : 1) * (a + bb));
+    } else {
+      const size_t ib = al((size_t)p->n * p->h * p->w * c.ldw * 2);
+      c.I = b;
+      c.Wt = b + ib;
+      c.O = reinterpret_cast<float*>(b + ib + al((size_t)p->f * p->kh * p->kw * c.ldw * 2));
+    }
+  }
+  size_t padded_total() const { return total + 4 * 256; }
+  char* ws(int64_t M, int64_t N) const {
+    (void)M; (void)N;
+    const float* o = p->op == NK_OP_MATMUL ? g.C : c.O;
+    int64_t MM, NN, KK;
+    gemm_view(p, MM, NN, KK);
+    return reinterpret_cast<char*>(const_cast<float*>(o)) + (((size_t)MM * NN * 4 + 255) / 256 * 256);
+  }
+  nk_status run(const nk_schedule& s, cudaStream_t st) {
+    int64_t M, N, K;
+    gemm_view(p, M, N, K);
+    const size_t wsb = s.split_k > 1 ? (size_t)s.split_k * M * N * 4 : 0;
+    if (p->op == NK_OP_MATMUL) return tc_gemm(g, s, ws(M, N), wsb, st);
+    return tc_conv(c, s, ws(M, N), wsb, st);
+  }
+};
+
+nk_status time_one(const nk_problem* p, const nk_schedule& s, int reps, float* ms, cudaStream_t st) {
+  Runner r(p, s);
+  void* buf = nullptr;
+  nk_status status = scratch(r.padded_total(), &buf);
+  if (status != NK_OK) return status;
+  r.bind(static_cast<char*>(buf));
+  if ((status = fill(r.op_bytes + 1024)) != NK_OK) return status;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+  for (int i = 0; i < 2; ++i)
+    if ((status = r.run(s, st)) != NK_OK) return status;
+  reps = reps < 1 ? 1 : reps;
+  std::vector<cudaEvent_t> ev(2 * reps);
+  for (auto& x : ev) cudaEventCreate(&x);
+  for (int i = 0; i < reps && status == NK_OK; ++i) {
+    cudaEventRecord(ev[2 * i], st);
+    status = r.run(s, st);
+    cudaEventRecord(ev[2 * i + 1], st);
+  }
+  e = cudaStreamSynchronize(st);
+  std::vector<float> t(reps, 0.f);
+  for (int i = 0; i < reps; ++i) cudaEventElapsedTime(&t[i], ev[2 * i], ev[2 * i + 1]);
+  for (auto& x : ev) cudaEventDestroy(x);
+  if (status != NK_OK) return status;
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize(tune)");
+  uint32_t flags = tc_read_and_clear_errors();
+  if (flags & kErrTimeout) return fail(NK_ERR_TIMEOUT, "a bounded device wait expired while timing");
+  std::sort(t.begin(), t.end());
+  *ms = t[reps / 2];
+  return NK_OK;
+}
+
+}  // namespace
+}  // namespace nk
+
+using namespace nk;
+
+extern "C" {
+
+nk_status nk_enumerate_schedules(const nk_problem* p, nk_schedule* out, int32_t cap, int32_t* count) {
+  nk_status s = check_problem(p);
+  if (s != NK_OK) return s;
+  if (!count) return fail(NK_ERR_INVALID_ARG, "count is NULL");
+  const auto v = enumerate(p);
+  *count = (int32_t)v.size();
+  for (int i = 0; i < (int)v.size() && i < cap && out; ++i) out[i] = v[i];
+  return NK_OK;
+}
+
+nk_status nk_default_schedule(const nk_problem* p, nk_schedule* out) {
+  nk_status s = check_problem(p);
+  if (s != NK_OK) return s;
+  if (!out) return fail(NK_ERR_INVALID_ARG, "out is NULL");
+  *out = default_of(p, sm_count());
+  return NK_OK;
+}
+
+nk_status nk_schedule_features(const nk_problem* p, const nk_schedule* s, int32_t count, float* f) {
+  nk_status st = check_problem(p);
+  if (st != NK_OK) return st;
+  if (count < 0 || (count > 0 && (!s || !f))) return fail(NK_ERR_INVALID_ARG, "bad feature arguments");
+  const int sms = sm_count();
+  for (int i = 0; i < count; ++i) features(p, s[i], sms, f + (size_t)i * NK_TUNE_FEATURES);
+  return NK_OK;
+}
+
+nk_status nk_time_schedule(const nk_problem* p, const nk_schedule* s, int32_t reps, float* median_ms,
+                           void* stream) {
+  nk_status st = check_problem(p);
+  if (st != NK_OK) return st;
+  if ((st = require_device()) != NK_OK) return st;
+  if (!s || !median_ms) return fail(NK_ERR_INVALID_ARG, "null pointer");
+  std::lock_guard<std::mutex> lk(g_mu);
+  return time_one(p, *s, reps, median_ms, static_cast<cudaStream_t>(stream));
+}
+
+nk_status nk_tune_release(void) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (g_scratch) cudaFree(g_scratch);
+  g_scratch = nullptr;
+  g_scratch_bytes = 0;
+  g_filled = 0;
+  return NK_OK;
+}
+
+nk_status nk_tune(const nk_problem* p, int32_t mode, int32_t topk, const float* mlp_params, int32_t reps,
+                  nk_schedule* best, nk_tune_report* rep, void* stream) {
+  nk_status st = check_problem(p);
+  if (st != NK_OK) return st;
+  if ((st = require_device()) != NK_OK) return st;
+  if (!best) return fail(NK_ERR_INVALID_ARG, "best is NULL");
+  if (mode != NK_TUNE_EXHAUSTIVE && mode != NK_TUNE_MODEL_TOPK) return fail(NK_ERR_INVALID_ARG, "unknown mode");
+  if (mode == NK_TUNE_MODEL_TOPK && (!mlp_params || topk < 1))
+    return fail(NK_ERR_INVALID_ARG, "model mode needs parameters and topk >= 1");
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  const auto cand = enumerate(p);
+  if (cand.empty()) return fail(NK_ERR_NO_SCHEDULE, "no legal schedule");
+  std::vector<int> order(cand.size());
+  for (size_t i = 0; i < cand.size(); ++i) order[i] = (int)i;
+  if (mode == NK_TUNE_MODEL_TOPK) {
+    const int sms = sm_count();
+    std::vector<float> feat(cand.size() * NK_TUNE_FEATURES);
+    for (size_t i = 0; i < cand.size(); ++i) features(p, cand[i], sms, feat.data() + i * NK_TUNE_FEATURES);
+    float* dX = nullptr;
+    cudaError_t e = cudaMalloc(&dX, feat.size() * 4 + cand.size() * 4);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(tune features)");
+    float* dy = dX + feat.size();
+    std::vector<float> pred(cand.size());
+    e = cudaMemcpyAsync(dX, feat.data(), feat.size() * 4, cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) st = nk_mlp_forward(mlp_params, dX, (int64_t)cand.size(), dy, stream);
+    if (e == cudaSuccess && st == NK_OK) e = cudaMemcpyAsync(pred.data(), dy, pred.size() * 4, cudaMemcpyDeviceToHost, cs);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+    cudaFree(dX);
+    if (st != NK_OK) return st;
+    if (e != cudaSuccess) return cuda_fail(e, "cost-model inference");
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return pred[a] < pred[b]; });
+    if ((int)order.size() > topk) order.resize(topk);
+    std::sort(order.begin(), order.end());   // time in enumeration order: same tie-break as exhaustive
+  }
+  std::lock_guard<std::mutex> lk(g_mu);
+  float best_ms = INFINITY;
+  int best_i = -1;
+  for (int i : order) {
+    float ms = 0.f;
+    st = time_one(p, cand[i], reps, &ms, cs);
+    if (st != NK_OK) return st;
+    if (ms < best_ms) { best_ms = ms; best_i = i; }
+  }
+  *best = cand[best_i];
+  if (rep) {
+    rep->candidates = (int32_t)cand.size();
+    rep->timed = (int32_t)order.size();
+    rep->best_ms = best_ms;
+    float dms = 0.f;
+    const nk_schedule d = default_of(p, sm_count());
+    st = time_one(p, d, reps, &dms, cs);
+    if (st != NK_OK) return st;
+    rep->default_ms = dms;
+  }
+  return NK_OK;
+}
+
+}  // extern "C"

@@ -42,11 +42,13 @@ def test_library_exports_every_declared_symbol(libpath):
 
 def test_ctypes_binding_loads_and_covers_header(libpath):
     import paper_2307_16080_gb300.nk as nk
-    L = nk.lib()
+    import paper_2307_16080_gb300.nk_tune as nt
+    L = nt.lib()
     for name in _declared():
         assert hasattr(L, name), name
-        assert name in nk.SIGNATURES, name
+        assert name in nk.SIGNATURES or name in nt.SIGNATURES, name
     assert nk.last_error() == ""
+    assert nt.nk_mlp_param_count() == 18817
 
 
 def test_no_device_means_error_not_fallback(libpath):

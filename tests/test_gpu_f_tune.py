@@ -1,0 +1,135 @@
+"""GPU checks of the cost-model kernels against the FP64 oracle, and of the
+schedule search (enumeration, timing, exhaustive and model-ranked tuning)."""
+import math
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle.nk_oracle as O
+from paper_2307_16080_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nt():
+    import paper_2307_16080_gb300.nk_tune as m
+    m.lib()
+    return m
+
+
+def _split(flat):
+    shapes = O.mlp_param_shapes()
+    out, o = {}, 0
+    for name in O.MLP_PARAM_NAMES:
+        n = int(np.prod(shapes[name]))
+        out[name] = flat[o:o + n].astype(np.float64).reshape(shapes[name])
+        o += n
+    return out
+
+
+def _join(p):
+    return np.concatenate([p[k].reshape(-1) for k in O.MLP_PARAM_NAMES]).astype(np.float32)
+
+
+def _params(seed):
+    from paper_2307_16080_gb300.costmodel import init_params
+    flat = init_params(seed)
+    flat[2048:2176] = synth.normal(seed, 20, (128,), sigma=0.1)     # nonzero biases
+    flat[18560:18688] = synth.normal(seed, 21, (128,), sigma=0.1)
+    flat[18816] = 0.3
+    return flat
+
+
+@pytest.mark.parametrize("B", [1, 37, 256])
+def test_mlp_forward_and_grad_vs_oracle(nt, B):
+    flat = _params(3)
+    X = synth.normal(30, B, (B, 16))
+    t = synth.normal(31, B, (B,))
+    P = torch.from_numpy(flat).cuda()
+    y = nt.nk_mlp_forward(P, torch.from_numpy(X).cuda())
+    g = torch.empty_like(P)
+    loss = torch.empty(1, device="cuda")
+    nt.nk_mlp_grad(P, torch.from_numpy(X).cuda(), torch.from_numpy(t).cuda(), g, loss)
+    torch.cuda.synchronize()
+    p64 = _split(flat)
+    yr, cache = O.mlp_forward(p64, X)
+    assert O.rel_frobenius(y.cpu().numpy(), yr) <= 1e-5
+    gr = O.mlp_backward(p64, cache, yr, t)
+    got = _split(g.cpu().numpy())
+    for k in O.MLP_PARAM_NAMES:
+        assert O.rel_frobenius(got[k], gr[k]) <= 1e-4, k
+    assert abs(loss.item() - O.mse_loss(yr, t)) <= 1e-5 * max(1.0, O.mse_loss(yr, t))
+    g2 = torch.empty_like(P)
+    nt.nk_mlp_grad(P, torch.from_numpy(X).cuda(), torch.from_numpy(t).cuda(), g2)
+    torch.cuda.synchronize()
+    assert torch.equal(g, g2)      # fixed-order reduction
+
+
+def test_adam_vs_oracle(nt):
+    flat = _params(4)
+    g = synth.normal(40, 0, flat.shape).astype(np.float32)
+    P = torch.from_numpy(flat).cuda()
+    m = torch.zeros_like(P)
+    v = torch.zeros_like(P)
+    gd = torch.from_numpy(g).cuda()
+    cur = {k: x for k, x in _split(flat).items()}
+    mo = {k: np.zeros_like(x) for k, x in cur.items()}
+    vo = {k: np.zeros_like(x) for k, x in cur.items()}
+    for step in (1, 2, 3):
+        nt.nk_mlp_adam(P, gd, m, v, step, lr=1e-2)
+        cur, mo, vo = O.adam_step(cur, _split(g), mo, vo, step, lr=1e-2)
+    torch.cuda.synchronize()
+    assert O.rel_frobenius(P.cpu().numpy(), _join(cur)) <= 1e-5
+
+
+def test_gpu_training_fits_linear_target(nt):
+    from paper_2307_16080_gb300.costmodel import train
+    X = synth.uniform(50, 0, (4096, 16), 0, 1)
+    w = synth.normal(50, 1, (16,))
+    y = X.astype(np.float64) @ w * 0.5 + 1.0
+    P, ym, ys, hist = train(X, y, epochs=60, batch=512, lr=3e-3)
+    assert hist[-1] < 0.05 * hist[0]
+
+
+def test_enumerate_features_and_default(nt):
+    p = nt.matmul_problem(1000, 700, 3000, "bf16")
+    cands = nt.nk_enumerate_schedules(p)
+    assert len(cands) > 50
+    assert nt.nk_default_schedule(p) in cands
+    F = nt.nk_schedule_features(p, cands)
+    assert F.shape == (len(cands), 16) and np.all(np.isfinite(F))
+    c = nt.conv_problem(8, 56, 56, 64, 64, 3, 3, 1, 1)
+    assert len(nt.nk_enumerate_schedules(c)) > 20
+
+
+def test_exhaustive_tune_picks_its_fastest_and_runs_correctly(nt):
+    import paper_2307_16080_gb300.nk as nk
+    M, N, K = 768, 1024, 2048
+    p = nt.matmul_problem(M, N, K, "bf16")
+    best, rep = nt.nk_tune(p, nt.NK_TUNE_EXHAUSTIVE, reps=3)
+    assert rep.timed == rep.candidates and rep.best_ms > 0
+    assert rep.best_ms <= rep.default_ms * 1.15
+    A, B = synth.matmul_uniform(M, N, K, seed=51)
+    c = torch.empty(M, N, device="cuda")
+    nk.nk_matmul(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), c, precision="bf16", schedule=best)
+    nk.nk_sync_status()
+    assert O.rel_frobenius(c.cpu().numpy(), O.matmul_precision(A, B, "bf16")) <= 1e-5
+
+
+def test_model_topk_tune_on_heldout_layers(nt):
+    from paper_2307_16080_gb300 import costmodel
+    if not os.path.exists(costmodel.MODEL_PATH):
+        pytest.skip("no trained cost model shipped")
+    params, _, _ = costmodel.load_model()
+    P = torch.from_numpy(params).cuda()
+    regrets = []
+    for L in synth.resnet_stack(8)[::5]:
+        p = nt.conv_problem(L["N"], L["H"], L["W"], L["C"], L["F"], L["KH"], L["KW"], L["stride"], L["pad"])
+        _, ex = nt.nk_tune(p, nt.NK_TUNE_EXHAUSTIVE, reps=5)
+        _, mo = nt.nk_tune(p, nt.NK_TUNE_MODEL_TOPK, topk=5, params=P, reps=5)
+        assert mo.timed == 5 and mo.candidates == ex.candidates
+        regrets.append(mo.best_ms / ex.best_ms - 1)
+    assert np.mean(regrets) <= 0.15, regrets
