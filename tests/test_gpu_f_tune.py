@@ -133,3 +133,20 @@ def test_model_topk_tune_on_heldout_layers(nt):
         assert mo.timed == 5 and mo.candidates == ex.candidates
         regrets.append(mo.best_ms / ex.best_ms - 1)
     assert np.mean(regrets) <= 0.15, regrets
+
+
+def test_shipped_model_regret_on_stored_heldout(nt):
+    """The shipped cost model, run by the library's forward kernel over the
+    stored held-out ResNet-stack measurements: its top-5 pick must be within
+    5% of the exhaustive optimum over the stack, and beat random-5 and the
+    built-in default."""
+    from paper_2307_16080_gb300 import costmodel
+    path = os.path.join(costmodel.MODEL_DIR, "corpus_heldout.npz")
+    if not os.path.exists(costmodel.MODEL_PATH) or not os.path.exists(path):
+        pytest.skip("no trained cost model shipped")
+    params, _, _ = costmodel.load_model()
+    c = costmodel.load_corpus(path)
+    s = costmodel.summarise(costmodel.regrets(c, costmodel.predict(params, c["X"]), k=5))
+    assert s["stack_model_regret"] <= 0.05, s
+    assert s["mean_model_regret"] < s["mean_random_regret"], s
+    assert s["mean_model_regret"] < s["mean_default_regret"], s
