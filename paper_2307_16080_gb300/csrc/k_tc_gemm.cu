@@ -190,14 +190,19 @@ __device__ __forceinline__ int conv_row(const ConvTile& c, int tm, int r) {
   return (n * c.OH + oh) * c.OW + ow;
 }
 
-template <int KIND, int CL, bool GROUPED, bool CONV = false>
+// PAIR: the two CTAs of a cluster form one 2-SM MMA (cta_group::2) computing a
+// 256 x BN tile; each holds its 128 rows of A and BN/2 rows of B^T, and the
+// even CTA's barriers gate the pair (its MMA thread is the only issuer).
+template <int KIND, int CL, bool GROUPED, bool CONV = false, bool PAIR = false>
 __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_constant__ TcParams p) {
+  static_assert(!PAIR || CL == 2, "a CTA pair is a cluster of two");
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = ptx::smem_u32(smem_raw);
   const uint32_t base = (raw + 1023) & ~1023u;
   uint8_t* base_ptr = smem_raw + (base - raw);
 
-  const int sb = stage_bytes(KIND, p.bn);
+  const int b_rows_smem = PAIR ? p.bn / 2 : p.bn;   // rows of B^T this CTA keeps per stage
+  const int sb = stage_bytes(KIND, b_rows_smem);
   const int S = p.stages;
   const uint32_t bar0 = base + S * sb;   // full[S], empty[S], tfull[2], tempty[2], drain
   auto full_bar = [&](int s) { return bar0 + 8u * s; };
@@ -222,11 +227,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       ptx::mbar_init(full_bar(s), 1);
-      ptx::mbar_init(empty_bar(s), CL);
+      ptx::mbar_init(empty_bar(s), PAIR ? 1 : CL);
     }
     for (int b = 0; b < 2; ++b) {
       ptx::mbar_init(tfull_bar(b), 1);
-      ptx::mbar_init(tempty_bar(b), 4);
+      ptx::mbar_init(tempty_bar(b), PAIR ? 8 : 4);   // a pair: both CTAs' epilogue warps
     }
     ptx::mbar_init(drain_bar, 1);
     *abort_flag = 0;
@@ -241,8 +246,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     }
   }
   if (warp == 1) {
-    ptx::tmem_alloc(ptx::smem_u32(tmem_slot), tmem_cols);
-    ptx::tmem_relinquish();
+    if (PAIR) {
+      ptx::tmem_alloc_pair(ptx::smem_u32(tmem_slot), tmem_cols);
+      ptx::tmem_relinquish_pair();
+    } else {
+      ptx::tmem_alloc(ptx::smem_u32(tmem_slot), tmem_cols);
+      ptx::tmem_relinquish();
+    }
   }
   ptx::tc_fence_before();
   __syncthreads();
@@ -251,7 +261,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
   const uint32_t tmem_base = *tmem_slot;
 
   const int a_bytes = kBM * kRowBytes;
-  const int b_bytes = p.bn * kRowBytes;
+  const int b_bytes = b_rows_smem * kRowBytes;
   // Stage layout: [A][B] or, for BF16x3, [A_hi][B_hi][A_lo][B_lo].
   auto a_smem = [&](int s, int part) { return base + s * sb + part * (a_bytes + b_bytes); };
   auto b_smem = [&](int s, int part) { return base + s * sb + part * (a_bytes + b_bytes) + a_bytes; };
@@ -271,6 +281,31 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
           const int s = it % S;
           const uint32_t ph = (uint32_t)(it / S) & 1u;
           if (!ptx::mbar_wait(empty_bar(s), ph ^ 1u, p.budget, abort_flag, &g_tc_err)) { ok = false; break; }
+          if constexpr (PAIR) {
+            // Both CTAs load their own halves; the even CTA's barrier counts both.
+            const uint32_t lf = ptx::mapa(full_bar(s), 0);
+            const int by = t.tn * p.bn + rank * b_rows_smem;
+            if constexpr (CONV) {
+              const ConvTile& c = p.cv;
+              if (rank == 0) ptx::mbar_arrive_expect_tx(full_bar(s), 2u * (p.a_box_bytes + (uint32_t)b_bytes));
+              const int tap = kb / c.cblocks, c0 = (kb % c.cblocks) * 64;
+              const int kh = tap / c.KW, kw = tap % c.KW;
+              const int tw = t.tm % c.tiles_w, th = (t.tm / c.tiles_w) % c.tiles_h;
+              const int tb = t.tm / (c.tiles_w * c.tiles_h);
+              ptx::tma_load_4d_pair(a_smem(s, 0), &p.tmA, lf, c0, tw * c.Q * c.sw + kw * c.dw - c.pl,
+                                    th * c.R * c.sh + kh * c.dh - c.pt, tb * c.NB);
+              ptx::tma_load_3d_pair(b_smem(s, 0), &p.tmB, lf, c0, tap, by);
+            } else {
+              if (rank == 0) ptx::mbar_arrive_expect_tx(full_bar(s), 2u * (uint32_t)sb);
+              const int kx = kb * kblk;
+              const int nparts = KIND == TC_BF16X3 ? 2 : 1;
+              for (int part = 0; part < nparts; ++part) {
+                ptx::tma_load_2d_pair(a_smem(s, part), part ? &p.tmA2 : t.ma, lf, kx, t.tm * kBM);
+                ptx::tma_load_2d_pair(b_smem(s, part), part ? &p.tmB2 : t.mb, lf, kx, by);
+              }
+            }
+            continue;
+          }
           if constexpr (CONV) {
             // K block kb = (filter tap, 64-channel block); the A box is the
             // input window that tap sees, shifted and strided by TMA.
@@ -307,15 +342,19 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
           }
         }
       }
-      // Drain: the last copy issued into each slot must land before exit.
+      // Drain: the last copy issued into each slot must land before exit.  In
+      // a pair the odd CTA cannot poll the even CTA's barrier; the MMA that
+      // consumed its copies frees its own slot, so it waits on that instead.
       const int last = it;
-      for (int j = last - 1; j >= 0 && j >= last - S; --j)
-        ptx::mbar_drain(full_bar(j % S), (uint32_t)(j / S) & 1u, 100000000ull);
+      for (int j = last - 1; j >= 0 && j >= last - S; --j) {
+        if (PAIR && rank != 0) ptx::mbar_drain(empty_bar(j % S), (uint32_t)(j / S) & 1u, 100000000ull);
+        else ptx::mbar_drain(full_bar(j % S), (uint32_t)(j / S) & 1u, 100000000ull);
+      }
     }
   } else if (warp == 1) {
     // -------------------------------------------------------------- MMA
-    if (lane == 0) {
-      const uint32_t idesc = ptx::make_idesc(KIND == TC_FP8 ? 0 : 1, kBM, p.bn);
+    if (lane == 0 && (!PAIR || rank == 0)) {
+      const uint32_t idesc = ptx::make_idesc(KIND == TC_FP8 ? 0 : 1, PAIR ? 2 * kBM : kBM, p.bn);
       int it = 0, tc = 0;
       bool ok = true;
       for (int u = cluster_id; u < p.units && ok; u += n_clusters, ++tc) {
@@ -339,22 +378,31 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
             const uint64_t ad = ptx::sw128_desc(a_smem(s, 0) + koff);
             const uint64_t bd = ptx::sw128_desc(b_smem(s, 0) + koff);
             const uint32_t accum = (kb > kb0 || k > 0) ? 1u : 0u;
-            ptx::tc_mma<KIND == TC_FP8>(d, ad, bd, idesc, accum);
+            if (PAIR) ptx::tc_mma_pair<KIND == TC_FP8>(d, ad, bd, idesc, accum);
+            else ptx::tc_mma<KIND == TC_FP8>(d, ad, bd, idesc, accum);
             if (KIND == TC_BF16X3) {
               const uint64_t ad2 = ptx::sw128_desc(a_smem(s, 1) + koff);
               const uint64_t bd2 = ptx::sw128_desc(b_smem(s, 1) + koff);
-              ptx::tc_mma<0>(d2, ad, bd2, idesc, accum);   // hi * lo
-              ptx::tc_mma<0>(d2, ad2, bd, idesc, 1u);      // lo * hi
+              if (PAIR) {
+                ptx::tc_mma_pair<0>(d2, ad, bd2, idesc, accum);   // hi * lo
+                ptx::tc_mma_pair<0>(d2, ad2, bd, idesc, 1u);      // lo * hi
+              } else {
+                ptx::tc_mma<0>(d2, ad, bd2, idesc, accum);   // hi * lo
+                ptx::tc_mma<0>(d2, ad2, bd, idesc, 1u);      // lo * hi
+              }
             }
           }
-          if (CL == 2) ptx::tc_commit_mc(empty_bar(s), (uint16_t)0x3);
+          if (PAIR) ptx::tc_commit_pair_mc(empty_bar(s), (uint16_t)0x3);
+          else if (CL == 2) ptx::tc_commit_mc(empty_bar(s), (uint16_t)0x3);
           else ptx::tc_commit(empty_bar(s));
         }
         if (!ok) break;
-        ptx::tc_commit(tfull_bar(acc));
+        if (PAIR) ptx::tc_commit_pair_mc(tfull_bar(acc), (uint16_t)0x3);
+        else ptx::tc_commit(tfull_bar(acc));
       }
       // Drain: every MMA this thread issued completes before TMEM is freed.
-      ptx::tc_commit(drain_bar);
+      if (PAIR) ptx::tc_commit_pair(drain_bar);
+      else ptx::tc_commit(drain_bar);
       ptx::mbar_drain(drain_bar, 0, 100000000ull);
     }
   } else {
@@ -430,14 +478,23 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
       }
       ptx::tc_fence_before();
       __syncwarp();
-      if (lane == 0) ptx::mbar_arrive(tempty_bar(acc));
+      if (lane == 0) {
+        if (PAIR) ptx::mbar_arrive_cluster(ptx::mapa(tempty_bar(acc), 0));   // the issuer's barrier
+        else ptx::mbar_arrive(tempty_bar(acc));
+      }
     }
   }
 
   ptx::tc_fence_before();
   __syncthreads();
+  // A pair frees TMEM only once the even CTA has drained every MMA that
+  // writes into either CTA's TMEM.
+  if (CL == 2) ptx::cluster_sync();
   ptx::tc_fence_after();
-  if (warp == 1) ptx::tmem_dealloc(tmem_base, tmem_cols);
+  if (warp == 1) {
+    if (PAIR) ptx::tmem_dealloc_pair(tmem_base, tmem_cols);
+    else ptx::tmem_dealloc(tmem_base, tmem_cols);
+  }
   if (CL == 2) ptx::cluster_sync();
 }
 
@@ -480,9 +537,14 @@ int smem_bytes(int kind, int bn, int stages) {
   return 1024 + stages * stage_bytes(kind, bn) + 8 * (2 * stages + 5) + 16;
 }
 
-template <int KIND, int CL, bool GROUPED = false, bool CONV = false>
+// Shared memory of a schedule: a CTA of a pair (tile_m 256) keeps half of B.
+int smem_of(int kind, const nk_schedule& s) {
+  return smem_bytes(kind, s.tile_m == 256 ? s.tile_n / 2 : s.tile_n, s.stages);
+}
+
+template <int KIND, int CL, bool GROUPED = false, bool CONV = false, bool PAIR = false>
 nk_status launch(const TcParams& p, int grid, int smem, cudaStream_t st) {
-  auto kern = tc_gemm_kernel<KIND, CL, GROUPED, CONV>;
+  auto kern = tc_gemm_kernel<KIND, CL, GROUPED, CONV, PAIR>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(tc_gemm_kernel)");
   cudaLaunchConfig_t cfg = {};
@@ -503,8 +565,9 @@ nk_status launch(const TcParams& p, int grid, int smem, cudaStream_t st) {
 }
 
 // CTAs that fit on one SM: shared memory and the 512 TMEM columns.
-int ctas_per_sm(int kind, int bn, int stages) {
-  const int sm = smem_bytes(kind, bn, stages);
+int ctas_per_sm(int kind, const nk_schedule& s) {
+  const int bn = s.tile_n;
+  const int sm = smem_of(kind, s);
   int by_smem = kMaxSmem / sm;
   const int acc = kind == TC_BF16X3 ? 2 * bn : bn;
   int cols = 2 * acc < 32 ? 32 : 2 * acc;
@@ -517,14 +580,15 @@ int ctas_per_sm(int kind, int bn, int stages) {
 
 bool tc_schedule_valid(int kind, const nk_schedule& s, int M, int N, int K) {
   (void)M; (void)N; (void)K;
-  if (s.tile_m != 128) return false;
+  // tile_m 256 = a CTA pair issuing 2-SM MMAs (cluster of two).
+  if (s.tile_m != 128 && !(s.tile_m == 256 && s.cluster == 2)) return false;
   if (s.tile_n != 64 && s.tile_n != 128 && s.tile_n != 256) return false;
   if (kind == TC_BF16X3 && s.tile_n > 128) return false;   // 2 accumulators x 2 buffers <= 512 cols
   if (s.tile_k != (kind == TC_FP8 ? 128 : 64)) return false;
   if (s.cluster != 1 && s.cluster != 2) return false;
   if (s.split_k < 1 || s.split_k > 32) return false;
   if (s.stages < 2 || s.stages > 8) return false;
-  if (smem_bytes(kind, s.tile_n, s.stages) > kMaxSmem) return false;
+  if (smem_of(kind, s) > kMaxSmem) return false;
   return true;
 }
 
@@ -613,19 +677,23 @@ nk_status tc_gemm(const TcGemm& g, const nk_schedule& s, void* ws, size_t ws_byt
   const bool cvec = ((reinterpret_cast<uintptr_t>(g.C) & 15) == 0) && (g.ldc % 4 == 0) &&
                     (splits == 1 || (g.N % 4 == 0 && (reinterpret_cast<uintptr_t>(ws) & 15) == 0));
   p.c_vec = cvec ? 1 : 0;
-  const int smem = smem_bytes(g.kind, s.tile_n, s.stages);
-  int grid = sms * ctas_per_sm(g.kind, s.tile_n, s.stages);
+  const int smem = smem_of(g.kind, s);
+  int grid = sms * ctas_per_sm(g.kind, s);
   grid = grid / CL * CL;
   const int need_ctas = p.units * CL;
   if (grid > need_ctas) grid = need_ctas;
   if (grid < CL) grid = CL;
-  switch (g.kind * 2 + (CL - 1)) {
-    case TC_BF16 * 2 + 0: status = launch<TC_BF16, 1>(p, grid, smem, st); break;
-    case TC_BF16 * 2 + 1: status = launch<TC_BF16, 2>(p, grid, smem, st); break;
-    case TC_FP8 * 2 + 0: status = launch<TC_FP8, 1>(p, grid, smem, st); break;
-    case TC_FP8 * 2 + 1: status = launch<TC_FP8, 2>(p, grid, smem, st); break;
-    case TC_BF16X3 * 2 + 0: status = launch<TC_BF16X3, 1>(p, grid, smem, st); break;
-    default: status = launch<TC_BF16X3, 2>(p, grid, smem, st); break;
+  const bool pair = s.tile_m == 256;
+  switch (g.kind * 3 + (pair ? 2 : CL - 1)) {
+    case TC_BF16 * 3 + 0: status = launch<TC_BF16, 1>(p, grid, smem, st); break;
+    case TC_BF16 * 3 + 1: status = launch<TC_BF16, 2>(p, grid, smem, st); break;
+    case TC_BF16 * 3 + 2: status = launch<TC_BF16, 2, false, false, true>(p, grid, smem, st); break;
+    case TC_FP8 * 3 + 0: status = launch<TC_FP8, 1>(p, grid, smem, st); break;
+    case TC_FP8 * 3 + 1: status = launch<TC_FP8, 2>(p, grid, smem, st); break;
+    case TC_FP8 * 3 + 2: status = launch<TC_FP8, 2, false, false, true>(p, grid, smem, st); break;
+    case TC_BF16X3 * 3 + 0: status = launch<TC_BF16X3, 1>(p, grid, smem, st); break;
+    case TC_BF16X3 * 3 + 1: status = launch<TC_BF16X3, 2>(p, grid, smem, st); break;
+    default: status = launch<TC_BF16X3, 2, false, false, true>(p, grid, smem, st); break;
   }
   if (status != NK_OK || splits == 1) return status;
   SplitReduce r;
@@ -774,13 +842,14 @@ nk_status tc_conv(const TcConv& c, const nk_schedule& s, void* ws, size_t ws_byt
   p.budget = wait_budget();
   p.c_vec = ((reinterpret_cast<uintptr_t>(c.O) & 15) == 0 && c.F % 4 == 0 &&
              (splits == 1 || (reinterpret_cast<uintptr_t>(ws) & 15) == 0)) ? 1 : 0;
-  const int smem = smem_bytes(TC_BF16, s.tile_n, s.stages);
-  int grid = sms * ctas_per_sm(TC_BF16, s.tile_n, s.stages);
+  const int smem = smem_of(TC_BF16, s);
+  int grid = sms * ctas_per_sm(TC_BF16, s);
   grid = grid / CL * CL;
   if (grid > p.units * CL) grid = p.units * CL;
   if (grid < CL) grid = CL;
-  status = CL == 2 ? launch<TC_BF16, 2, false, true>(p, grid, smem, st)
-                   : launch<TC_BF16, 1, false, true>(p, grid, smem, st);
+  if (s.tile_m == 256) status = launch<TC_BF16, 2, false, true, true>(p, grid, smem, st);
+  else if (CL == 2) status = launch<TC_BF16, 2, false, true>(p, grid, smem, st);
+  else status = launch<TC_BF16, 1, false, true>(p, grid, smem, st);
   if (status != NK_OK || splits == 1) return status;
   SplitReduce r{};
   r.partial = p.partial;
@@ -850,7 +919,7 @@ nk_status build_grouped(int G, const nk_gemm_group* groups, int precision, const
   if (precision != NK_PREC_BF16)
     return fail(NK_ERR_UNSUPPORTED, "grouped GEMM runs BF16 operands (NK_PREC_BF16) only");
   const nk_schedule s = grouped_schedule(user);
-  if (s.cluster != 1 || s.split_k != 1 || !tc_schedule_valid(TC_BF16, s, 1, 1, 1))
+  if (s.cluster != 1 || s.split_k != 1 || s.tile_m != 128 || !tc_schedule_valid(TC_BF16, s, 1, 1, 1))
     return fail(NK_ERR_NO_SCHEDULE, "grouped schedule needs cluster 1, split_k 1 and a legal tile");
   int sms = 0;
   nk_status st = require_device(&sms);
@@ -914,8 +983,8 @@ nk_status build_grouped(int G, const nk_gemm_group* groups, int precision, const
   p.groups = reinterpret_cast<const GroupDesc*>(db + off_desc);
   p.tile_start = reinterpret_cast<const int*>(db + off_start);
   plan.units = (int)total;
-  plan.smem = smem_bytes(TC_BF16, s.tile_n, s.stages);
-  int grid = sms * ctas_per_sm(TC_BF16, s.tile_n, s.stages);
+  plan.smem = smem_of(TC_BF16, s);
+  int grid = sms * ctas_per_sm(TC_BF16, s);
   plan.grid = grid < plan.units ? grid : plan.units;
   return NK_OK;
 }

@@ -64,6 +64,8 @@ def test_outlier_precision_bounds(nk, prec):
 
 SCHEDULES = [(128, bn, 64, cl, st, sk) for bn in (64, 128, 256) for cl in (1, 2)
              for st in (2, 4) for sk in (1, 3)]
+# CTA pairs issuing 2-SM MMAs (tile_m 256, cluster 2)
+SCHEDULES += [(256, bn, 64, 2, st, sk) for bn in (64, 128, 256) for st in (3, 6) for sk in (1, 3)]
 
 
 @pytest.mark.parametrize("sched", SCHEDULES)
@@ -75,7 +77,8 @@ def test_bf16_schedules_bitwise(nk, sched):
     np.testing.assert_array_equal(C, O.matmul(A, B))
 
 
-@pytest.mark.parametrize("sched", [(128, 64, 64, 1, 2, 1), (128, 128, 64, 2, 3, 2), (128, 64, 64, 2, 4, 3)])
+@pytest.mark.parametrize("sched", [(128, 64, 64, 1, 2, 1), (128, 128, 64, 2, 3, 2), (128, 64, 64, 2, 4, 3),
+                                   (256, 128, 64, 2, 3, 1), (256, 64, 64, 2, 4, 2)])
 def test_bf16x3_schedules_bitwise(nk, sched):
     M, N, K = 260, 200, 384
     A = synth.small_ints(67, 1, (M, K))
@@ -84,7 +87,8 @@ def test_bf16x3_schedules_bitwise(nk, sched):
     np.testing.assert_array_equal(C, O.matmul(A, B))
 
 
-@pytest.mark.parametrize("sched", [(128, 128, 128, 1, 4, 1), (128, 256, 128, 2, 4, 2), (128, 64, 128, 1, 3, 1)])
+@pytest.mark.parametrize("sched", [(128, 128, 128, 1, 4, 1), (128, 256, 128, 2, 4, 2), (128, 64, 128, 1, 3, 1),
+                                   (256, 256, 128, 2, 6, 1), (256, 128, 128, 2, 4, 2)])
 def test_fp8_schedules_bitwise(nk, sched):
     M, N, K = 260, 384, 640
     A = synth.small_ints(63, 1, (M, K)) / 2
@@ -131,3 +135,16 @@ def test_full_size_sampled_rows(nk, n, prec):
     if prec == "bf16":
         Rb = O.matmul(O.bf16_rn(A[rows]), O.bf16_rn(B))
         assert O.rel_frobenius(got, Rb) <= 1e-5
+
+
+@pytest.mark.parametrize("prec,sched", [("bf16", (256, 256, 64, 2, 6, 1)), ("fp8", (256, 256, 128, 2, 6, 1)),
+                                        ("bf16x3", (256, 128, 64, 2, 3, 1))])
+def test_pair_full_size_sampled_rows(nk, prec, sched):
+    n = 8192
+    A, B = synth.matmul_outlier(n, n, n)
+    C = _mm(nk, dev(A), dev(B), n, n, prec, schedule=sched)
+    rows = np.sort(synth.raw_u64(68, n, 64) % np.uint64(n)).astype(np.int64)
+    got = host(C[torch.from_numpy(rows).to(DEV)])
+    assert O.rel_frobenius(got, O.matmul(A[rows], B)) <= TOL[prec]
+    if prec == "bf16":
+        assert O.rel_frobenius(got, O.matmul(O.bf16_rn(A[rows]), O.bf16_rn(B))) <= 1e-5
