@@ -51,17 +51,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
 
 // Bounded wait on phase `parity` of barrier `bar`.  Returns false when the
 // CTA is aborting (flag already set by another role, or this wait ran out of
-// its iteration budget or of about four seconds).
+// its iteration budget or of about four seconds).  The fast path is a bare
+// poll: the wall clock (a slow register to read) and the abort flag are only
+// consulted every 1024 polls, so a wait that ends soon costs no timer read.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int64_t budget,
                                           volatile int* abort_flag, unsigned int* err_word) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = globaltimer();
-  for (int64_t i = 1;; ++i) {
+  uint64_t t0 = 0;
+  for (int64_t i = 0;; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
     bool give_up = i >= budget;
-    if ((i & 255) == 0) {
+    if ((i & 1023) == 1023) {
       if (*abort_flag) return false;
-      give_up |= globaltimer() - t0 > 4000000000ull;
+      const uint64_t now = globaltimer();
+      if (t0 == 0) t0 = now;
+      give_up |= now - t0 > 4000000000ull;
     }
     if (give_up) {
       atomicOr(err_word, 1u);
