@@ -193,9 +193,17 @@ __device__ __forceinline__ int conv_row(const ConvTile& c, int tm, int r) {
 // PAIR: the two CTAs of a cluster form one 2-SM MMA (cta_group::2) computing a
 // 256 x BN tile; each holds its 128 rows of A and BN/2 rows of B^T, and the
 // even CTA's barriers gate the pair (its MMA thread is the only issuer).
-template <int KIND, int CL, bool GROUPED, bool CONV = false, bool PAIR = false>
-__global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_constant__ TcParams p) {
+//
+// WIDE: a pair computing a 256 x 512 tile as two independent N = 256
+// accumulator chains that share the A tile.  One chain of dependent MMAs on a
+// single accumulator issues about one instruction per ~190 cycles, while an
+// N = 256 MMA holds only 128 cycles of math; interleaving two chains hides
+// that latency.  Both chains fill the 512 TMEM columns, so the accumulator is
+// single-buffered and eight epilogue warps drain it.
+template <int KIND, int CL, bool GROUPED, bool CONV = false, bool PAIR = false, bool WIDE = false>
+__global__ void __launch_bounds__(WIDE ? 320 : 192, 1) tc_gemm_kernel(const __grid_constant__ TcParams p) {
   static_assert(!PAIR || CL == 2, "a CTA pair is a cluster of two");
+  static_assert(!WIDE || (PAIR && KIND != TC_BF16X3 && !GROUPED), "wide tiles are pair tiles");
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = ptx::smem_u32(smem_raw);
   const uint32_t base = (raw + 1023) & ~1023u;
@@ -222,7 +230,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
   // hi*lo + lo*hi corrections accumulate apart and meet in the epilogue, so
   // the large term sees K/16 roundings instead of 3K/16).
   const int acc_cols = KIND == TC_BF16X3 ? 2 * p.bn : p.bn;
-  const uint32_t tmem_cols = 2u * (uint32_t)acc_cols < 32u ? 32u : 2u * (uint32_t)acc_cols;
+  const uint32_t tmem_cols = WIDE ? 512u : 2u * (uint32_t)acc_cols < 32u ? 32u : 2u * (uint32_t)acc_cols;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
@@ -231,7 +239,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     }
     for (int b = 0; b < 2; ++b) {
       ptx::mbar_init(tfull_bar(b), 1);
-      ptx::mbar_init(tempty_bar(b), PAIR ? 8 : 4);   // a pair: both CTAs' epilogue warps
+      ptx::mbar_init(tempty_bar(b), WIDE ? 16 : PAIR ? 8 : 4);   // every epilogue warp of the pair
     }
     ptx::mbar_init(drain_bar, 1);
     *abort_flag = 0;
@@ -298,6 +306,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
             } else {
               if (rank == 0) ptx::mbar_arrive_expect_tx(full_bar(s), 2u * (uint32_t)sb);
               const int kx = kb * kblk;
+              if (WIDE) {
+                // chain h (N columns h*256 .. h*256+255): this CTA holds its 128 rows of B^T
+                ptx::tma_load_2d_pair(a_smem(s, 0), t.ma, lf, kx, t.tm * kBM);
+                ptx::tma_load_2d_pair(b_smem(s, 0), t.mb, lf, kx, t.tn * p.bn + rank * 128);
+                ptx::tma_load_2d_pair(b_smem(s, 0) + 128 * kRowBytes, t.mb, lf, kx, t.tn * p.bn + 256 + rank * 128);
+                continue;
+              }
               const int nparts = KIND == TC_BF16X3 ? 2 : 1;
               for (int part = 0; part < nparts; ++part) {
                 ptx::tma_load_2d_pair(a_smem(s, part), part ? &p.tmA2 : t.ma, lf, kx, t.tm * kBM);
@@ -354,19 +369,19 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
   } else if (warp == 1) {
     // -------------------------------------------------------------- MMA
     if (lane == 0 && (!PAIR || rank == 0)) {
-      const uint32_t idesc = ptx::make_idesc(KIND == TC_FP8 ? 0 : 1, PAIR ? 2 * kBM : kBM, p.bn);
+      const uint32_t idesc = ptx::make_idesc(KIND == TC_FP8 ? 0 : 1, PAIR ? 2 * kBM : kBM, WIDE ? 256 : p.bn);
       int it = 0, tc = 0;
       bool ok = true;
       for (int u = cluster_id; u < p.units && ok; u += n_clusters, ++tc) {
         const UnitView t = view_unit<GROUPED>(p, u, CL, rank);
         const int kb0 = t.kb0;
         const int kb1 = t.kb1;
-        const int acc = tc & 1;
-        const uint32_t aph = (uint32_t)(tc >> 1) & 1u;
+        const int acc = WIDE ? 0 : tc & 1;   // a wide tile's two chains fill TMEM: one buffer
+        const uint32_t aph = WIDE ? (uint32_t)tc & 1u : (uint32_t)(tc >> 1) & 1u;
         if (!ptx::mbar_wait(tempty_bar(acc), aph ^ 1u, p.budget, abort_flag, &g_tc_err)) break;
         ptx::tc_fence_after();
         const uint32_t d = tmem_base + (uint32_t)(acc * acc_cols);
-        const uint32_t d2 = d + (uint32_t)p.bn;   // BF16x3 correction accumulator
+        const uint32_t d2 = d + (uint32_t)(WIDE ? 256 : p.bn);   // BF16x3 corrections / second wide chain
         for (int kb = kb0; kb < kb1; ++kb, ++it) {
           const int s = it % S;
           const uint32_t ph = (uint32_t)(it / S) & 1u;
@@ -380,6 +395,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
             const uint32_t accum = (kb > kb0 || k > 0) ? 1u : 0u;
             if (PAIR) ptx::tc_mma_pair<KIND == TC_FP8>(d, ad, bd, idesc, accum);
             else ptx::tc_mma<KIND == TC_FP8>(d, ad, bd, idesc, accum);
+            if (WIDE) {   // second chain: B^T rows 128..255 of this CTA's stage
+              const uint64_t bw = ptx::sw128_desc(b_smem(s, 0) + 128 * kRowBytes + koff);
+              ptx::tc_mma_pair<KIND == TC_FP8>(d2, ad, bw, idesc, accum);
+            }
             if (KIND == TC_BF16X3) {
               const uint64_t ad2 = ptx::sw128_desc(a_smem(s, 1) + koff);
               const uint64_t bd2 = ptx::sw128_desc(b_smem(s, 1) + koff);
@@ -413,13 +432,16 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     int tc = 0;
     for (int u = cluster_id; u < p.units; u += n_clusters, ++tc) {
       const UnitView t = view_unit<GROUPED>(p, u, CL, rank);
-      const int acc = tc & 1;
-      const uint32_t aph = (uint32_t)(tc >> 1) & 1u;
+      const int acc = WIDE ? 0 : tc & 1;
+      const uint32_t aph = WIDE ? (uint32_t)tc & 1u : (uint32_t)(tc >> 1) & 1u;
       if (!ptx::mbar_wait(tfull_bar(acc), aph, p.budget, abort_flag, &g_tc_err)) break;
       ptx::tc_fence_after();
       const int row = CONV ? conv_row(p.cv, t.tm, q * 32 + lane) : t.tm * kBM + q * 32 + lane;
       const bool row_ok = CONV ? row >= 0 : row < t.M;
-      for (int c0 = 0; c0 < p.bn; c0 += 32) {
+      // a wide tile has two warps per lane quarter, each draining one chain's 256 columns
+      const int c_begin = WIDE ? ((warp - 2) / 4) * 256 : 0;
+      const int c_end = WIDE ? c_begin + 256 : p.bn;
+      for (int c0 = c_begin; c0 < c_end; c0 += 32) {
         float v[32];
         const uint32_t ta = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * acc_cols + c0);
         ptx::tmem_ld32(ta, v);
@@ -542,14 +564,14 @@ int smem_of(int kind, const nk_schedule& s) {
   return smem_bytes(kind, s.tile_m == 256 ? s.tile_n / 2 : s.tile_n, s.stages);
 }
 
-template <int KIND, int CL, bool GROUPED = false, bool CONV = false, bool PAIR = false>
+template <int KIND, int CL, bool GROUPED = false, bool CONV = false, bool PAIR = false, bool WIDE = false>
 nk_status launch(const TcParams& p, int grid, int smem, cudaStream_t st) {
-  auto kern = tc_gemm_kernel<KIND, CL, GROUPED, CONV, PAIR>;
+  auto kern = tc_gemm_kernel<KIND, CL, GROUPED, CONV, PAIR, WIDE>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(tc_gemm_kernel)");
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(kThreads);
+  cfg.blockDim = dim3(WIDE ? 320 : kThreads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
@@ -566,6 +588,7 @@ nk_status launch(const TcParams& p, int grid, int smem, cudaStream_t st) {
 
 // CTAs that fit on one SM: shared memory and the 512 TMEM columns.
 int ctas_per_sm(int kind, const nk_schedule& s) {
+  if (s.tile_n == 512) return 1;   // a wide tile holds all 512 TMEM columns
   const int bn = s.tile_n;
   const int sm = smem_of(kind, s);
   int by_smem = kMaxSmem / sm;
@@ -582,7 +605,8 @@ bool tc_schedule_valid(int kind, const nk_schedule& s, int M, int N, int K) {
   (void)M; (void)N; (void)K;
   // tile_m 256 = a CTA pair issuing 2-SM MMAs (cluster of two).
   if (s.tile_m != 128 && !(s.tile_m == 256 && s.cluster == 2)) return false;
-  if (s.tile_n != 64 && s.tile_n != 128 && s.tile_n != 256) return false;
+  if (s.tile_n != 64 && s.tile_n != 128 && s.tile_n != 256 && s.tile_n != 512) return false;
+  if (s.tile_n == 512 && (s.tile_m != 256 || kind == TC_BF16X3)) return false;   // wide pair tiles only
   if (kind == TC_BF16X3 && s.tile_n > 128) return false;   // 2 accumulators x 2 buffers <= 512 cols
   if (s.tile_k != (kind == TC_FP8 ? 128 : 64)) return false;
   if (s.cluster != 1 && s.cluster != 2) return false;
@@ -641,7 +665,8 @@ nk_status tc_gemm(const TcGemm& g, const nk_schedule& s, void* ws, size_t ws_byt
   memset(&p, 0, sizeof p);
   const int CL = s.cluster;
   if ((status = make_kmajor_map(&p.tmA, fp8, g.A, g.M, g.K, g.lda, kBM)) != NK_OK) return status;
-  if ((status = make_kmajor_map(&p.tmB, fp8, g.B, g.N, g.K, g.ldb, s.tile_n / CL)) != NK_OK) return status;
+  const int b_box = s.tile_n == 512 ? 128 : s.tile_n / CL;   // a wide tile loads B^T in 128-row boxes
+  if ((status = make_kmajor_map(&p.tmB, fp8, g.B, g.N, g.K, g.ldb, b_box)) != NK_OK) return status;
   if (g.kind == TC_BF16X3) {
     if ((status = make_kmajor_map(&p.tmA2, fp8, g.A2, g.M, g.K, g.lda, kBM)) != NK_OK) return status;
     if ((status = make_kmajor_map(&p.tmB2, fp8, g.B2, g.N, g.K, g.ldb, s.tile_n / CL)) != NK_OK) return status;
@@ -684,6 +709,10 @@ nk_status tc_gemm(const TcGemm& g, const nk_schedule& s, void* ws, size_t ws_byt
   if (grid > need_ctas) grid = need_ctas;
   if (grid < CL) grid = CL;
   const bool pair = s.tile_m == 256;
+  if (s.tile_n == 512) {
+    if (g.kind == TC_FP8) status = launch<TC_FP8, 2, false, false, true, true>(p, grid, smem, st);
+    else status = launch<TC_BF16, 2, false, false, true, true>(p, grid, smem, st);
+  } else
   switch (g.kind * 3 + (pair ? 2 : CL - 1)) {
     case TC_BF16 * 3 + 0: status = launch<TC_BF16, 1>(p, grid, smem, st); break;
     case TC_BF16 * 3 + 1: status = launch<TC_BF16, 2>(p, grid, smem, st); break;
@@ -813,6 +842,7 @@ nk_status tc_conv(const TcConv& c, const nk_schedule& s, void* ws, size_t ws_byt
   TcParams p;
   memset(&p, 0, sizeof p);
   const int CL = s.cluster;
+  if (s.tile_n == 512) return fail(NK_ERR_NO_SCHEDULE, "wide 256 x 512 tiles are for matmul");
   if ((status = make_conv_maps(p, c, t, s.tile_n / CL)) != NK_OK) return status;
   p.cv = t;
   p.a_box_bytes = (uint32_t)(t.Q * t.R * t.NB * kRowBytes);

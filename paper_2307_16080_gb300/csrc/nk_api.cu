@@ -441,7 +441,7 @@ static nk_status plan_tc_conv(const nk_tensor* I, const nk_tensor* W, const nk_t
   if (S.cluster == 0) S.cluster = d.cluster;
   if (S.stages == 0) S.stages = d.stages;
   if (S.split_k == 0) S.split_k = d.split_k;
-  if (!tc_schedule_valid(TC_BF16, S, g.n * g.oh * g.ow, F, g.kh * g.kw * g.c))
+  if (!tc_schedule_valid(TC_BF16, S, g.n * g.oh * g.ow, F, g.kh * g.kw * g.c) || S.tile_n == 512)
     return fail(NK_ERR_NO_SCHEDULE, "illegal conv schedule");
   P.sched = S;
   P.Cp = (g.c + 7) / 8 * 8;

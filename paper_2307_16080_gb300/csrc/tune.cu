@@ -114,11 +114,12 @@ std::vector<nk_schedule> enumerate(const nk_problem* p) {
   const int tk = kind == TC_FP8 ? 128 : 64;
   const int64_t nkb = p->op == NK_OP_CONV2D ? (int64_t)p->kh * p->kw * ((p->c + 63) / 64) : (K + tk - 1) / tk;
   for (int tm : {128, 256})
-  for (int tn : {64, 128, 256})
+  for (int tn : {64, 128, 256, 512})
     for (int cl : {1, 2})
       for (int split : {1, 2, 4, 8, 16})
         for (int st = 2; st <= 8; ++st) {
           if (tm == 256 && cl != 2) continue;
+          if (tn == 512 && p->op == NK_OP_CONV2D) continue;
           nk_schedule s{tm, tn, tk, cl, st, split};
           if (split > nkb) continue;
           if (!tc_schedule_valid(kind, s, (int)M, (int)N, (int)K)) continue;
