@@ -1,23 +1,30 @@
 #!/usr/bin/env python
-"""Benchmark: linalg.matmul precision sweep at M = N = K = 8192 on one GB300.
+"""Benchmark: linalg.matmul precision sweep at M = N = K = 8192 on GB300.
 
-One step is one pass of the whole BF16 hot path over the synthetic operands:
-operand prep (FP32 -> BF16 casts, B transposed to K-major) followed by the
-tcgen05 GEMM with its epilogue, all through the C ABI.  `value` is the useful
-FLOP rate of the whole step (2*M*N*K / step time); the roofline object times
-the GEMM kernel alone with CUDA events on its stream.  Inputs (268 MB per
-FP32 operand) are larger than the 129 MB L2, so no flush is needed between
-steps.  FP32, BF16x3 and FP8 GEMM throughputs of the same sweep are reported
-beside it.
+One step is one pass of the whole BF16 hot path over synthetic operands
+already resident in HBM: operand prep (FP32 -> BF16 casts, B transposed to
+K-major) and the tcgen05 GEMM with its epilogue, all through the C ABI.
+`value` is the useful FLOP rate of the whole step (2*M*N*K / step time); the
+roofline object times the GEMM kernel alone with CUDA events on its stream.
+The FP32 operands (268 MB each) exceed the 129 MB L2, so no flush is needed.
+
+Beside the headline the line carries: the rest of the precision sweep (FP8,
+BF16x3, FP32 and the ratios to FP32), an end-to-end number through pinned
+host buffers with the copies inside the timed region, the grouped-GEMM
+config (one persistent launch replayed from a CUDA graph vs one launch per
+GEMM), the convolution configs, the ResNet-style stack with schedules from
+the learned cost model vs exhaustive search, and the FP64 oracle timed on
+the host's cores on a bounded sample.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl nk|reference]
 
-With --impl reference the FP64 CPU oracle is timed on a bounded sample of
-the same workload (rank 0 only).
+Under torchrun every rank runs its own independent problem (weak scaling);
+rank 0 prints the line.  --impl reference times the FP64 CPU oracle alone.
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -33,6 +40,7 @@ sys.path.insert(0, ROOT)
 
 N_DEFAULT = 8192
 METRIC = "TFLOP/s & % of tensor peak, matmul/conv2d, BF16/FP8 vs FP32 at stated error"
+GEMM_SOURCES = ("paper_2307_16080_gb300/csrc/k_tc_gemm.cu", "paper_2307_16080_gb300/csrc/tc_ptx.cuh")
 
 
 def peaks():
@@ -42,6 +50,25 @@ def peaks():
         return float(p["bf16_tflops"]), float(p["hbm_gbs"]), "measured"
     except Exception:
         return 1900.0, 6800.0, "fallback"
+
+
+def source_sha():
+    h = hashlib.sha256()
+    for f in GEMM_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(key):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the kernel source as it is now (else None)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f)[key]
+        return rec["dram_bytes_per_launch"] if rec.get("source_sha256") == source_sha() else None
+    except Exception:
+        return None
 
 
 class ClockSampler:
@@ -60,9 +87,8 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.t = threading.Thread(target=self._read, daemon=True)
-            self.t.start()
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
         except Exception:
             self.proc = None
 
@@ -96,50 +122,239 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def host_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        info = threadpool_info()
+        if info:
+            return max(int(i.get("num_threads", 1)) for i in info)
+    except Exception:
+        pass
+    return len(os.sched_getaffinity(0))
+
+
 def cpu_baseline(A, B, rows: int):
-    """The FP64 oracle (as it stands) on a sample of `rows` rows of the BF16 workload."""
+    """The FP64 oracle (as it stands) on `rows` output rows of the BF16 workload."""
     import oracle.nk_oracle as O
     t0 = time.perf_counter()
     O.matmul_precision(A[:rows], B, "bf16")
     dt = time.perf_counter() - t0
     flops = 2.0 * rows * B.shape[0] * B.shape[1]
-    try:
-        from threadpoolctl import threadpool_info
-        cores = max(int(i.get("num_threads", 1)) for i in threadpool_info()) if threadpool_info() else 1
-    except Exception:
-        cores = len(os.sched_getaffinity(0))
-    return {"value": flops / dt / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
-            "sample": f"{rows} of {A.shape[0]} output rows of the BF16 8192^3 matmul "
-                      f"(bf16 rounding + FP64 numpy matmul), {dt:.1f} s"}
+    return {"value": flops / dt / 1e12, "unit": "TFLOP/s", "cores": host_threads(), "kind": "oracle",
+            "sample": f"{rows} of {A.shape[0]} output rows of the BF16 {A.shape[0]}^3 matmul "
+                      f"(bf16 rounding of both operands + FP64 numpy matmul), {dt:.1f} s"}
 
 
 def run_reference(args, rank):
     if rank != 0:
         return
+    import oracle.nk_oracle as O
     from paper_2307_16080_gb300 import synth
     n = args.n
     A, B = synth.matmul_outlier(n, n, n)
     rows = args.ref_rows
-    for _ in range(args.warmup):
-        pass
+    for _ in range(min(args.warmup, 1)):
+        O.matmul_precision(A[:rows], B, "bf16")
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        import oracle.nk_oracle as O
         O.matmul_precision(A[:rows], B, "bf16")
         times.append(time.perf_counter() - t0)
     flops = 2.0 * rows * n * n
     value = flops * len(times) / sum(times) / 1e12
-    cores = len(os.sched_getaffinity(0))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": f"linalg.matmul bf16 {n}x{n}x{n} (precision sweep), oracle sample"},
-            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
-                             "sample": f"{rows} output rows per step"},
+            "config": {"workload": f"linalg.matmul precision sweep, BF16, M=N=K={n}; FP64 oracle on a sample"},
+            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": host_threads(), "kind": "oracle",
+                             "sample": f"{rows} of {n} output rows per step"},
             "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def time_fn(torch, fn, reps, warm=2):
+    st = torch.cuda.current_stream()
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(reps):
+        fn()
+    e1.record(st)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def sweep_report(torch, nk, dev, a32, b32, c, flop, kern_tflops):
+    """GEMM kernel throughput of the other precisions on the same operands."""
+    out = {"bf16": kern_tflops}
+    amax = torch.empty(2, device=dev)
+    nk.nk_amax(a32, amax[0:1])
+    nk.nk_amax(b32, amax[1:2])
+    sc = torch.empty(2, device=dev)
+    n = a32.shape[0]
+    a8 = torch.empty(n, n, dtype=torch.uint8, device=dev)
+    bt8 = torch.empty(n, n, dtype=torch.uint8, device=dev)
+    nk.nk_cast_fp8(a32, amax[0:1], a8, scale_out=sc[0:1])
+    nk.nk_cast_fp8(b32, amax[1:2], bt8, transpose=True, scale_out=sc[1:2])
+    torch.cuda.synchronize()
+    sa, sb = float(sc[0].item()), float(sc[1].item())
+    ws8 = nk.workspace(nk.nk_matmul_workspace_size(a8, bt8.t(), c, "fp8"), dev)
+    t8 = time_fn(torch, lambda: nk.nk_matmul(a8, bt8.t(), c, precision="fp8", scale_a=sa, scale_b=sb, ws=ws8), 10)
+    out["fp8"] = flop / (t8 * 1e-3) / 1e12
+    del a8, bt8, ws8
+    wsx = nk.workspace(nk.nk_matmul_workspace_size(a32, b32, c, "bf16x3"), dev)
+    tx = time_fn(torch, lambda: nk.nk_matmul(a32, b32, c, precision="bf16x3", ws=wsx), 5)
+    out["bf16x3_with_prep"] = flop / (tx * 1e-3) / 1e12
+    del wsx
+    wsf = nk.workspace(nk.nk_matmul_workspace_size(a32, b32, c, "f32"), dev)
+    tf = time_fn(torch, lambda: nk.nk_matmul(a32, b32, c, precision="f32", ws=wsf), 2, warm=1)
+    out["f32"] = flop / (tf * 1e-3) / 1e12
+    out["bf16_over_f32"] = out["bf16"] / out["f32"]
+    out["fp8_over_f32"] = out["fp8"] / out["f32"]
+    out["unit"] = "TFLOP/s (GEMM kernel; bf16x3 includes its split pass)"
+    nk.nk_sync_status()
+    return out
+
+
+def e2e_report(torch, nk, dev, A, B, reps):
+    """Pinned host FP32 A, B in and host FP32 C out every step through the
+    public API, with uploads, compute and downloads of consecutive steps on
+    three streams (double-buffered), as a user would pipeline them."""
+    n = A.shape[0]
+    a_h = torch.from_numpy(A).pin_memory()
+    b_h = torch.from_numpy(B).pin_memory()
+    c_h = [torch.empty(n, n).pin_memory() for _ in range(2)]
+    a32 = [torch.empty(n, n, device=dev) for _ in range(2)]
+    b32 = [torch.empty(n, n, device=dev) for _ in range(2)]
+    cc = [torch.empty(n, n, device=dev) for _ in range(2)]
+    a16 = torch.empty(n, n, dtype=torch.bfloat16, device=dev)
+    bt16 = torch.empty(n, n, dtype=torch.bfloat16, device=dev)
+    ws = nk.workspace(nk.nk_matmul_workspace_size(a16, bt16.t(), cc[0], "bf16"), dev)
+    s_up, s_dn = torch.cuda.Stream(), torch.cuda.Stream()
+    s_c = torch.cuda.current_stream()
+    comp_done = [torch.cuda.Event() for _ in range(2)]
+    down_done = [torch.cuda.Event() for _ in range(2)]
+    up_done = [torch.cuda.Event() for _ in range(2)]
+    for j in range(2):
+        comp_done[j].record(s_c)
+        down_done[j].record(s_c)
+
+    def run(k):
+        for i in range(k):
+            j = i % 2
+            with torch.cuda.stream(s_up):
+                s_up.wait_event(comp_done[j])
+                a32[j].copy_(a_h, non_blocking=True)
+                b32[j].copy_(b_h, non_blocking=True)
+                up_done[j].record(s_up)
+            s_c.wait_event(up_done[j])
+            s_c.wait_event(down_done[j])
+            nk.nk_cast_bf16(a32[j], a16)
+            nk.nk_cast_bf16(b32[j], bt16, transpose=True)
+            nk.nk_matmul(a16, bt16.t(), cc[j], precision="bf16", ws=ws)
+            comp_done[j].record(s_c)
+            with torch.cuda.stream(s_dn):
+                s_dn.wait_event(comp_done[j])
+                c_h[j].copy_(cc[j], non_blocking=True)
+                down_done[j].record(s_dn)
+        torch.cuda.synchronize()
+
+    run(2)
+    t0 = time.perf_counter()
+    run(reps)
+    ms = (time.perf_counter() - t0) * 1e3 / reps
+    nk.nk_sync_status()
+    return {"value": 2.0 * n ** 3 / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms,
+            "h2d_bytes_per_step": 2 * n * n * 4, "d2h_bytes_per_step": n * n * 4,
+            "how": "host wall clock over pipelined steps (upload / compute / download streams)"}
+
+
+def grouped_report(torch, nk, synth, dev):
+    """512 uneven BF16 GEMMs: one persistent launch replayed from a CUDA graph
+    vs one nk_matmul launch per GEMM."""
+    shapes = [tuple(int(v) for v in s) for s in synth.grouped_problems(512)]
+    a = [torch.empty(M, K, device=dev).uniform_(-1, 1).to(torch.bfloat16) for (M, N, K) in shapes]
+    bt = [torch.empty(N, K, device=dev).uniform_(-1, 1).to(torch.bfloat16) for (M, N, K) in shapes]
+    c = [torch.empty(M, N, device=dev) for (M, N, K) in shapes]
+    flop = float(sum(2.0 * M * N * K for (M, N, K) in shapes))
+    groups, G = nk.make_groups(a, bt, c)
+    plan = nk.nk_grouped_plan_create(groups, G)
+    graph = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        nk.nk_grouped_plan_run(plan)
+        with torch.cuda.graph(graph, stream=s):
+            nk.nk_grouped_plan_run(plan)
+    torch.cuda.current_stream().wait_stream(s)
+    t_graph = time_fn(torch, graph.replay, 20)
+    wss = [nk.workspace(nk.nk_matmul_workspace_size(a[g], bt[g].t(), c[g], "bf16"), dev) for g in range(G)]
+
+    def per_gemm():
+        for g in range(G):
+            nk.nk_matmul(a[g], bt[g].t(), c[g], precision="bf16", ws=wss[g])
+    t_loop = time_fn(torch, per_gemm, 5)
+    nk.nk_sync_status()
+    nk.nk_grouped_plan_destroy(plan)
+    return {"groups": G, "useful_flop": flop, "persistent_graph_ms": t_graph, "per_gemm_launches_ms": t_loop,
+            "persistent_graph_tflops": flop / (t_graph * 1e-3) / 1e12,
+            "per_gemm_tflops": flop / (t_loop * 1e-3) / 1e12, "speedup": t_loop / t_graph,
+            "launches": {"persistent": 1, "per_gemm": G}}
+
+
+def conv_report(torch, nk, synth, dev):
+    """FP32 conv config (8x56x56x64, 3x3x64x64, s1 p1, bias + ReLU) on the
+    CUDA cores, and the same layer in BF16 on the tensor cores."""
+    I, W, bias = synth.conv_resnet_block()
+    i32, w32, b32 = (torch.from_numpy(x).to(dev) for x in (I, W, bias))
+    out = torch.empty(8, 56, 56, 64, device=dev)
+    flop = 2.0 * 8 * 56 * 56 * 64 * 9 * 64
+    t32 = time_fn(torch, lambda: nk.nk_conv2d_nhwc_hwcf(i32, w32, out, pad=(1, 1, 1, 1), bias=b32, relu=True), 20)
+    i16 = i32.to(torch.bfloat16)
+    ws = nk.workspace(nk.nk_conv2d_workspace_size(i16, w32, out, pad=(1, 1, 1, 1), precision="bf16"), dev)
+    t16 = time_fn(torch, lambda: nk.nk_conv2d_nhwc_hwcf(i16, w32, out, pad=(1, 1, 1, 1), precision="bf16",
+                                                        bias=b32, relu=True, ws=ws), 20)
+    nk.nk_sync_status()
+    return {"f32_ms": t32, "f32_tflops": flop / (t32 * 1e-3) / 1e12, "bf16_ms": t16,
+            "bf16_tflops": flop / (t16 * 1e-3) / 1e12, "bf16_over_f32": t32 / t16,
+            "note": "bf16 time includes the per-call FP32 -> BF16 weight cast"}
+
+
+def resnet_report(torch, synth, dev):
+    """The 20-layer ResNet-style stack (BF16 conv, tensor cores) at batch 1,
+    8, 32: total time with the built-in default schedules, with the cost
+    model's top-5 (timed) pick, and with exhaustive search."""
+    from paper_2307_16080_gb300 import costmodel
+    from paper_2307_16080_gb300 import nk_tune as nt
+    if not os.path.exists(costmodel.MODEL_PATH):
+        return None
+    params, _, _ = costmodel.load_model()
+    P = torch.from_numpy(params).to(dev)
+    out = {}
+    for b in (1, 8, 32):
+        tot = {"default_ms": 0.0, "model_top5_ms": 0.0, "exhaustive_ms": 0.0, "flop": 0.0}
+        timed = {"model": 0, "exhaustive": 0}
+        for L in synth.resnet_stack(b):
+            p = nt.conv_problem(L["N"], L["H"], L["W"], L["C"], L["F"], L["KH"], L["KW"], L["stride"], L["pad"])
+            _, ex = nt.nk_tune(p, nt.NK_TUNE_EXHAUSTIVE, reps=3)
+            _, mo = nt.nk_tune(p, nt.NK_TUNE_MODEL_TOPK, topk=5, params=P, reps=3)
+            tot["default_ms"] += ex.default_ms
+            tot["exhaustive_ms"] += ex.best_ms
+            tot["model_top5_ms"] += mo.best_ms
+            timed["model"] += mo.timed
+            timed["exhaustive"] += ex.timed
+            oh = (L["H"] + 2 * L["pad"] - L["KH"]) // L["stride"] + 1
+            tot["flop"] += 2.0 * b * oh * oh * L["F"] * L["KH"] * L["KW"] * L["C"]
+        tot["model_regret"] = tot["model_top5_ms"] / tot["exhaustive_ms"] - 1
+        tot["default_regret"] = tot["default_ms"] / tot["exhaustive_ms"] - 1
+        tot["model_tflops"] = tot["flop"] / (tot["model_top5_ms"] * 1e-3) / 1e12
+        tot["schedules_timed"] = timed
+        out[f"batch{b}"] = tot
+    nt.nk_tune_release()
+    return out
 
 
 def main():
@@ -155,6 +370,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--no-check", action="store_true", help="skip the sampled accuracy check")
+    ap.add_argument("--no-extra", action="store_true", help="skip the grouped / conv / ResNet reports")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -169,7 +385,8 @@ def main():
     import torch.distributed as dist
 
     import paper_2307_16080_gb300.nk as nk
-    from paper_2307_16080_gb300 import synth
+    from paper_2307_16080_gb300 import nk_tune as nt
+    from paper_2307_16080_gb300 import shard, synth
 
     torch.cuda.set_device(local)
     if world > 1:
@@ -182,7 +399,7 @@ def main():
         torch.cuda.synchronize()
 
     n = args.n
-    A, B = synth.matmul_outlier(n, n, n)            # same problem on every rank (weak scaling)
+    A, B = synth.matmul_outlier(n, n, n)            # one independent problem per rank (weak scaling)
     a32 = torch.from_numpy(A).to(dev)
     b32 = torch.from_numpy(B).to(dev)
     c = torch.empty(n, n, device=dev)
@@ -190,6 +407,7 @@ def main():
     bt16 = torch.empty(n, n, dtype=torch.bfloat16, device=dev)   # B^T, K-major
     st = torch.cuda.current_stream()
     ws = nk.workspace(nk.nk_matmul_workspace_size(a16, bt16.t(), c, "bf16"), dev)
+    sched = nt.nk_default_schedule(nt.matmul_problem(n, n, n, "bf16"))
 
     def step(ev_k=None):
         nk.nk_cast_bf16(a32, a16)
@@ -207,7 +425,7 @@ def main():
     clocks = ClockSampler(local)
     barrier()
     clocks.start()
-    time.sleep(0.3)
+    time.sleep(0.2)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     e0.record(st)
@@ -217,94 +435,34 @@ def main():
     barrier()
     clk = clocks.stop()
     nk.nk_sync_status()
-    ms = e0.elapsed_time(e1)
+    ms = shard.max_over_ranks(e0.elapsed_time(e1))
     kern_ms = sum(a.elapsed_time(b) for a, b in kev) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     flop = 2.0 * n * n * n
     value = flop * args.steps * world / (ms * 1e-3) / 1e12
-    ms_step = ms / args.steps
+    kern_tflops = flop / (kern_ms * 1e-3) / 1e12
 
-    # accuracy of this run's output on sampled rows (device FP64 norm vs host oracle rows)
-    extra = {}
+    accuracy = {}
     if rank == 0 and not args.no_check:
         import oracle.nk_oracle as O
         rows = np.sort(synth.raw_u64(77, 1, 32) % np.uint64(n)).astype(np.int64)
         got = c[torch.from_numpy(rows).to(dev)].cpu().numpy()
-        extra["err_vs_bf16_inputs_sampled"] = O.rel_frobenius(got, O.matmul(O.bf16_rn(A[rows]), O.bf16_rn(B)))
-        extra["err_vs_fp32_inputs_sampled"] = O.rel_frobenius(got, O.matmul(A[rows], B))
+        accuracy["err_vs_bf16_inputs_sampled"] = O.rel_frobenius(got, O.matmul(O.bf16_rn(A[rows]), O.bf16_rn(B)))
+        accuracy["err_vs_fp32_inputs_sampled"] = O.rel_frobenius(got, O.matmul(A[rows], B))
+        accuracy["rows"] = len(rows)
 
-    # precision sweep: GEMM kernel time per precision (operands already prepared)
-    sweep = {}
-    if not args.no_sweep:
-        def time_it(fn, reps):
-            for _ in range(2):
-                fn()
-            torch.cuda.synchronize()
-            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            s0.record(st)
-            for _ in range(reps):
-                fn()
-            s1.record(st)
-            torch.cuda.synchronize()
-            return s0.elapsed_time(s1) / reps
-        sweep["bf16"] = flop / (kern_ms * 1e-3) / 1e12
-        amax = torch.empty(2, device=dev)
-        nk.nk_amax(a32, amax[0:1])
-        nk.nk_amax(b32, amax[1:2])
-        sc = torch.empty(2, device=dev)
-        a8 = torch.empty(n, n, dtype=torch.uint8, device=dev)
-        bt8 = torch.empty(n, n, dtype=torch.uint8, device=dev)
-        nk.nk_cast_fp8(a32, amax[0:1], a8, scale_out=sc[0:1])
-        nk.nk_cast_fp8(b32, amax[1:2], bt8, transpose=True, scale_out=sc[1:2])
-        torch.cuda.synchronize()
-        sa, sb = float(sc[0].item()), float(sc[1].item())
-        ws8 = nk.workspace(nk.nk_matmul_workspace_size(a8, bt8.t(), c, "fp8"), dev)
-        t8 = time_it(lambda: nk.nk_matmul(a8, bt8.t(), c, precision="fp8", scale_a=sa, scale_b=sb, ws=ws8), 10)
-        sweep["fp8"] = flop / (t8 * 1e-3) / 1e12
-        del a8, bt8
-        wsx = nk.workspace(nk.nk_matmul_workspace_size(a32, b32, c, "bf16x3"), dev)
-        tx = time_it(lambda: nk.nk_matmul(a32, b32, c, precision="bf16x3", ws=wsx), 5)
-        sweep["bf16x3_with_prep"] = flop / (tx * 1e-3) / 1e12
-        del wsx
-        wsf = nk.workspace(nk.nk_matmul_workspace_size(a32, b32, c, "f32"), dev)
-        tf = time_it(lambda: nk.nk_matmul(a32, b32, c, precision="f32", ws=wsf), 2)
-        sweep["f32"] = flop / (tf * 1e-3) / 1e12
-        sweep["bf16_over_f32"] = sweep["bf16"] / sweep["f32"]
-        sweep["fp8_over_f32"] = sweep["fp8"] / sweep["f32"]
-        sweep["unit"] = "TFLOP/s (GEMM kernel; bf16x3 includes its split pass)"
-        nk.nk_sync_status()
-
-    # end to end through the public API: pinned host FP32 in, host FP32 C out
+    sweep = None if args.no_sweep else sweep_report(torch, nk, dev, a32, b32, c, flop, kern_tflops)
     e2e = None
     if not args.no_e2e:
-        a_h = torch.from_numpy(A).pin_memory()
-        b_h = torch.from_numpy(B).pin_memory()
-        c_h = torch.empty(n, n).pin_memory()
-
-        def e2e_step():
-            a32.copy_(a_h, non_blocking=True)
-            b32.copy_(b_h, non_blocking=True)
-            step()
-            c_h.copy_(c, non_blocking=True)
-
-        e2e_step()
-        torch.cuda.synchronize()
-        e2e_reps = max(3, args.steps // 4)
-        barrier()
-        t0 = time.perf_counter()
-        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        f0.record(st)
-        for _ in range(e2e_reps):
-            e2e_step()
-        f1.record(st)
-        barrier()
-        e2e_ms = max(f0.elapsed_time(f1), (time.perf_counter() - t0) * 1e3) / e2e_reps
-        nk.nk_sync_status()
-        e2e = {"value": flop / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
-               "h2d_bytes_per_step": 2 * n * n * 4, "d2h_bytes_per_step": n * n * 4}
+        del a32, b32
+        torch.cuda.empty_cache()
+        e2e = e2e_report(torch, nk, dev, A, B, max(4, args.steps // 2))
+    extra = {}
+    if not args.no_extra and rank == 0:
+        extra["grouped_512_bf16"] = grouped_report(torch, nk, synth, dev)
+        extra["conv_8x56x56x64_3x3"] = conv_report(torch, nk, synth, dev)
+        rr = resnet_report(torch, synth, dev)
+        if rr is not None:
+            extra["resnet_stack_bf16"] = rr
 
     if rank != 0:
         if world > 1:
@@ -312,7 +470,6 @@ def main():
             dist.destroy_process_group()
         return
     bf16_peak, _, src = peaks()
-    kern_tflops = flop / (kern_ms * 1e-3) / 1e12
     line = {
         "metric": METRIC,
         "value": value,
@@ -320,7 +477,7 @@ def main():
         "n_gpus": world,
         "steps": args.steps,
         "warmup": args.warmup,
-        "ms_per_step": ms_step,
+        "ms_per_step": ms / args.steps,
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
@@ -328,17 +485,21 @@ def main():
         "data": "synthetic",
         "config": {"workload": f"linalg.matmul precision sweep, BF16 in / FP32 accumulate, M=N=K={n}",
                    "inputs": "A, B ~ N(0,1) with 1% of entries x100 (SplitMix64 seed 3)",
-                   "step": "cast A, cast+transpose B to BF16, tcgen05 GEMM (FP32 out)",
+                   "step": "cast A, cast+transpose B to BF16, tcgen05 GEMM (FP32 out), one nk_* call each",
+                   "schedule": {"tile_m": sched[0], "tile_n": sched[1], "tile_k": sched[2], "cluster": sched[3],
+                                "stages": sched[4], "split_k": sched[5]},
                    "l2": "inputs larger than L2 (268 MB FP32 per operand); no flush"},
         "roofline": {"bound": "tensor", "achieved": kern_tflops, "peak": bf16_peak, "unit": "TFLOP/s",
-                     "frac": kern_tflops / bf16_peak, "traffic": None,
-                     "kernel": "tc_gemm_kernel<BF16,1>", "peak_source": f"{src} bf16 burst"},
+                     "frac": kern_tflops / bf16_peak, "traffic": recorded_traffic("tc_gemm_bf16_8192"),
+                     "kernel": "tc_gemm_kernel (BF16)", "peak_source": f"{src} bf16 burst (MEASURED_PEAKS.json)",
+                     "algorithmic_flop_per_launch": flop},
         "gpu_launches": 3 * args.steps,
         "clocks": clk,
         "e2e": e2e,
         "sweep": sweep,
-        "accuracy": extra,
+        "accuracy": accuracy,
     }
+    line.update(extra)
     if world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(A, B, args.cpu_rows)
     print(json.dumps(line), flush=True)

@@ -626,6 +626,12 @@ nk_schedule tc_default_schedule(int kind, int M, int N, int K, int sms) {
   s.cluster = 1;
   s.stages = 2;
   while (s.stages < 8 && smem_bytes(kind, s.tile_n, s.stages + 1) <= kMaxSmem) ++s.stages;
+  // Large BF16 / FP8 problems: wide pair tiles (256 x 512, two MMA chains)
+  // when there are at least two waves of them.
+  if (kind != TC_BF16X3 && (int64_t)((M + 255) / 256) * ((N + 511) / 512) >= sms) {
+    s.tile_m = 256; s.tile_n = 512; s.cluster = 2; s.stages = 4; s.split_k = 1;
+    return s;
+  }
   // Split K when the output tiles cannot fill the GPU and K is deep.
   const int tiles = ((M + 127) / 128) * ((N + s.tile_n - 1) / s.tile_n);
   const int nkb = (K + s.tile_k - 1) / s.tile_k;
