@@ -326,7 +326,8 @@ def conv_report(torch, nk, synth, dev):
 def resnet_report(torch, synth, dev):
     """The 20-layer ResNet-style stack (BF16 conv, tensor cores) at batch 1,
     8, 32: total time with the built-in default schedules, with the cost
-    model's top-5 (timed) pick, and with exhaustive search."""
+    model's top-5 (timed) pick, with the derivative-free (1+1) evolution
+    strategy on the same budget of 5 timings, and with exhaustive search."""
     from paper_2307_16080_gb300 import costmodel
     from paper_2307_16080_gb300 import nk_tune as nt
     if not os.path.exists(costmodel.MODEL_PATH):
@@ -335,21 +336,25 @@ def resnet_report(torch, synth, dev):
     P = torch.from_numpy(params).to(dev)
     out = {}
     for b in (1, 8, 32):
-        tot = {"default_ms": 0.0, "model_top5_ms": 0.0, "exhaustive_ms": 0.0, "flop": 0.0}
-        timed = {"model": 0, "exhaustive": 0}
+        tot = {"default_ms": 0.0, "model_top5_ms": 0.0, "evolution5_ms": 0.0, "exhaustive_ms": 0.0, "flop": 0.0}
+        timed = {"model": 0, "evolution": 0, "exhaustive": 0}
         for L in synth.resnet_stack(b):
             p = nt.conv_problem(L["N"], L["H"], L["W"], L["C"], L["F"], L["KH"], L["KW"], L["stride"], L["pad"])
             _, ex = nt.nk_tune(p, nt.NK_TUNE_EXHAUSTIVE, reps=3)
             _, mo = nt.nk_tune(p, nt.NK_TUNE_MODEL_TOPK, topk=5, params=P, reps=3)
+            _, es = nt.nk_tune(p, nt.NK_TUNE_EVOLUTION, topk=5, reps=3)
             tot["default_ms"] += ex.default_ms
             tot["exhaustive_ms"] += ex.best_ms
             tot["model_top5_ms"] += mo.best_ms
+            tot["evolution5_ms"] += es.best_ms
             timed["model"] += mo.timed
+            timed["evolution"] += es.timed
             timed["exhaustive"] += ex.timed
             oh = (L["H"] + 2 * L["pad"] - L["KH"]) // L["stride"] + 1
             tot["flop"] += 2.0 * b * oh * oh * L["F"] * L["KH"] * L["KW"] * L["C"]
         tot["model_regret"] = tot["model_top5_ms"] / tot["exhaustive_ms"] - 1
         tot["default_regret"] = tot["default_ms"] / tot["exhaustive_ms"] - 1
+        tot["evolution_regret"] = tot["evolution5_ms"] / tot["exhaustive_ms"] - 1
         tot["model_tflops"] = tot["flop"] / (tot["model_top5_ms"] * 1e-3) / 1e12
         tot["schedules_timed"] = timed
         out[f"batch{b}"] = tot

@@ -186,6 +186,21 @@ nk_status nk_conv2d_workspace_size(const nk_tensor* I, const nk_tensor* W,
                                    const int64_t pad[4], int32_t precision,
                                    const nk_schedule* sched, size_t* bytes);
 
+/* The convolution exactly as Sec. 4.1 Listing "2dnchwconv" lays it out:
+ * I: [N,CI,H,W] (NCHW), K: [CO,CI,KH,KW] (FCHW, contiguous), O: [N,CO,OH,OW],
+ * all FP32 with unit stride along W;
+ *   O[n,co,ho,wo] = ReLU?(beta*O + bias[co] + sum_{ci,ki,kj}
+ *        I[n,ci,ho*sh+ki*dh-pt, wo*sw+kj*dw-pl] * K[co,ci,ki,kj])
+ * (zero padding).  A direct, output-parallel kernel for few channels (the
+ * tuning experiment of Sec. 4.3 uses CI=1, CO=3, 3x3 on 1280x1280), bound by
+ * HBM rather than by the tensor cores.  Limits: at most 64 filter taps and a
+ * halo tile of 64 x 176 input elements per 16 x 64 output tile
+ * (NK_ERR_UNSUPPORTED beyond).  Allocates nothing.                          */
+nk_status nk_conv2d_nchw_fchw(const nk_tensor* I, const nk_tensor* K,
+                              nk_tensor* O, const int64_t stride[2],
+                              const int64_t dilation[2], const int64_t pad[4],
+                              const nk_epilogue* epi, void* stream);
+
 /* --------------------------------------------------------- operand prep */
 
 /* amax = max |x| over n FP32 values, written as one float to `amax` (device).

@@ -19,7 +19,12 @@ extern "C" {
 #endif
 
 typedef enum { NK_OP_MATMUL = 0, NK_OP_CONV2D = 1 } nk_op;
-typedef enum { NK_TUNE_EXHAUSTIVE = 0, NK_TUNE_MODEL_TOPK = 1 } nk_tune_mode;
+/* EXHAUSTIVE: time every legal schedule.  MODEL_TOPK: rank all with the cost
+ * model, time the top `topk`.  EVOLUTION: a derivative-free (1+1) evolution
+ * strategy over the schedule grid -- the black-box search of Sec. 4.3 --
+ * started from the built-in default, `topk` timings in all (mlp_params are
+ * not used).                                                               */
+typedef enum { NK_TUNE_EXHAUSTIVE = 0, NK_TUNE_MODEL_TOPK = 1, NK_TUNE_EVOLUTION = 2 } nk_tune_mode;
 
 /* A tensor-core problem: matmul (M, N, K) or conv (n, h, w, c -> f with a
  * kh x kw filter, equal stride and padding on both axes, dilation 1).

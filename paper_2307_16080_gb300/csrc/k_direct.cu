@@ -1,0 +1,170 @@
+// k_direct.cu -- the convolution of Sec. 4.1 Listing "2dnchwconv" as written:
+// NCHW input, FCHW kernel, output-parallel,
+//   out[n,co,ho,wo] += in[n, ci, ho*sh + ki*dh - pt, wo*sw + kj*dw - pl] * ker[co,ci,ki,kj]
+// (stride 1, no padding in the listing; stride, dilation and zero padding
+// here).  With a handful of channels -- the tuning experiment of Sec. 4.3
+// uses (N, C, H, W) = (1, 1, 1280, 1280) and (Ci, Co, K) = (1, 3, 3) -- the
+// contraction is far too short for tensor cores and the kernel is bound by
+// HBM: each input element is read once through a shared-memory halo tile,
+// each output element written once with 128-bit stores.
+//
+// A CTA computes a 16 x 64 output tile of one image for up to 8 output
+// channels; each thread owns 4 consecutive output columns of one row for
+// every channel of the group.  Input channels stream through shared memory
+// one at a time, with the group's filter taps for that channel beside them.
+#include <cuda_runtime.h>
+
+#include "nk_internal.cuh"
+
+namespace nk {
+namespace {
+
+constexpr int TH = 16, TW = 64, CO_G = 8, THREADS = 256;
+constexpr int MAX_IN_H = 64, MAX_IN_W = 176;   // halo tile limits: 44 KB of the 48 KB static shared memory
+
+struct Direct {
+  const float* I;
+  int64_t sIn, sIc, sIh;   // input strides (width stride 1)
+  const float* Kr;         // FCHW, contiguous
+  float* O;
+  int64_t sOn, sOc, sOh;   // output strides (width stride 1)
+  int N, CI, H, W, CO, KH, KW, OH, OW;
+  int sh, sw, dh, dw, pt, pl;
+  const float* bias;
+  int relu;
+  float beta;
+  int in_h, in_w;          // halo tile extent
+};
+
+__global__ void __launch_bounds__(THREADS) direct_conv_kernel(Direct p) {
+  __shared__ float tile[MAX_IN_H * MAX_IN_W];
+  __shared__ float ker[CO_G * 64];   // taps of one input channel for the channel group (<= 64 taps)
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int wo0 = blockIdx.x * TW, ho0 = blockIdx.y * TH;
+  const int n = blockIdx.z / ((p.CO + CO_G - 1) / CO_G);
+  const int cg = blockIdx.z % ((p.CO + CO_G - 1) / CO_G);
+  const int co0 = cg * CO_G;
+  const int ncog = min(CO_G, p.CO - co0);
+  const int ho = ho0 + ty;
+  const int wo = wo0 + tx * 4;
+  const int taps = p.KH * p.KW;
+  const int ih0 = ho0 * p.sh - p.pt, iw0 = wo0 * p.sw - p.pl;
+  float acc[CO_G][4];
+#pragma unroll
+  for (int c = 0; c < CO_G; ++c)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[c][j] = 0.f;
+
+  for (int ci = 0; ci < p.CI; ++ci) {
+    __syncthreads();
+    const float* src = p.I + n * p.sIn + ci * p.sIc;
+    for (int e = threadIdx.x; e < p.in_h * p.in_w; e += THREADS) {
+      const int r = e / p.in_w, c = e % p.in_w;
+      const int ih = ih0 + r, iw = iw0 + c;
+      tile[e] = (ih >= 0 && ih < p.H && iw >= 0 && iw < p.W) ? __ldg(src + ih * p.sIh + iw) : 0.f;
+    }
+    for (int e = threadIdx.x; e < ncog * taps; e += THREADS) {
+      const int c = e / taps, t = e % taps;
+      ker[c * 64 + t] = __ldg(p.Kr + ((int64_t)(co0 + c) * p.CI + ci) * taps + t);
+    }
+    __syncthreads();
+    for (int ki = 0; ki < p.KH; ++ki) {
+      const int r = ty * p.sh + ki * p.dh;
+      for (int kj = 0; kj < p.KW; ++kj) {
+        float x[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) x[j] = tile[r * p.in_w + (tx * 4 + j) * p.sw + kj * p.dw];
+        const int t = ki * p.KW + kj;
+#pragma unroll
+        for (int c = 0; c < CO_G; ++c) {
+          if (c < ncog) {
+            const float w = ker[c * 64 + t];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[c][j] = fmaf(x[j], w, acc[c][j]);
+          }
+        }
+      }
+    }
+  }
+  if (ho >= p.OH) return;
+#pragma unroll
+  for (int c = 0; c < CO_G; ++c) {
+    if (c >= ncog) break;
+    float* dst = p.O + n * p.sOn + (int64_t)(co0 + c) * p.sOc + (int64_t)ho * p.sOh + wo;
+    const float b = p.bias ? p.bias[co0 + c] : 0.f;
+    float v[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      float o = acc[c][j];
+      if (p.beta != 0.f && wo + j < p.OW) o = fmaf(p.beta, dst[j], o);
+      o += b;
+      if (p.relu) o = (o > 0.f || o != o) ? o : 0.f;
+      v[j] = o;
+    }
+    if (wo + 3 < p.OW && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
+      *reinterpret_cast<float4*>(dst) = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (wo + j < p.OW) dst[j] = v[j];
+    }
+  }
+}
+
+}  // namespace
+}  // namespace nk
+
+using namespace nk;
+
+extern "C" nk_status nk_conv2d_nchw_fchw(const nk_tensor* I, const nk_tensor* K, nk_tensor* O,
+                                         const int64_t stride[2], const int64_t dilation[2],
+                                         const int64_t pad[4], const nk_epilogue* epi, void* stream) {
+  nk_status s = require_device();
+  if (s != NK_OK) return s;
+  if (!I || !K || !O || !stride || !dilation || !pad) return fail(NK_ERR_INVALID_ARG, "null argument");
+  if (I->rank != 4 || K->rank != 4 || O->rank != 4) return fail(NK_ERR_INVALID_ARG, "I, K, O must have rank 4");
+  if (I->dtype != NK_F32 || K->dtype != NK_F32 || O->dtype != NK_F32)
+    return fail(NK_ERR_UNSUPPORTED, "the direct NCHW convolution is FP32");
+  if (I->stride[3] != 1 || O->stride[3] != 1) return fail(NK_ERR_UNSUPPORTED, "width must have unit stride");
+  const int64_t taps = K->shape[2] * K->shape[3];
+  if (K->stride[3] != 1 || K->stride[2] != K->shape[3] || K->stride[1] != taps ||
+      K->stride[0] != K->shape[1] * taps)
+    return fail(NK_ERR_UNSUPPORTED, "the kernel must be contiguous FCHW");
+  if (I->shape[1] != K->shape[1]) return fail(NK_ERR_INVALID_ARG, "input channels differ from the kernel's");
+  for (int i = 0; i < 2; ++i)
+    if (stride[i] < 1 || dilation[i] < 1) return fail(NK_ERR_INVALID_ARG, "stride and dilation must be >= 1");
+  for (int i = 0; i < 4; ++i)
+    if (pad[i] < 0) return fail(NK_ERR_INVALID_ARG, "padding must be >= 0");
+  Direct p{};
+  p.N = (int)I->shape[0]; p.CI = (int)I->shape[1]; p.H = (int)I->shape[2]; p.W = (int)I->shape[3];
+  p.CO = (int)K->shape[0]; p.KH = (int)K->shape[2]; p.KW = (int)K->shape[3];
+  p.sh = (int)stride[0]; p.sw = (int)stride[1]; p.dh = (int)dilation[0]; p.dw = (int)dilation[1];
+  p.pt = (int)pad[0]; p.pl = (int)pad[2];
+  const int64_t oh = (p.H + pad[0] + pad[1] - p.dh * (p.KH - 1) - 1) / p.sh + 1;
+  const int64_t ow = (p.W + pad[2] + pad[3] - p.dw * (p.KW - 1) - 1) / p.sw + 1;
+  if (oh < 1 || ow < 1) return fail(NK_ERR_INVALID_ARG, "empty output");
+  if (O->shape[0] != p.N || O->shape[1] != p.CO || O->shape[2] != oh || O->shape[3] != ow)
+    return fail(NK_ERR_INVALID_ARG, "O must be [%d,%d,%lld,%lld]", p.N, p.CO, (long long)oh, (long long)ow);
+  p.OH = (int)oh; p.OW = (int)ow;
+  if (taps > 64) return fail(NK_ERR_UNSUPPORTED, "more than 64 filter taps");
+  p.in_h = (TH - 1) * p.sh + (p.KH - 1) * p.dh + 1;
+  p.in_w = (TW - 1) * p.sw + (p.KW - 1) * p.dw + 1;
+  if (p.in_h > MAX_IN_H || p.in_w > MAX_IN_W)
+    return fail(NK_ERR_UNSUPPORTED, "stride/dilation/filter too large for the direct kernel's halo tile");
+  p.I = static_cast<const float*>(I->ptr);
+  p.sIn = I->stride[0]; p.sIc = I->stride[1]; p.sIh = I->stride[2];
+  p.Kr = static_cast<const float*>(K->ptr);
+  p.O = static_cast<float*>(O->ptr);
+  p.sOn = O->stride[0]; p.sOc = O->stride[1]; p.sOh = O->stride[2];
+  const nk_epilogue e0{nullptr, 0, 0, 1.f, 1.f};
+  const nk_epilogue& E = epi ? *epi : e0;
+  p.bias = E.bias;
+  p.relu = E.relu;
+  p.beta = E.accumulate ? 1.f : 0.f;
+  const int groups = (p.CO + CO_G - 1) / CO_G;
+  if ((int64_t)p.N * groups > 65535) return fail(NK_ERR_UNSUPPORTED, "batch x channel groups too large");
+  dim3 grid((unsigned)((p.OW + TW - 1) / TW), (unsigned)((p.OH + TH - 1) / TH), (unsigned)(p.N * groups));
+  if (grid.y > 65535) return fail(NK_ERR_UNSUPPORTED, "output too tall");
+  direct_conv_kernel<<<grid, THREADS, 0, static_cast<cudaStream_t>(stream)>>>(p);
+  return check_launch("direct_conv_kernel");
+}

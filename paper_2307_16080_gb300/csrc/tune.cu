@@ -262,6 +262,93 @@ nk_status time_one(const nk_problem* p, const nk_schedule& s, int reps, float* m
   return NK_OK;
 }
 
+// (1+1) evolution strategy on the schedule grid.  Coordinates: tile_m,
+// tile_n, cluster, stages, split_k, each an ordered list of levels.  A child
+// moves one coordinate one level (or, with probability 1/4, to a random
+// level); illegal or already-timed children are redrawn; the child replaces
+// the parent when it is faster.  SplitMix64 seeded from the problem, so the
+// search is repeatable.  `budget` timings in all, the start included.
+struct Rng {
+  uint64_t s;
+  uint64_t next() {
+    uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  }
+  int below(int n) { return (int)(next() % (uint64_t)n); }
+};
+
+nk_status evolve(const nk_problem* p, const std::vector<nk_schedule>& cand, int budget, int reps,
+                 cudaStream_t cs, int* best_i, float* best_ms) {
+  static const int L_TM[] = {128, 256}, L_TN[] = {64, 128, 256, 512}, L_CL[] = {1, 2},
+                   L_ST[] = {2, 3, 4, 5, 6, 7, 8}, L_SK[] = {1, 2, 4, 8, 16};
+  static const int* LV[5] = {L_TM, L_TN, L_CL, L_ST, L_SK};
+  static const int NL[5] = {2, 4, 2, 7, 5};
+  auto level_of = [&](int c, int v) {
+    for (int i = 0; i < NL[c]; ++i)
+      if (LV[c][i] == v) return i;
+    return 0;
+  };
+  auto find = [&](const int* lv) -> int {
+    for (size_t i = 0; i < cand.size(); ++i) {
+      const nk_schedule& s = cand[i];
+      if (s.tile_m == LV[0][lv[0]] && s.tile_n == LV[1][lv[1]] && s.cluster == LV[2][lv[2]] &&
+          s.stages == LV[3][lv[3]] && s.split_k == LV[4][lv[4]])
+        return (int)i;
+    }
+    return -1;
+  };
+  Rng rng{(uint64_t)p->op * 1000003ull ^ (uint64_t)p->M * 7919ull ^ (uint64_t)p->N * 104729ull ^
+          (uint64_t)p->K * 1299709ull ^ (uint64_t)p->n * 15485863ull ^ (uint64_t)p->h * 32452843ull ^
+          (uint64_t)p->c * 49979687ull ^ (uint64_t)p->f * 67867967ull ^ (uint64_t)p->kh * 86028121ull ^
+          (uint64_t)p->stride * 104395301ull ^ (uint64_t)p->precision};
+  std::vector<char> seen(cand.size(), 0);
+  const nk_schedule d = default_of(p, sm_count());
+  int cur = -1;
+  for (size_t i = 0; i < cand.size(); ++i)
+    if (cand[i].tile_m == d.tile_m && cand[i].tile_n == d.tile_n && cand[i].cluster == d.cluster &&
+        cand[i].stages == d.stages && cand[i].split_k == d.split_k)
+      cur = (int)i;
+  if (cur < 0) cur = 0;
+  float cur_ms = 0.f;
+  nk_status st = time_one(p, cand[cur], reps, &cur_ms, cs);
+  if (st != NK_OK) return st;
+  seen[cur] = 1;
+  int timed = 1;
+  const int limit = budget < (int)cand.size() ? budget : (int)cand.size();
+  while (timed < limit) {
+    int lv[5];
+    const nk_schedule& s = cand[cur];
+    const int base[5] = {level_of(0, s.tile_m), level_of(1, s.tile_n), level_of(2, s.cluster),
+                         level_of(3, s.stages), level_of(4, s.split_k)};
+    int child = -1;
+    for (int tries = 0; tries < 64 && child < 0; ++tries) {
+      for (int c = 0; c < 5; ++c) lv[c] = base[c];
+      const int c = rng.below(5);
+      if (rng.below(4) == 0) lv[c] = rng.below(NL[c]);
+      else lv[c] = lv[c] + (rng.below(2) ? 1 : -1);
+      if (lv[c] < 0 || lv[c] >= NL[c]) continue;
+      const int i = find(lv);
+      if (i >= 0 && !seen[i]) child = i;
+    }
+    if (child < 0) {   // the neighbourhood is exhausted: any untimed candidate
+      int k = rng.below((int)cand.size());
+      for (size_t j = 0; j < cand.size() && seen[k]; ++j) k = (k + 1) % (int)cand.size();
+      if (seen[k]) break;
+      child = k;
+    }
+    float ms = 0.f;
+    if ((st = time_one(p, cand[child], reps, &ms, cs)) != NK_OK) return st;
+    seen[child] = 1;
+    ++timed;
+    if (ms < cur_ms) { cur = child; cur_ms = ms; }
+  }
+  *best_i = cur;
+  *best_ms = cur_ms;
+  return NK_OK;
+}
+
 }  // namespace
 }  // namespace nk
 
@@ -321,12 +408,32 @@ nk_status nk_tune(const nk_problem* p, int32_t mode, int32_t topk, const float* 
   if (st != NK_OK) return st;
   if ((st = require_device()) != NK_OK) return st;
   if (!best) return fail(NK_ERR_INVALID_ARG, "best is NULL");
-  if (mode != NK_TUNE_EXHAUSTIVE && mode != NK_TUNE_MODEL_TOPK) return fail(NK_ERR_INVALID_ARG, "unknown mode");
+  if (mode != NK_TUNE_EXHAUSTIVE && mode != NK_TUNE_MODEL_TOPK && mode != NK_TUNE_EVOLUTION)
+    return fail(NK_ERR_INVALID_ARG, "unknown mode");
   if (mode == NK_TUNE_MODEL_TOPK && (!mlp_params || topk < 1))
     return fail(NK_ERR_INVALID_ARG, "model mode needs parameters and topk >= 1");
+  if (mode == NK_TUNE_EVOLUTION && topk < 1) return fail(NK_ERR_INVALID_ARG, "evolution needs a budget >= 1");
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
   const auto cand = enumerate(p);
   if (cand.empty()) return fail(NK_ERR_NO_SCHEDULE, "no legal schedule");
+  if (mode == NK_TUNE_EVOLUTION) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    int bi = 0;
+    float bms = 0.f;
+    st = evolve(p, cand, topk, reps, cs, &bi, &bms);
+    if (st != NK_OK) return st;
+    *best = cand[bi];
+    if (rep) {
+      rep->candidates = (int32_t)cand.size();
+      rep->timed = topk < (int)cand.size() ? topk : (int32_t)cand.size();
+      rep->best_ms = bms;
+      float dms = 0.f;
+      st = time_one(p, default_of(p, sm_count()), reps, &dms, cs);
+      if (st != NK_OK) return st;
+      rep->default_ms = dms;
+    }
+    return NK_OK;
+  }
   std::vector<int> order(cand.size());
   for (size_t i = 0; i < cand.size(); ++i) order[i] = (int)i;
   if (mode == NK_TUNE_MODEL_TOPK) {

@@ -73,6 +73,8 @@ SIGNATURES = {
                                    ctypes.POINTER(_I64), _I32, _PE, _PS, _P, _SZ, _P]),
     "nk_conv2d_workspace_size": (_I32, [_PT, _PT, _PT, ctypes.POINTER(_I64), ctypes.POINTER(_I64),
                                         ctypes.POINTER(_I64), _I32, _PS, ctypes.POINTER(_SZ)]),
+    "nk_conv2d_nchw_fchw": (_I32, [_PT, _PT, _PT, ctypes.POINTER(_I64), ctypes.POINTER(_I64),
+                                   ctypes.POINTER(_I64), _PE, _P]),
     "nk_amax": (_I32, [_P, _I64, _P, _P, _SZ, _P]),
     "nk_prep_workspace_size": (_SZ, [_I64]),
     "nk_cast_bf16": (_I32, [_P, _I64, _I64, _I64, _P, _I64, _I32, _P]),
@@ -211,6 +213,17 @@ def nk_conv2d_nhwc_hwcf(I, W, O, stride=(1, 1), dilation=(1, 1), pad=(0, 0, 0, 0
                                      PREC[precision], ctypes.byref(e), _sched(schedule),
                                      ws.data_ptr() if ws is not None else None,
                                      ws.numel() if ws is not None else 0, _stream(stream)))
+    return O
+
+
+def nk_conv2d_nchw_fchw(I, K, O, stride=(1, 1), dilation=(1, 1), pad=(0, 0, 0, 0), bias=None, relu=False,
+                        accumulate=False, stream=None):
+    """Direct NCHW / FCHW convolution (Listing "2dnchwconv" layout)."""
+    ti, tk, to = as_nk_tensor(I), as_nk_tensor(K), as_nk_tensor(O)
+    st, dl, pd = _conv_args(stride, dilation, pad)
+    e = _epi(bias, relu, accumulate, 1.0, 1.0)
+    _check(lib().nk_conv2d_nchw_fchw(ctypes.byref(ti), ctypes.byref(tk), ctypes.byref(to), st, dl, pd,
+                                     ctypes.byref(e), _stream(stream)))
     return O
 
 

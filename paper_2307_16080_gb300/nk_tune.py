@@ -11,7 +11,7 @@ from . import nk
 from .nk import _I32, _I64, _P, _SZ, _check, _stream, nk_schedule
 
 NK_OP_MATMUL, NK_OP_CONV2D = 0, 1
-NK_TUNE_EXHAUSTIVE, NK_TUNE_MODEL_TOPK = 0, 1
+NK_TUNE_EXHAUSTIVE, NK_TUNE_MODEL_TOPK, NK_TUNE_EVOLUTION = 0, 1, 2
 NK_TUNE_FEATURES = 16
 
 

@@ -150,3 +150,16 @@ def test_shipped_model_regret_on_stored_heldout(nt):
     assert s["stack_model_regret"] <= 0.05, s
     assert s["mean_model_regret"] < s["mean_random_regret"], s
     assert s["mean_model_regret"] < s["mean_default_regret"], s
+
+
+def test_evolution_search_respects_budget_and_improves_on_default(nt):
+    """The derivative-free (1+1) evolution strategy (the black-box search of
+    Sec. 4.3): exactly `budget` timings, repeatable, never worse than the
+    start it was given (the default schedule, timed first)."""
+    p = nt.conv_problem(8, 28, 28, 128, 128, 3, 3, 1, 1)
+    b1, r1 = nt.nk_tune(p, nt.NK_TUNE_EVOLUTION, topk=12, reps=3)
+    b2, r2 = nt.nk_tune(p, nt.NK_TUNE_EVOLUTION, topk=12, reps=3)
+    assert r1.timed == 12 and r2.timed == 12 and r1.candidates > 12
+    assert r1.best_ms <= r1.default_ms * 1.10
+    _, ex = nt.nk_tune(p, nt.NK_TUNE_EXHAUSTIVE, reps=3)
+    assert ex.best_ms <= r1.best_ms * 1.10
