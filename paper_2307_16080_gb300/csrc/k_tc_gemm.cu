@@ -91,7 +91,14 @@ struct TcParams {
   // implicit-GEMM convolution (tmA: 4-D NHWC input map, tmB: 3-D [F][taps][C] map)
   ConvTile cv;
   uint32_t a_box_bytes;         // bytes TMA writes per A stage (16 KB unless a conv tile is short)
+  // epilogue through shared memory and TMA stores (plain GEMM, beta = 0, one K slice)
+  CUtensorMap tmC;
+  int c_tma;
 };
+
+// Epilogue staging: one 32 x 32 FP32 box (4 KB, 128B-swizzled) per epilogue warp.
+constexpr int kStageBox = 4096;
+__host__ __device__ inline int staging_bytes(bool wide) { return (wide ? 8 : 4) * kStageBox; }
 
 struct GroupDesc {
   int M, N, K, tiles_n;
@@ -212,13 +219,14 @@ __global__ void __launch_bounds__(WIDE ? 320 : 192, 1) tc_gemm_kernel(const __gr
   const int b_rows_smem = PAIR ? p.bn / 2 : p.bn;   // rows of B^T this CTA keeps per stage
   const int sb = stage_bytes(KIND, b_rows_smem);
   const int S = p.stages;
-  const uint32_t bar0 = base + S * sb;   // full[S], empty[S], tfull[2], tempty[2], drain
+  const uint32_t stg0 = base + S * sb;   // epilogue staging boxes
+  const uint32_t bar0 = stg0 + staging_bytes(WIDE);   // full[S], empty[S], tfull[2], tempty[2], drain
   auto full_bar = [&](int s) { return bar0 + 8u * s; };
   auto empty_bar = [&](int s) { return bar0 + 8u * (S + s); };
   auto tfull_bar = [&](int b) { return bar0 + 8u * (2 * S + b); };
   auto tempty_bar = [&](int b) { return bar0 + 8u * (2 * S + 2 + b); };
   const uint32_t drain_bar = bar0 + 8u * (2 * S + 4);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(base_ptr + S * sb + 8 * (2 * S + 5));
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(base_ptr + S * sb + staging_bytes(WIDE) + 8 * (2 * S + 5));
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x / 32;
@@ -452,6 +460,38 @@ __global__ void __launch_bounds__(WIDE ? 320 : 192, 1) tc_gemm_kernel(const __gr
           for (int j = 0; j < 32; ++j) v[j] += w[j];
         }
         const int col0 = t.tn * p.bn + c0;
+        if (!GROUPED && !CONV && p.c_tma) {
+          // Coalesced epilogue: registers -> this warp's 128B-swizzled 32 x 32
+          // staging box -> one TMA store (rows / columns past C are clipped).
+          if (col0 >= t.N) continue;
+          const uint32_t stg = stg0 + (uint32_t)((warp - 2) * kStageBox);
+          if (lane == 0) ptx::bulk_wait_read0();   // the box's previous store has read it
+          __syncwarp();
+          const float bm = (p.bias && p.bias_on_m && row_ok) ? __ldg(p.bias + row) : 0.f;
+#pragma unroll
+          for (int j16 = 0; j16 < 8; ++j16) {
+            float o[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const int j = 4 * j16 + e;
+              float x = alpha * v[j];
+              if (p.bias) x += p.bias_on_m ? bm : (col0 + j < t.N ? __ldg(p.bias + col0 + j) : 0.f);
+              if (p.relu) x = (x > 0.f || x != x) ? x : 0.f;
+              o[e] = x;
+            }
+            const uint32_t addr = stg + (uint32_t)(lane * 128 + ((j16 ^ (lane & 7)) * 16));
+            asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(o[0]), "f"(o[1]), "f"(o[2]),
+                         "f"(o[3])
+                         : "memory");
+          }
+          ptx::fence_proxy_async_smem();
+          __syncwarp();
+          if (lane == 0) {
+            ptx::tma_store_2d(&p.tmC, stg, col0, t.tm * kBM + q * 32);
+            ptx::bulk_commit();
+          }
+          continue;
+        }
         if (!row_ok || col0 >= t.N) continue;
         if (p.partial) {
           float* dst = p.partial + ((int64_t)t.split * p.M + row) * p.N + col0;
@@ -505,6 +545,7 @@ __global__ void __launch_bounds__(WIDE ? 320 : 192, 1) tc_gemm_kernel(const __gr
         else ptx::mbar_arrive(tempty_bar(acc));
       }
     }
+    if (!GROUPED && !CONV && p.c_tma && lane == 0) ptx::bulk_wait0();   // every store has landed
   }
 
   ptx::tc_fence_before();
@@ -555,13 +596,13 @@ nk_status make_kmajor_map(CUtensorMap* m, bool fp8, const void* ptr, int64_t row
   return NK_OK;
 }
 
-int smem_bytes(int kind, int bn, int stages) {
-  return 1024 + stages * stage_bytes(kind, bn) + 8 * (2 * stages + 5) + 16;
+int smem_bytes(int kind, int bn, int stages, bool wide = false) {
+  return 1024 + stages * stage_bytes(kind, bn) + staging_bytes(wide) + 8 * (2 * stages + 5) + 16;
 }
 
 // Shared memory of a schedule: a CTA of a pair (tile_m 256) keeps half of B.
 int smem_of(int kind, const nk_schedule& s) {
-  return smem_bytes(kind, s.tile_m == 256 ? s.tile_n / 2 : s.tile_n, s.stages);
+  return smem_bytes(kind, s.tile_m == 256 ? s.tile_n / 2 : s.tile_n, s.stages, s.tile_n == 512);
 }
 
 template <int KIND, int CL, bool GROUPED = false, bool CONV = false, bool PAIR = false, bool WIDE = false>
@@ -708,6 +749,19 @@ nk_status tc_gemm(const TcGemm& g, const nk_schedule& s, void* ws, size_t ws_byt
   const bool cvec = ((reinterpret_cast<uintptr_t>(g.C) & 15) == 0) && (g.ldc % 4 == 0) &&
                     (splits == 1 || (g.N % 4 == 0 && (reinterpret_cast<uintptr_t>(ws) & 15) == 0));
   p.c_vec = cvec ? 1 : 0;
+  // TMA-store epilogue: plain overwrite of a 16-byte aligned C in one K slice.
+  p.c_tma = 0;
+  if (splits == 1 && g.beta == 0.f && (reinterpret_cast<uintptr_t>(g.C) & 15) == 0 && (g.ldc * 4) % 16 == 0) {
+    auto fn = encode_fn();
+    cuuint64_t dims[2] = {(cuuint64_t)g.N, (cuuint64_t)g.M};
+    cuuint64_t strides[1] = {(cuuint64_t)(g.ldc * 4)};
+    cuuint32_t box[2] = {32, 32};
+    cuuint32_t es[2] = {1, 1};
+    if (fn && fn(&p.tmC, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, g.C, dims, strides, box, es,
+                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
+      p.c_tma = 1;
+  }
   const int smem = smem_of(g.kind, s);
   int grid = sms * ctas_per_sm(g.kind, s);
   grid = grid / CL * CL;
