@@ -308,7 +308,12 @@ size_t prep_amax_ws(int64_t) { return kAmaxBlocks * sizeof(float); }
 
 nk_status prep_amax(const float* x, int64_t rows, int64_t cols, int64_t ld, float* amax, void* ws,
                     size_t ws_bytes, cudaStream_t st) {
-  if (!x || !amax) return fail(NK_ERR_INVALID_ARG, "amax: null pointer");
+  if (!amax) return fail(NK_ERR_INVALID_ARG, "amax: null pointer");
+  if (rows * cols == 0) {   // max over nothing: 0 (the scale then falls back to 1)
+    cudaError_t e = cudaMemsetAsync(amax, 0, sizeof(float), st);
+    return e == cudaSuccess ? NK_OK : cuda_fail(e, "cudaMemsetAsync(amax)");
+  }
+  if (!x) return fail(NK_ERR_INVALID_ARG, "amax: null pointer");
   if (!ws || ws_bytes < prep_amax_ws(rows * cols))
     return fail(NK_ERR_WORKSPACE, "amax needs %zu bytes of workspace", prep_amax_ws(rows * cols));
   amax_stage1<<<kAmaxBlocks, 256, 0, st>>>(x, rows, cols, ld, static_cast<float*>(ws));
