@@ -20,7 +20,7 @@ namespace nk {
 namespace {
 
 constexpr int TH = 16, TW = 64, CO_G = 8, THREADS = 256;
-constexpr int MAX_IN_H = 64, MAX_IN_W = 176;   // halo tile limits: 44 KB of the 48 KB static shared memory
+constexpr int MAX_IN_H = 64, MAX_IN_W = 176;   // halo tile limits (44 KB of shared memory)
 
 struct Direct {
   const float* I;
@@ -36,9 +36,13 @@ struct Direct {
   int in_h, in_w;          // halo tile extent
 };
 
+// Shared memory is sized to the actual halo tile (18 x 66 floats for a 3 x 3
+// stride-1 filter), so many CTAs share an SM and keep enough loads in flight
+// to reach HBM bandwidth.
 __global__ void __launch_bounds__(THREADS) direct_conv_kernel(Direct p) {
-  __shared__ float tile[MAX_IN_H * MAX_IN_W];
-  __shared__ float ker[CO_G * 64];   // taps of one input channel for the channel group (<= 64 taps)
+  extern __shared__ float smem_f[];
+  float* ker = smem_f;                    // [CO_G][64] taps of one input channel
+  float* tile = smem_f + CO_G * 64;       // [in_h][in_w] halo tile
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   const int wo0 = blockIdx.x * TW, ho0 = blockIdx.y * TH;
   const int n = blockIdx.z / ((p.CO + CO_G - 1) / CO_G);
@@ -165,6 +169,7 @@ extern "C" nk_status nk_conv2d_nchw_fchw(const nk_tensor* I, const nk_tensor* K,
   if ((int64_t)p.N * groups > 65535) return fail(NK_ERR_UNSUPPORTED, "batch x channel groups too large");
   dim3 grid((unsigned)((p.OW + TW - 1) / TW), (unsigned)((p.OH + TH - 1) / TH), (unsigned)(p.N * groups));
   if (grid.y > 65535) return fail(NK_ERR_UNSUPPORTED, "output too tall");
-  direct_conv_kernel<<<grid, THREADS, 0, static_cast<cudaStream_t>(stream)>>>(p);
+  const size_t smem = (size_t)(CO_G * 64 + p.in_h * p.in_w) * sizeof(float);
+  direct_conv_kernel<<<grid, THREADS, smem, static_cast<cudaStream_t>(stream)>>>(p);
   return check_launch("direct_conv_kernel");
 }

@@ -36,24 +36,34 @@ __global__ void amax_stage1(const float* __restrict__ x, int64_t rows, int64_t c
                             float* __restrict__ partial) {
   float m = 0.f;
   bool nan = false;
-  const bool vec = (cols % 4 == 0) && (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(x) & 15) == 0);
-  if (vec) {
-    const int64_t cq = cols / 4;
-    const int64_t total = rows * cq;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-         i += (int64_t)gridDim.x * blockDim.x) {
-      const int64_t r = i / cq, c = (i % cq) * 4;
-      float4 v = __ldg(reinterpret_cast<const float4*>(x + r * ld + c));
+  const bool al = (reinterpret_cast<uintptr_t>(x) & 15) == 0;
+  if (al && ld == cols && (rows * cols) % 4 == 0) {
+    // dense: one flat run of float4, no index arithmetic per element
+    const float4* x4 = reinterpret_cast<const float4*>(x);
+    const int64_t n4 = rows * cols / 4;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+      const float4 v = __ldg(x4 + i);
       nan |= (v.x != v.x) | (v.y != v.y) | (v.z != v.z) | (v.w != v.w);
       m = fmaxf(m, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
     }
   } else {
-    const int64_t total = rows * cols;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-         i += (int64_t)gridDim.x * blockDim.x) {
-      float v = x[(i / cols) * ld + (i % cols)];
-      nan |= (v != v);
-      m = fmaxf(m, fabsf(v));
+    // strided rows: blocks stride over rows, threads over the row
+    const bool vec = al && (cols % 4 == 0) && (ld % 4 == 0);
+    for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
+      const float* row = x + r * ld;
+      if (vec) {
+        for (int64_t c = threadIdx.x; c < cols / 4; c += blockDim.x) {
+          const float4 v = __ldg(reinterpret_cast<const float4*>(row) + c);
+          nan |= (v.x != v.x) | (v.y != v.y) | (v.z != v.z) | (v.w != v.w);
+          m = fmaxf(m, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+        }
+      } else {
+        for (int64_t c = threadIdx.x; c < cols; c += blockDim.x) {
+          const float v = row[c];
+          nan |= (v != v);
+          m = fmaxf(m, fabsf(v));
+        }
+      }
     }
   }
   if (__any_sync(0xffffffffu, nan)) m = __int_as_float(0x7fc00000);

@@ -98,7 +98,9 @@ struct TcParams {
 
 // Epilogue staging: one 32 x 32 FP32 box (4 KB, 128B-swizzled) per epilogue warp.
 constexpr int kStageBox = 4096;
-__host__ __device__ inline int staging_bytes(bool wide) { return (wide ? 8 : 4) * kStageBox; }
+__host__ __device__ inline int staging_bytes(bool wide, int mch = 1) {
+  return mch > 1 ? 0 : (wide ? 8 : 4) * kStageBox;   // tall tiles store directly
+}
 
 struct GroupDesc {
   int M, N, K, tiles_n;
@@ -108,8 +110,10 @@ struct GroupDesc {
   int pad;
 };
 
-__host__ __device__ inline int stage_bytes(int kind, int bn) {
-  const int ab = kBM * kRowBytes + bn * kRowBytes;
+// One pipeline stage: mch A tiles of 128 rows (one per accumulator chain)
+// and one B^T tile of bn rows, each row 128 bytes; BF16x3 doubles it (hi, lo).
+__host__ __device__ inline int stage_bytes(int kind, int bn, int mch = 1) {
+  const int ab = mch * kBM * kRowBytes + bn * kRowBytes;
   return kind == TC_BF16X3 ? 2 * ab : ab;
 }
 
@@ -207,26 +211,31 @@ __device__ __forceinline__ int conv_row(const ConvTile& c, int tm, int r) {
 // N = 256 MMA holds only 128 cycles of math; interleaving two chains hides
 // that latency.  Both chains fill the 512 TMEM columns, so the accumulator is
 // single-buffered and eight epilogue warps drain it.
-template <int KIND, int CL, bool GROUPED, bool CONV = false, bool PAIR = false, bool WIDE = false>
+//
+// MCH > 1 (tall tile, one CTA): MCH stacked 128-row tiles of A share one B
+// tile, each with its own accumulator chain, so narrow problems (N = 64, 128)
+// keep several independent MMA chains in flight.
+template <int KIND, int CL, bool GROUPED, bool CONV = false, bool PAIR = false, bool WIDE = false, int MCH = 1>
 __global__ void __launch_bounds__(WIDE ? 320 : 192, 1) tc_gemm_kernel(const __grid_constant__ TcParams p) {
   static_assert(!PAIR || CL == 2, "a CTA pair is a cluster of two");
   static_assert(!WIDE || (PAIR && KIND != TC_BF16X3 && !GROUPED), "wide tiles are pair tiles");
+  static_assert(MCH == 1 || (!PAIR && !GROUPED && KIND != TC_BF16X3 && CL == 1), "tall tiles: one CTA");
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = ptx::smem_u32(smem_raw);
   const uint32_t base = (raw + 1023) & ~1023u;
   uint8_t* base_ptr = smem_raw + (base - raw);
 
   const int b_rows_smem = PAIR ? p.bn / 2 : p.bn;   // rows of B^T this CTA keeps per stage
-  const int sb = stage_bytes(KIND, b_rows_smem);
+  const int sb = stage_bytes(KIND, b_rows_smem, MCH);
   const int S = p.stages;
   const uint32_t stg0 = base + S * sb;   // epilogue staging boxes
-  const uint32_t bar0 = stg0 + staging_bytes(WIDE);   // full[S], empty[S], tfull[2], tempty[2], drain
+  const uint32_t bar0 = stg0 + staging_bytes(WIDE, MCH);   // full[S], empty[S], tfull[2], tempty[2], drain
   auto full_bar = [&](int s) { return bar0 + 8u * s; };
   auto empty_bar = [&](int s) { return bar0 + 8u * (S + s); };
   auto tfull_bar = [&](int b) { return bar0 + 8u * (2 * S + b); };
   auto tempty_bar = [&](int b) { return bar0 + 8u * (2 * S + 2 + b); };
   const uint32_t drain_bar = bar0 + 8u * (2 * S + 4);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(base_ptr + S * sb + staging_bytes(WIDE) + 8 * (2 * S + 5));
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(base_ptr + S * sb + staging_bytes(WIDE, MCH) + 8 * (2 * S + 5));
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x / 32;
@@ -237,7 +246,7 @@ __global__ void __launch_bounds__(WIDE ? 320 : 192, 1) tc_gemm_kernel(const __gr
   // Accumulator columns per buffer: BN, or 2*BN for BF16x3 (hi*hi and the
   // hi*lo + lo*hi corrections accumulate apart and meet in the epilogue, so
   // the large term sees K/16 roundings instead of 3K/16).
-  const int acc_cols = KIND == TC_BF16X3 ? 2 * p.bn : p.bn;
+  const int acc_cols = KIND == TC_BF16X3 ? 2 * p.bn : MCH * p.bn;
   const uint32_t tmem_cols = WIDE ? 512u : 2u * (uint32_t)acc_cols < 32u ? 32u : 2u * (uint32_t)acc_cols;
 
   if (threadIdx.x == 0) {
@@ -276,7 +285,7 @@ __global__ void __launch_bounds__(WIDE ? 320 : 192, 1) tc_gemm_kernel(const __gr
   if (CL == 2) ptx::cluster_sync();
   const uint32_t tmem_base = *tmem_slot;
 
-  const int a_bytes = kBM * kRowBytes;
+  const int a_bytes = MCH * kBM * kRowBytes;
   const int b_bytes = b_rows_smem * kRowBytes;
   // Stage layout: [A][B] or, for BF16x3, [A_hi][B_hi][A_lo][B_lo].
   auto a_smem = [&](int s, int part) { return base + s * sb + part * (a_bytes + b_bytes); };
@@ -333,13 +342,16 @@ __global__ void __launch_bounds__(WIDE ? 320 : 192, 1) tc_gemm_kernel(const __gr
             // K block kb = (filter tap, 64-channel block); the A box is the
             // input window that tap sees, shifted and strided by TMA.
             const ConvTile& c = p.cv;
-            ptx::mbar_arrive_expect_tx(full_bar(s), p.a_box_bytes + (uint32_t)b_bytes);
+            ptx::mbar_arrive_expect_tx(full_bar(s), MCH * p.a_box_bytes + (uint32_t)b_bytes);
             const int tap = kb / c.cblocks, c0 = (kb % c.cblocks) * 64;
             const int kh = tap / c.KW, kw = tap % c.KW;
-            const int tw = t.tm % c.tiles_w, th = (t.tm / c.tiles_w) % c.tiles_h;
-            const int tb = t.tm / (c.tiles_w * c.tiles_h);
-            ptx::tma_load_4d(a_smem(s, 0), &p.tmA, full_bar(s), c0, tw * c.Q * c.sw + kw * c.dw - c.pl,
-                             th * c.R * c.sh + kh * c.dh - c.pt, tb * c.NB);
+            for (int ch = 0; ch < MCH; ++ch) {
+              const int ct = t.tm * MCH + ch;   // conv tile of this chain
+              const int tw = ct % c.tiles_w, th = (ct / c.tiles_w) % c.tiles_h;
+              const int tb = ct / (c.tiles_w * c.tiles_h);
+              ptx::tma_load_4d(a_smem(s, 0) + ch * kBM * kRowBytes, &p.tmA, full_bar(s), c0,
+                               tw * c.Q * c.sw + kw * c.dw - c.pl, th * c.R * c.sh + kh * c.dh - c.pt, tb * c.NB);
+            }
             const int fy = t.tn * p.bn + rank * b_rows;
             if (CL == 2)
               ptx::tma_load_3d_mc(b_smem(s, 0) + rank * b_rows * kRowBytes, &p.tmB, full_bar(s), c0, tap,
@@ -350,13 +362,14 @@ __global__ void __launch_bounds__(WIDE ? 320 : 192, 1) tc_gemm_kernel(const __gr
           }
           ptx::mbar_arrive_expect_tx(full_bar(s), (uint32_t)sb);
           const int kx = kb * kblk;
-          const int ay = t.tm * kBM;
+          const int ay = t.tm * MCH * kBM;
           const int by = t.tn * p.bn + rank * b_rows;
           const int nparts = KIND == TC_BF16X3 ? 2 : 1;
           for (int part = 0; part < nparts; ++part) {
             const CUtensorMap* ma = part ? &p.tmA2 : t.ma;
             const CUtensorMap* mb = part ? &p.tmB2 : t.mb;
-            ptx::tma_load_2d(a_smem(s, part), ma, full_bar(s), kx, ay);
+            for (int ch = 0; ch < MCH; ++ch)
+              ptx::tma_load_2d(a_smem(s, part) + ch * kBM * kRowBytes, ma, full_bar(s), kx, ay + ch * kBM);
             if (CL == 2)
               ptx::tma_load_2d_mc(b_smem(s, part) + rank * b_rows * kRowBytes, mb, full_bar(s), kx, by,
                                   (uint16_t)0x3);
@@ -403,6 +416,11 @@ __global__ void __launch_bounds__(WIDE ? 320 : 192, 1) tc_gemm_kernel(const __gr
             const uint32_t accum = (kb > kb0 || k > 0) ? 1u : 0u;
             if (PAIR) ptx::tc_mma_pair<KIND == TC_FP8>(d, ad, bd, idesc, accum);
             else ptx::tc_mma<KIND == TC_FP8>(d, ad, bd, idesc, accum);
+#pragma unroll
+            for (int ch = 1; ch < MCH; ++ch)   // further chains: their own A rows, the same B
+              ptx::tc_mma<KIND == TC_FP8>(d + (uint32_t)(ch * p.bn),
+                                          ptx::sw128_desc(a_smem(s, 0) + ch * kBM * kRowBytes + koff), bd, idesc,
+                                          accum);
             if (WIDE) {   // second chain: B^T rows 128..255 of this CTA's stage
               const uint64_t bw = ptx::sw128_desc(b_smem(s, 0) + 128 * kRowBytes + koff);
               ptx::tc_mma_pair<KIND == TC_FP8>(d2, ad, bw, idesc, accum);
@@ -444,14 +462,17 @@ __global__ void __launch_bounds__(WIDE ? 320 : 192, 1) tc_gemm_kernel(const __gr
       const uint32_t aph = WIDE ? (uint32_t)tc & 1u : (uint32_t)(tc >> 1) & 1u;
       if (!ptx::mbar_wait(tfull_bar(acc), aph, p.budget, abort_flag, &g_tc_err)) break;
       ptx::tc_fence_after();
-      const int row = CONV ? conv_row(p.cv, t.tm, q * 32 + lane) : t.tm * kBM + q * 32 + lane;
+      for (int ch = 0; ch < MCH; ++ch) {   // chains of a tall tile (one otherwise)
+      const int tmc = t.tm * MCH + ch;
+      const int row = CONV ? conv_row(p.cv, tmc, q * 32 + lane) : tmc * kBM + q * 32 + lane;
       const bool row_ok = CONV ? row >= 0 : row < t.M;
       // a wide tile has two warps per lane quarter, each draining one chain's 256 columns
       const int c_begin = WIDE ? ((warp - 2) / 4) * 256 : 0;
       const int c_end = WIDE ? c_begin + 256 : p.bn;
       for (int c0 = c_begin; c0 < c_end; c0 += 32) {
         float v[32];
-        const uint32_t ta = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * acc_cols + c0);
+        const uint32_t ta =
+            tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * acc_cols + ch * p.bn + c0);
         ptx::tmem_ld32(ta, v);
         if (KIND == TC_BF16X3) {
           float w[32];
@@ -487,7 +508,7 @@ __global__ void __launch_bounds__(WIDE ? 320 : 192, 1) tc_gemm_kernel(const __gr
           ptx::fence_proxy_async_smem();
           __syncwarp();
           if (lane == 0) {
-            ptx::tma_store_2d(&p.tmC, stg, col0, t.tm * kBM + q * 32);
+            ptx::tma_store_2d(&p.tmC, stg, col0, tmc * kBM + q * 32);
             ptx::bulk_commit();
           }
           continue;
@@ -537,6 +558,7 @@ __global__ void __launch_bounds__(WIDE ? 320 : 192, 1) tc_gemm_kernel(const __gr
             dst[j] = x;
           }
         }
+      }
       }
       ptx::tc_fence_before();
       __syncwarp();
@@ -596,18 +618,24 @@ nk_status make_kmajor_map(CUtensorMap* m, bool fp8, const void* ptr, int64_t row
   return NK_OK;
 }
 
-int smem_bytes(int kind, int bn, int stages, bool wide = false) {
-  return 1024 + stages * stage_bytes(kind, bn) + staging_bytes(wide) + 8 * (2 * stages + 5) + 16;
+int smem_bytes(int kind, int bn, int stages, bool wide = false, int mch = 1) {
+  return 1024 + stages * stage_bytes(kind, bn, mch) + staging_bytes(wide, mch) + 8 * (2 * stages + 5) + 16;
 }
+
+// Accumulator chains along M of a one-CTA schedule: tile_m 256 / 512 with
+// cluster 1 are tall tiles of 2 / 4 chains (tile_m 256 with cluster 2 is a pair).
+int chains_of(const nk_schedule& s) { return (s.cluster == 1 && s.tile_m > 128) ? s.tile_m / 128 : 1; }
 
 // Shared memory of a schedule: a CTA of a pair (tile_m 256) keeps half of B.
 int smem_of(int kind, const nk_schedule& s) {
-  return smem_bytes(kind, s.tile_m == 256 ? s.tile_n / 2 : s.tile_n, s.stages, s.tile_n == 512);
+  const bool pair = s.cluster == 2 && s.tile_m == 256;
+  return smem_bytes(kind, pair ? s.tile_n / 2 : s.tile_n, s.stages, s.tile_n == 512, chains_of(s));
 }
 
-template <int KIND, int CL, bool GROUPED = false, bool CONV = false, bool PAIR = false, bool WIDE = false>
+template <int KIND, int CL, bool GROUPED = false, bool CONV = false, bool PAIR = false, bool WIDE = false,
+          int MCH = 1>
 nk_status launch(const TcParams& p, int grid, int smem, cudaStream_t st) {
-  auto kern = tc_gemm_kernel<KIND, CL, GROUPED, CONV, PAIR, WIDE>;
+  auto kern = tc_gemm_kernel<KIND, CL, GROUPED, CONV, PAIR, WIDE, MCH>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(tc_gemm_kernel)");
   cudaLaunchConfig_t cfg = {};
@@ -633,7 +661,7 @@ int ctas_per_sm(int kind, const nk_schedule& s) {
   const int bn = s.tile_n;
   const int sm = smem_of(kind, s);
   int by_smem = kMaxSmem / sm;
-  const int acc = kind == TC_BF16X3 ? 2 * bn : bn;
+  const int acc = kind == TC_BF16X3 ? 2 * bn : chains_of(s) * bn;
   int cols = 2 * acc < 32 ? 32 : 2 * acc;
   int by_tmem = 512 / cols;
   int r = by_smem < by_tmem ? by_smem : by_tmem;
@@ -644,8 +672,11 @@ int ctas_per_sm(int kind, const nk_schedule& s) {
 
 bool tc_schedule_valid(int kind, const nk_schedule& s, int M, int N, int K) {
   (void)M; (void)N; (void)K;
-  // tile_m 256 = a CTA pair issuing 2-SM MMAs (cluster of two).
-  if (s.tile_m != 128 && !(s.tile_m == 256 && s.cluster == 2)) return false;
+  // tile_m 256 with cluster 2 = a CTA pair issuing 2-SM MMAs; tile_m 256 / 512
+  // with cluster 1 = a tall tile of 2 / 4 accumulator chains sharing B.
+  if (s.tile_m != 128 && s.tile_m != 256 && s.tile_m != 512) return false;
+  if (s.tile_m == 512 && s.cluster != 1) return false;
+  if (chains_of(s) > 1 && (kind == TC_BF16X3 || chains_of(s) * s.tile_n > 256)) return false;
   if (s.tile_n != 64 && s.tile_n != 128 && s.tile_n != 256 && s.tile_n != 512) return false;
   if (s.tile_n == 512 && (s.tile_m != 256 || kind == TC_BF16X3)) return false;   // wide pair tiles only
   if (kind == TC_BF16X3 && s.tile_n > 128) return false;   // 2 accumulators x 2 buffers <= 512 cols
@@ -721,7 +752,8 @@ nk_status tc_gemm(const TcGemm& g, const nk_schedule& s, void* ws, size_t ws_byt
   p.M = g.M; p.N = g.N; p.K = g.K;
   p.bn = s.tile_n;
   p.stages = s.stages;
-  const int tm = (g.M + kBM - 1) / kBM;
+  const int mch = chains_of(s);
+  const int tm = (g.M + kBM * mch - 1) / (kBM * mch);
   p.tiles_m = (tm + CL - 1) / CL * CL;
   p.tiles_n = (g.N + s.tile_n - 1) / s.tile_n;
   p.nkb = (g.K + s.tile_k - 1) / s.tile_k;
@@ -751,7 +783,7 @@ nk_status tc_gemm(const TcGemm& g, const nk_schedule& s, void* ws, size_t ws_byt
   p.c_vec = cvec ? 1 : 0;
   // TMA-store epilogue: plain overwrite of a 16-byte aligned C in one K slice.
   p.c_tma = 0;
-  if (splits == 1 && g.beta == 0.f && (reinterpret_cast<uintptr_t>(g.C) & 15) == 0 && (g.ldc * 4) % 16 == 0) {
+  if (mch == 1 && splits == 1 && g.beta == 0.f && (reinterpret_cast<uintptr_t>(g.C) & 15) == 0 && (g.ldc * 4) % 16 == 0) {
     auto fn = encode_fn();
     cuuint64_t dims[2] = {(cuuint64_t)g.N, (cuuint64_t)g.M};
     cuuint64_t strides[1] = {(cuuint64_t)(g.ldc * 4)};
@@ -772,6 +804,12 @@ nk_status tc_gemm(const TcGemm& g, const nk_schedule& s, void* ws, size_t ws_byt
   if (s.tile_n == 512) {
     if (g.kind == TC_FP8) status = launch<TC_FP8, 2, false, false, true, true>(p, grid, smem, st);
     else status = launch<TC_BF16, 2, false, false, true, true>(p, grid, smem, st);
+  } else if (mch == 2) {
+    if (g.kind == TC_FP8) status = launch<TC_FP8, 1, false, false, false, false, 2>(p, grid, smem, st);
+    else status = launch<TC_BF16, 1, false, false, false, false, 2>(p, grid, smem, st);
+  } else if (mch == 4) {
+    if (g.kind == TC_FP8) status = launch<TC_FP8, 1, false, false, false, false, 4>(p, grid, smem, st);
+    else status = launch<TC_BF16, 1, false, false, false, false, 4>(p, grid, smem, st);
   } else
   switch (g.kind * 3 + (pair ? 2 : CL - 1)) {
     case TC_BF16 * 3 + 0: status = launch<TC_BF16, 1>(p, grid, smem, st); break;
@@ -871,12 +909,25 @@ nk_schedule tc_conv_default_schedule(const ConvGeom& g, int F, int sms) {
   s.tile_k = 64;
   s.tile_n = F <= 64 ? 64 : F <= 128 ? 128 : 256;
   s.cluster = 1;
-  s.stages = 2;
-  while (s.stages < 8 && smem_bytes(TC_BF16, s.tile_n, s.stages + 1) <= kMaxSmem) ++s.stages;
   const ConvTile t = choose_conv_tile(g);
-  const int tiles = t.tiles_w * t.tiles_h * ((g.n + t.NB - 1) / t.NB) * ((F + s.tile_n - 1) / s.tile_n);
-  const int nkb = g.kh * g.kw * t.cblocks;
+  const int ctiles = t.tiles_w * t.tiles_h * ((g.n + t.NB - 1) / t.NB);
+  const int ntn = (F + s.tile_n - 1) / s.tile_n;
+  // Narrow filters: stack 4 (F <= 64) or 2 (F <= 128) conv tiles per CTA as
+  // independent accumulator chains, while that still leaves a wave of CTAs.
+  if (s.tile_n <= 128) {
+    const int mch = s.tile_n == 64 ? 4 : 2;
+    if ((ctiles + mch - 1) / mch * ntn >= sms) s.tile_m = 128 * mch;
+  }
+  s.stages = 2;
   s.split_k = 1;
+  for (;;) {
+    nk_schedule n = s;
+    n.stages = s.stages + 1;
+    if (n.stages > 8 || smem_of(TC_BF16, n) > kMaxSmem) break;
+    s = n;
+  }
+  const int tiles = (ctiles + chains_of(s) - 1) / chains_of(s) * ntn;
+  const int nkb = g.kh * g.kw * t.cblocks;
   while (tiles * s.split_k * 2 <= sms && nkb / (s.split_k * 2) >= 4 && s.split_k < 16) s.split_k *= 2;
   return s;
 }
@@ -909,7 +960,9 @@ nk_status tc_conv(const TcConv& c, const nk_schedule& s, void* ws, size_t ws_byt
   p.M = M; p.N = c.F; p.K = g.kh * g.kw * g.c;
   p.bn = s.tile_n;
   p.stages = s.stages;
-  const int tm = t.tiles_w * t.tiles_h * ((g.n + t.NB - 1) / t.NB);
+  const int mch = chains_of(s);
+  const int ctiles = t.tiles_w * t.tiles_h * ((g.n + t.NB - 1) / t.NB);
+  const int tm = (ctiles + mch - 1) / mch;
   p.tiles_m = (tm + CL - 1) / CL * CL;
   p.tiles_n = (c.F + s.tile_n - 1) / s.tile_n;
   p.nkb = g.kh * g.kw * t.cblocks;
@@ -937,7 +990,9 @@ nk_status tc_conv(const TcConv& c, const nk_schedule& s, void* ws, size_t ws_byt
   grid = grid / CL * CL;
   if (grid > p.units * CL) grid = p.units * CL;
   if (grid < CL) grid = CL;
-  if (s.tile_m == 256) status = launch<TC_BF16, 2, false, true, true>(p, grid, smem, st);
+  if (mch == 2) status = launch<TC_BF16, 1, false, true, false, false, 2>(p, grid, smem, st);
+  else if (mch == 4) status = launch<TC_BF16, 1, false, true, false, false, 4>(p, grid, smem, st);
+  else if (s.tile_m == 256) status = launch<TC_BF16, 2, false, true, true>(p, grid, smem, st);
   else if (CL == 2) status = launch<TC_BF16, 2, false, true>(p, grid, smem, st);
   else status = launch<TC_BF16, 1, false, true>(p, grid, smem, st);
   if (status != NK_OK || splits == 1) return status;

@@ -113,12 +113,11 @@ std::vector<nk_schedule> enumerate(const nk_problem* p) {
   gemm_view(p, M, N, K);
   const int tk = kind == TC_FP8 ? 128 : 64;
   const int64_t nkb = p->op == NK_OP_CONV2D ? (int64_t)p->kh * p->kw * ((p->c + 63) / 64) : (K + tk - 1) / tk;
-  for (int tm : {128, 256})
+  for (int tm : {128, 256, 512})
   for (int tn : {64, 128, 256, 512})
     for (int cl : {1, 2})
       for (int split : {1, 2, 4, 8, 16})
         for (int st = 2; st <= 8; ++st) {
-          if (tm == 256 && cl != 2) continue;
           if (tn == 512 && p->op == NK_OP_CONV2D) continue;
           nk_schedule s{tm, tn, tk, cl, st, split};
           if (split > nkb) continue;
@@ -281,10 +280,10 @@ struct Rng {
 
 nk_status evolve(const nk_problem* p, const std::vector<nk_schedule>& cand, int budget, int reps,
                  cudaStream_t cs, int* best_i, float* best_ms) {
-  static const int L_TM[] = {128, 256}, L_TN[] = {64, 128, 256, 512}, L_CL[] = {1, 2},
+  static const int L_TM[] = {128, 256, 512}, L_TN[] = {64, 128, 256, 512}, L_CL[] = {1, 2},
                    L_ST[] = {2, 3, 4, 5, 6, 7, 8}, L_SK[] = {1, 2, 4, 8, 16};
   static const int* LV[5] = {L_TM, L_TN, L_CL, L_ST, L_SK};
-  static const int NL[5] = {2, 4, 2, 7, 5};
+  static const int NL[5] = {3, 4, 2, 7, 5};
   auto level_of = [&](int c, int v) {
     for (int i = 0; i < NL[c]; ++i)
       if (LV[c][i] == v) return i;

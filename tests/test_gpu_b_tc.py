@@ -68,6 +68,9 @@ SCHEDULES = [(128, bn, 64, cl, st, sk) for bn in (64, 128, 256) for cl in (1, 2)
 SCHEDULES += [(256, bn, 64, 2, st, sk) for bn in (64, 128, 256) for st in (3, 6) for sk in (1, 3)]
 # wide pair tiles: 256 x 512 as two N = 256 accumulator chains
 SCHEDULES += [(256, 512, 64, 2, st, sk) for st in (2, 4) for sk in (1, 3)]
+# tall tiles: 2 or 4 stacked M tiles as independent chains sharing B (one CTA)
+SCHEDULES += [(256, bn, 64, 1, st, sk) for bn in (64, 128) for st in (2, 4) for sk in (1, 3)]
+SCHEDULES += [(512, 64, 64, 1, st, sk) for st in (2, 3) for sk in (1, 3)]
 
 
 @pytest.mark.parametrize("sched", SCHEDULES)
@@ -91,7 +94,8 @@ def test_bf16x3_schedules_bitwise(nk, sched):
 
 @pytest.mark.parametrize("sched", [(128, 128, 128, 1, 4, 1), (128, 256, 128, 2, 4, 2), (128, 64, 128, 1, 3, 1),
                                    (256, 256, 128, 2, 6, 1), (256, 128, 128, 2, 4, 2),
-                                   (256, 512, 128, 2, 4, 1), (256, 512, 128, 2, 3, 2)])
+                                   (256, 512, 128, 2, 4, 1), (256, 512, 128, 2, 3, 2),
+                                   (256, 128, 128, 1, 4, 1), (512, 64, 128, 1, 3, 2)])
 def test_fp8_schedules_bitwise(nk, sched):
     M, N, K = 260, 384, 640
     A = synth.small_ints(63, 1, (M, K)) / 2

@@ -61,7 +61,8 @@ def test_bf16_conv_small_ints_bitwise(nk, case):
 
 
 @pytest.mark.parametrize("sched", [(128, 64, 64, 1, 4, 1), (128, 128, 64, 2, 3, 1), (128, 64, 64, 2, 5, 3),
-                                   (128, 256, 64, 1, 4, 2), (256, 128, 64, 2, 4, 1), (256, 64, 64, 2, 6, 3)])
+                                   (128, 256, 64, 1, 4, 2), (256, 128, 64, 2, 4, 1), (256, 64, 64, 2, 6, 3),
+                                   (256, 128, 64, 1, 4, 1), (512, 64, 64, 1, 3, 1), (512, 64, 64, 1, 2, 3)])
 def test_bf16_conv_schedules_bitwise(nk, sched):
     N, H, Wd, C, F, KH, KW = 2, 15, 17, 96, 160, 3, 3
     I = synth.small_ints(82, 1, (N, H, Wd, C))
