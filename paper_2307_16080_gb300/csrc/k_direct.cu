@@ -62,10 +62,20 @@ __global__ void __launch_bounds__(THREADS) direct_conv_kernel(Direct p) {
   for (int ci = 0; ci < p.CI; ++ci) {
     __syncthreads();
     const float* src = p.I + n * p.sIn + ci * p.sIc;
-    for (int e = threadIdx.x; e < p.in_h * p.in_w; e += THREADS) {
-      const int r = e / p.in_w, c = e % p.in_w;
-      const int ih = ih0 + r, iw = iw0 + c;
-      tile[e] = (ih >= 0 && ih < p.H && iw >= 0 && iw < p.W) ? __ldg(src + ih * p.sIh + iw) : 0.f;
+    // Eight loads in flight per thread before any lands in shared memory.
+    const int total = p.in_h * p.in_w;
+    for (int e0 = threadIdx.x; e0 < total; e0 += 8 * THREADS) {
+      float v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * THREADS;
+        const int r = e / p.in_w, c = e - r * p.in_w;
+        const int ih = ih0 + r, iw = iw0 + c;
+        v[u] = (e < total && ih >= 0 && ih < p.H && iw >= 0 && iw < p.W) ? __ldg(src + ih * p.sIh + iw) : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (e0 + u * THREADS < total) tile[e0 + u * THREADS] = v[u];
     }
     for (int e = threadIdx.x; e < ncog * taps; e += THREADS) {
       const int c = e / taps, t = e % taps;
