@@ -215,8 +215,15 @@ __device__ __forceinline__ int conv_row(const ConvTile& c, int tm, int r) {
 // MCH > 1 (tall tile, one CTA): MCH stacked 128-row tiles of A share one B
 // tile, each with its own accumulator chain, so narrow problems (N = 64, 128)
 // keep several independent MMA chains in flight.
-template <int KIND, int CL, bool GROUPED, bool CONV = false, bool PAIR = false, bool WIDE = false, int MCH = 1>
+//
+// TCONV: the convolution computed transposed, O^T = W^T im2col(I): the MMA's
+// 128 rows are filters and its N = 256 columns output pixels, so narrow
+// filter counts (F <= 128) still issue full-width MMAs.  A is the filter
+// tile (3-D map of [F][taps][C]), B the input window of a 256-pixel tile.
+template <int KIND, int CL, bool GROUPED, bool CONV = false, bool PAIR = false, bool WIDE = false, int MCH = 1,
+          bool TCONV = false>
 __global__ void __launch_bounds__(WIDE ? 320 : 192, 1) tc_gemm_kernel(const __grid_constant__ TcParams p) {
+  static_assert(!TCONV || (!CONV && !PAIR && !WIDE && MCH == 1 && CL == 1 && KIND == TC_BF16), "TCONV: one CTA");
   static_assert(!PAIR || CL == 2, "a CTA pair is a cluster of two");
   static_assert(!WIDE || (PAIR && KIND != TC_BF16X3 && !GROUPED), "wide tiles are pair tiles");
   static_assert(MCH == 1 || (!PAIR && !GROUPED && KIND != TC_BF16X3 && CL == 1), "tall tiles: one CTA");
@@ -336,6 +343,20 @@ __global__ void __launch_bounds__(WIDE ? 320 : 192, 1) tc_gemm_kernel(const __gr
                 ptx::tma_load_2d_pair(b_smem(s, part), part ? &p.tmB2 : t.mb, lf, kx, by);
               }
             }
+            continue;
+          }
+          if constexpr (TCONV) {
+            // A: 128 filters x 64 channels of tap `tap`; B: the tap's input window
+            // for the 256-pixel tile.
+            const ConvTile& c = p.cv;
+            ptx::mbar_arrive_expect_tx(full_bar(s), (uint32_t)(kBM * kRowBytes) + p.a_box_bytes);
+            const int tap = kb / c.cblocks, c0 = (kb % c.cblocks) * 64;
+            const int kh = tap / c.KW, kw = tap % c.KW;
+            const int tw = t.tm % c.tiles_w, th = (t.tm / c.tiles_w) % c.tiles_h;
+            const int tb = t.tm / (c.tiles_w * c.tiles_h);
+            ptx::tma_load_3d(a_smem(s, 0), &p.tmB, full_bar(s), c0, tap, t.tn * kBM);
+            ptx::tma_load_4d(b_smem(s, 0), &p.tmA, full_bar(s), c0, tw * c.Q * c.sw + kw * c.dw - c.pl,
+                             th * c.R * c.sh + kh * c.dh - c.pt, tb * c.NB);
             continue;
           }
           if constexpr (CONV) {
@@ -479,6 +500,27 @@ __global__ void __launch_bounds__(WIDE ? 320 : 192, 1) tc_gemm_kernel(const __gr
           ptx::tmem_ld32(ta + (uint32_t)p.bn, w);
 #pragma unroll
           for (int j = 0; j < 32; ++j) v[j] += w[j];
+        }
+        if constexpr (TCONV) {
+          // lane = filter f, column j = pixel c0 + j of the tile: for each j the
+          // warp writes 32 consecutive filters of one output row.
+          const int f = t.tn * kBM + q * 32 + lane;
+          const float bf = (p.bias && f < p.N) ? __ldg(p.bias + f) : 0.f;
+          for (int j = 0; j < 32; ++j) {
+            const int orow = conv_row(p.cv, t.tm, c0 + j);
+            if (orow < 0 || f >= p.N) continue;
+            if (p.partial) {
+              p.partial[((int64_t)t.split * p.M + orow) * p.N + f] = v[j];
+              continue;
+            }
+            float* dst = p.C + (int64_t)orow * p.ldc + f;
+            float x = alpha * v[j];
+            if (p.beta != 0.f) x = fmaf(p.beta, *dst, x);
+            x += bf;
+            if (p.relu) x = (x > 0.f || x != x) ? x : 0.f;
+            *dst = x;
+          }
+          continue;
         }
         const int col0 = t.tn * p.bn + c0;
         if (!GROUPED && !CONV && p.c_tma) {
@@ -633,9 +675,9 @@ int smem_of(int kind, const nk_schedule& s) {
 }
 
 template <int KIND, int CL, bool GROUPED = false, bool CONV = false, bool PAIR = false, bool WIDE = false,
-          int MCH = 1>
+          int MCH = 1, bool TCONV = false>
 nk_status launch(const TcParams& p, int grid, int smem, cudaStream_t st) {
-  auto kern = tc_gemm_kernel<KIND, CL, GROUPED, CONV, PAIR, WIDE, MCH>;
+  auto kern = tc_gemm_kernel<KIND, CL, GROUPED, CONV, PAIR, WIDE, MCH, TCONV>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(tc_gemm_kernel)");
   cudaLaunchConfig_t cfg = {};
@@ -849,14 +891,14 @@ namespace {
 
 // Output tile (Q columns x R rows x NB images, <= 128 GEMM rows) with the
 // fewest tiles; ties go to the widest rows.
-ConvTile choose_conv_tile(const ConvGeom& g) {
+ConvTile choose_conv_tile(const ConvGeom& g, int maxrows = 128) {
   ConvTile best{};
   int64_t best_tiles = INT64_MAX;
-  for (int Q = 1; Q <= 128 && Q <= g.ow; ++Q) {
+  for (int Q = 1; Q <= maxrows && Q <= g.ow; ++Q) {
     if (Q * g.sw > 256) break;
-    for (int R = 1; Q * R <= 128 && R <= g.oh; ++R) {
+    for (int R = 1; Q * R <= maxrows && R <= g.oh; ++R) {
       if (R * g.sh > 256) break;
-      const int NB = std::max(1, std::min(g.n, 128 / (Q * R)));
+      const int NB = std::max(1, std::min(g.n, maxrows / (Q * R)));
       const int64_t tiles = (int64_t)((g.n + NB - 1) / NB) * ((g.oh + R - 1) / R) * ((g.ow + Q - 1) / Q);
       if (tiles < best_tiles || (tiles == best_tiles && Q > best.Q)) {
         best_tiles = tiles;
@@ -909,15 +951,12 @@ nk_schedule tc_conv_default_schedule(const ConvGeom& g, int F, int sms) {
   s.tile_k = 64;
   s.tile_n = F <= 64 ? 64 : F <= 128 ? 128 : 256;
   s.cluster = 1;
-  const ConvTile t = choose_conv_tile(g);
+  // Narrow filter counts: the transposed orientation (128 filters x 256 pixels).
+  if (F <= 128) { s.tile_m = 256; s.tile_n = 128; }
+  const bool tconv = s.tile_m == 256;
+  const ConvTile t = choose_conv_tile(g, tconv ? 256 : 128);
   const int ctiles = t.tiles_w * t.tiles_h * ((g.n + t.NB - 1) / t.NB);
-  const int ntn = (F + s.tile_n - 1) / s.tile_n;
-  // Narrow filters: stack 4 (F <= 64) or 2 (F <= 128) conv tiles per CTA as
-  // independent accumulator chains, while that still leaves a wave of CTAs.
-  if (s.tile_n <= 128) {
-    const int mch = s.tile_n == 64 ? 4 : 2;
-    if ((ctiles + mch - 1) / mch * ntn >= sms) s.tile_m = 128 * mch;
-  }
+  const int ntn = tconv ? (F + 127) / 128 : (F + s.tile_n - 1) / s.tile_n;
   s.stages = 2;
   s.split_k = 1;
   for (;;) {
@@ -926,7 +965,7 @@ nk_schedule tc_conv_default_schedule(const ConvGeom& g, int F, int sms) {
     if (n.stages > 8 || smem_of(TC_BF16, n) > kMaxSmem) break;
     s = n;
   }
-  const int tiles = (ctiles + chains_of(s) - 1) / chains_of(s) * ntn;
+  const int tiles = ctiles * ntn;
   const int nkb = g.kh * g.kw * t.cblocks;
   while (tiles * s.split_k * 2 <= sms && nkb / (s.split_k * 2) >= 4 && s.split_k < 16) s.split_k *= 2;
   return s;
@@ -948,23 +987,26 @@ nk_status tc_conv(const TcConv& c, const nk_schedule& s, void* ws, size_t ws_byt
   if ((c.sI_w * 2) % 16 || (c.sI_h * 2) % 16 || (c.sI_n * 2) % 16 || (c.ldw * 2) % 16 ||
       (reinterpret_cast<uintptr_t>(c.I) & 15) || (reinterpret_cast<uintptr_t>(c.Wt) & 15))
     return fail(NK_ERR_MISALIGNED, "conv operands need 16-byte aligned bases and strides");
-  const ConvTile t = choose_conv_tile(g);
+  // tile_m 256 on one CTA: the transposed orientation (128 filters x 256 pixels)
+  const bool tconv = s.tile_m == 256 && s.cluster == 1;
+  if (tconv && s.tile_n != 128) return fail(NK_ERR_NO_SCHEDULE, "transposed conv tiles use tile_n 128");
+  const ConvTile t = choose_conv_tile(g, tconv ? 256 : 128);
   if (g.sw > 8 || g.sh > 8) return fail(NK_ERR_UNSUPPORTED, "conv stride above 8");
   TcParams p;
   memset(&p, 0, sizeof p);
   const int CL = s.cluster;
   if (s.tile_n == 512) return fail(NK_ERR_NO_SCHEDULE, "wide 256 x 512 tiles are for matmul");
-  if ((status = make_conv_maps(p, c, t, s.tile_n / CL)) != NK_OK) return status;
+  if ((status = make_conv_maps(p, c, t, tconv ? kBM : s.tile_n / CL)) != NK_OK) return status;
   p.cv = t;
   p.a_box_bytes = (uint32_t)(t.Q * t.R * t.NB * kRowBytes);
   p.M = M; p.N = c.F; p.K = g.kh * g.kw * g.c;
-  p.bn = s.tile_n;
+  p.bn = tconv ? 256 : s.tile_n;
   p.stages = s.stages;
-  const int mch = chains_of(s);
+  const int mch = tconv ? 1 : chains_of(s);
   const int ctiles = t.tiles_w * t.tiles_h * ((g.n + t.NB - 1) / t.NB);
   const int tm = (ctiles + mch - 1) / mch;
   p.tiles_m = (tm + CL - 1) / CL * CL;
-  p.tiles_n = (c.F + s.tile_n - 1) / s.tile_n;
+  p.tiles_n = tconv ? (c.F + kBM - 1) / kBM : (c.F + s.tile_n - 1) / s.tile_n;
   p.nkb = g.kh * g.kw * t.cblocks;
   int splits = s.split_k > p.nkb ? p.nkb : s.split_k;
   p.kb_per_split = (p.nkb + splits - 1) / splits;
@@ -990,7 +1032,8 @@ nk_status tc_conv(const TcConv& c, const nk_schedule& s, void* ws, size_t ws_byt
   grid = grid / CL * CL;
   if (grid > p.units * CL) grid = p.units * CL;
   if (grid < CL) grid = CL;
-  if (mch == 2) status = launch<TC_BF16, 1, false, true, false, false, 2>(p, grid, smem, st);
+  if (tconv) status = launch<TC_BF16, 1, false, false, false, false, 1, true>(p, grid, smem, st);
+  else if (mch == 2) status = launch<TC_BF16, 1, false, true, false, false, 2>(p, grid, smem, st);
   else if (mch == 4) status = launch<TC_BF16, 1, false, true, false, false, 4>(p, grid, smem, st);
   else if (s.tile_m == 256) status = launch<TC_BF16, 2, false, true, true>(p, grid, smem, st);
   else if (CL == 2) status = launch<TC_BF16, 2, false, true>(p, grid, smem, st);

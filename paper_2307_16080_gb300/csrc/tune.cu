@@ -119,6 +119,7 @@ std::vector<nk_schedule> enumerate(const nk_problem* p) {
       for (int split : {1, 2, 4, 8, 16})
         for (int st = 2; st <= 8; ++st) {
           if (tn == 512 && p->op == NK_OP_CONV2D) continue;
+          if (p->op == NK_OP_CONV2D && tm == 256 && cl == 1 && tn != 128) continue;   // transposed conv
           nk_schedule s{tm, tn, tk, cl, st, split};
           if (split > nkb) continue;
           if (!tc_schedule_valid(kind, s, (int)M, (int)N, (int)K)) continue;

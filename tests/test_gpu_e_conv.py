@@ -62,7 +62,8 @@ def test_bf16_conv_small_ints_bitwise(nk, case):
 
 @pytest.mark.parametrize("sched", [(128, 64, 64, 1, 4, 1), (128, 128, 64, 2, 3, 1), (128, 64, 64, 2, 5, 3),
                                    (128, 256, 64, 1, 4, 2), (256, 128, 64, 2, 4, 1), (256, 64, 64, 2, 6, 3),
-                                   (256, 128, 64, 1, 4, 1), (512, 64, 64, 1, 3, 1), (512, 64, 64, 1, 2, 3)])
+                                   (256, 128, 64, 1, 4, 1), (512, 64, 64, 1, 3, 1), (512, 64, 64, 1, 2, 3),
+                                   (256, 128, 64, 1, 2, 3), (256, 128, 64, 1, 3, 2)])
 def test_bf16_conv_schedules_bitwise(nk, sched):
     N, H, Wd, C, F, KH, KW = 2, 15, 17, 96, 160, 3, 3
     I = synth.small_ints(82, 1, (N, H, Wd, C))
@@ -96,3 +97,13 @@ def test_bf16_resnet_stack_layers(nk, batch):
         got = _conv(nk, I, W, st, (1, 1), pad)
         R = O.conv2d_nhwc_hwcf(O.bf16_rn(I), O.bf16_rn(W), st, (1, 1), pad)
         assert O.rel_frobenius(got, R) <= 1e-5, (li, L)
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_bf16_conv_transposed_orientation_bitwise(nk, case):
+    """Tiles of 128 filters x 256 output pixels (O^T = W^T im2col)."""
+    N, H, Wd, C, F, KH, KW, st, dl, pad = case
+    I = synth.small_ints(85, H * 100 + C, (N, H, Wd, C))
+    W = synth.small_ints(85, F * 100 + KH, (KH, KW, C, F))
+    got = _conv(nk, I, W, st, dl, pad, schedule=(256, 128, 64, 1, 4, 1))
+    np.testing.assert_array_equal(got, O.conv2d_nhwc_hwcf(I, W, st, dl, pad))
