@@ -244,6 +244,17 @@ __global__ void __launch_bounds__(WIDE ? 320 : 192, 1) tc_gemm_kernel(const __gr
   const uint32_t drain_bar = bar0 + 8u * (2 * S + 4);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(base_ptr + S * sb + staging_bytes(WIDE, MCH) + 8 * (2 * S + 5));
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  {
+    // Guard: the launch must have given this layout enough dynamic shared
+    // memory; otherwise report and leave before touching any of it.
+    uint32_t dsz;
+    asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dsz));
+    const uint32_t need = (base - raw) + (uint32_t)(S * sb + staging_bytes(WIDE, MCH) + 8 * (2 * S + 5) + 8);
+    if (need > dsz) {
+      if (threadIdx.x == 0) atomicOr(&g_tc_err, 2u);
+      return;
+    }
+  }
 
   const int warp = threadIdx.x / 32;
   const int lane = threadIdx.x % 32;
@@ -962,7 +973,8 @@ nk_schedule tc_conv_default_schedule(const ConvGeom& g, int F, int sms) {
   for (;;) {
     nk_schedule n = s;
     n.stages = s.stages + 1;
-    if (n.stages > 8 || smem_of(TC_BF16, n) > kMaxSmem) break;
+    const int need = tconv ? smem_bytes(TC_BF16, 256, n.stages) : smem_of(TC_BF16, n);
+    if (n.stages > 8 || need > kMaxSmem) break;
     s = n;
   }
   const int tiles = ctiles * ntn;
@@ -1027,7 +1039,9 @@ nk_status tc_conv(const TcConv& c, const nk_schedule& s, void* ws, size_t ws_byt
   p.budget = wait_budget();
   p.c_vec = ((reinterpret_cast<uintptr_t>(c.O) & 15) == 0 && c.F % 4 == 0 &&
              (splits == 1 || (reinterpret_cast<uintptr_t>(ws) & 15) == 0)) ? 1 : 0;
-  const int smem = smem_of(TC_BF16, s);
+  // the transposed tile keeps 256 rows of B (pixels) per stage and one chain
+  const int smem = tconv ? smem_bytes(TC_BF16, 256, s.stages) : smem_of(TC_BF16, s);
+  if (smem > kMaxSmem) return fail(NK_ERR_NO_SCHEDULE, "conv schedule needs %d bytes of shared memory", smem);
   int grid = sms * ctas_per_sm(TC_BF16, s);
   grid = grid / CL * CL;
   if (grid > p.units * CL) grid = p.units * CL;

@@ -283,6 +283,7 @@ nk_status nk_sync_status(void* stream) {
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
   uint32_t flags = 0;
   collect_device_errors(&flags);
+  if (flags & kErrLaunch) return fail(NK_ERR_CUDA, "a kernel was launched with less shared memory than its layout");
   if (flags & kErrTimeout) return fail(NK_ERR_TIMEOUT, "a bounded device wait expired");
   return NK_OK;
 }

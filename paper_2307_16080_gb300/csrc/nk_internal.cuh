@@ -26,7 +26,7 @@ nk_status require_device(int* sms = nullptr);
 // Device-side failure word.  Bit 0: a bounded wait expired.  Each
 // translation unit that owns waiting kernels defines its own copy; the host
 // reads and clears all of them in nk_sync_status.
-enum : uint32_t { kErrTimeout = 1u };
+enum : uint32_t { kErrTimeout = 1u, kErrLaunch = 2u };   // kErrLaunch: too little shared memory
 
 // Spin budget shared by the waiting kernels (set through nk_set_wait_budget).
 int64_t wait_budget();
