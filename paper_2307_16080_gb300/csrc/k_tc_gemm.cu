@@ -499,6 +499,13 @@ __global__ void __launch_bounds__(WIDE ? 320 : 192, 1) tc_gemm_kernel(const __gr
       const int row = CONV ? conv_row(p.cv, tmc, q * 32 + lane) : tmc * kBM + q * 32 + lane;
       const bool row_ok = CONV ? row >= 0 : row < t.M;
       // a wide tile has two warps per lane quarter, each draining one chain's 256 columns
+      // transposed conv: origin of this pixel tile and the pixel cursor
+      int tc_ow = 0, tc_oh = 0, tc_n = 0, cur_q = 0, cur_r = 0, cur_b = 0;
+      if constexpr (TCONV) {
+        tc_ow = (tmc % p.cv.tiles_w) * p.cv.Q;
+        tc_oh = ((tmc / p.cv.tiles_w) % p.cv.tiles_h) * p.cv.R;
+        tc_n = (tmc / (p.cv.tiles_w * p.cv.tiles_h)) * p.cv.NB;
+      }
       const int c_begin = WIDE ? ((warp - 2) / 4) * 256 : 0;
       const int c_end = WIDE ? c_begin + 256 : p.bn;
       for (int c0 = c_begin; c0 < c_end; c0 += 32) {
@@ -514,12 +521,22 @@ __global__ void __launch_bounds__(WIDE ? 320 : 192, 1) tc_gemm_kernel(const __gr
         }
         if constexpr (TCONV) {
           // lane = filter f, column j = pixel c0 + j of the tile: for each j the
-          // warp writes 32 consecutive filters of one output row.
+          // warp writes 32 consecutive filters of one output row.  The pixel's
+          // (column, row, image) inside the tile advance as a cursor shared by
+          // all lanes; columns arrive in order, so it carries across chunks.
           const int f = t.tn * kBM + q * 32 + lane;
           const float bf = (p.bias && f < p.N) ? __ldg(p.bias + f) : 0.f;
+          const ConvTile& cv = p.cv;
           for (int j = 0; j < 32; ++j) {
-            const int orow = conv_row(p.cv, t.tm, c0 + j);
-            if (orow < 0 || f >= p.N) continue;
+            const int pix = c0 + j;
+            const bool inside = pix < cv.Q * cv.R * cv.NB && tc_ow + cur_q < cv.OW && tc_oh + cur_r < cv.OH &&
+                                tc_n + cur_b < cv.N;
+            const int orow = ((tc_n + cur_b) * cv.OH + tc_oh + cur_r) * cv.OW + tc_ow + cur_q;
+            if (++cur_q == cv.Q) {
+              cur_q = 0;
+              if (++cur_r == cv.R) { cur_r = 0; ++cur_b; }
+            }
+            if (!inside || f >= p.N) continue;
             if (p.partial) {
               p.partial[((int64_t)t.split * p.M + orow) * p.N + f] = v[j];
               continue;
