@@ -62,10 +62,15 @@ nk_status nk_default_schedule(const nk_problem* p, nk_schedule* out);
 nk_status nk_schedule_features(const nk_problem* p, const nk_schedule* s, int32_t count,
                                float* features);
 
-/* Median over `reps` timed launches (after two warm-ups) of one schedule on
- * synthetic operands of the problem's shape, in milliseconds.  Synchronises
- * `stream`; allocates and keeps library-owned scratch operands (grown on
- * demand, released by nk_tune_release).                                    */
+/* Median device time, in milliseconds, of one run of a schedule on synthetic
+ * operands of the problem's shape.  After warm-up runs, `inner` back-to-back
+ * runs (so that one sample lasts about 400 us: the GPU event clock ticks in
+ * steps of about 2 us) are captured into a CUDA graph; `reps` replays, each
+ * between two CUDA events on a library-owned stream and all queued behind a
+ * short hold kernel so that host-side call overhead is not timed, give
+ * `reps` samples of time / inner.  Synchronises `stream` first; allocates
+ * and keeps library-owned scratch operands (grown on demand, released by
+ * nk_tune_release).                                                        */
 nk_status nk_time_schedule(const nk_problem* p, const nk_schedule* s, int32_t reps,
                            float* median_ms, void* stream);
 nk_status nk_tune_release(void);

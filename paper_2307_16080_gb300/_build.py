@@ -13,7 +13,7 @@ CSRC = os.path.join(PKG, "csrc")
 ROOT = os.path.dirname(PKG)
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libnk.so")
-SOURCES = ["nk_api.cu", "k_simt.cu", "k_prep.cu", "k_tc_gemm.cu", "k_mlp.cu", "tune.cu", "k_direct.cu"]
+SOURCES = ["nk_api.cu", "k_simt.cu", "k_prep.cu", "k_tc_gemm.cu", "k_tc_halo.cu", "k_mlp.cu", "tune.cu", "k_direct.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]

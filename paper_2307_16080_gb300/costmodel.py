@@ -40,7 +40,7 @@ def _r64(x):
 
 
 def training_problems(seed: int = synth.SEED_COSTMODEL):
-    """~180 matmul and conv problems (none of them a held-out ResNet layer)."""
+    """~250 matmul and conv problems (none of them a held-out ResNet layer)."""
     probs = []
     u = synth.uniform01(seed, 500, 4096)
     k = 0
@@ -51,7 +51,7 @@ def training_problems(seed: int = synth.SEED_COSTMODEL):
         return u[k - 1]
 
     precs = ["bf16", "fp8", "bf16x3"]
-    for i in range(120):
+    for i in range(150):
         prec = precs[i % 3]
         hi = 8192 if prec != "bf16x3" else 4096
         M, N, K = (_r64(math.exp(math.log(128) + (math.log(hi) - math.log(128)) * nxt())) for _ in range(3))
@@ -59,7 +59,7 @@ def training_problems(seed: int = synth.SEED_COSTMODEL):
     resnet = {(L["H"], L["C"], L["F"], L["KH"], L["stride"]) for b in (1, 8, 32) for L in synth.resnet_stack(b)}
     chans = [16, 32, 48, 64, 96, 128, 192, 256, 384]
     sizes = [8, 12, 16, 20, 24, 32, 40, 48, 64]
-    while len(probs) < 180:
+    while len(probs) < 250:
         n = [1, 2, 4, 8, 16][int(nxt() * 5)]
         h = sizes[int(nxt() * len(sizes))]
         c = chans[int(nxt() * len(chans))]

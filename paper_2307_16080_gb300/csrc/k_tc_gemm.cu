@@ -215,15 +215,8 @@ __device__ __forceinline__ int conv_row(const ConvTile& c, int tm, int r) {
 // MCH > 1 (tall tile, one CTA): MCH stacked 128-row tiles of A share one B
 // tile, each with its own accumulator chain, so narrow problems (N = 64, 128)
 // keep several independent MMA chains in flight.
-//
-// TCONV: the convolution computed transposed, O^T = W^T im2col(I): the MMA's
-// 128 rows are filters and its N = 256 columns output pixels, so narrow
-// filter counts (F <= 128) still issue full-width MMAs.  A is the filter
-// tile (3-D map of [F][taps][C]), B the input window of a 256-pixel tile.
-template <int KIND, int CL, bool GROUPED, bool CONV = false, bool PAIR = false, bool WIDE = false, int MCH = 1,
-          bool TCONV = false>
+template <int KIND, int CL, bool GROUPED, bool CONV = false, bool PAIR = false, bool WIDE = false, int MCH = 1>
 __global__ void __launch_bounds__(WIDE ? 320 : 192, 1) tc_gemm_kernel(const __grid_constant__ TcParams p) {
-  static_assert(!TCONV || (!CONV && !PAIR && !WIDE && MCH == 1 && CL == 1 && KIND == TC_BF16), "TCONV: one CTA");
   static_assert(!PAIR || CL == 2, "a CTA pair is a cluster of two");
   static_assert(!WIDE || (PAIR && KIND != TC_BF16X3 && !GROUPED), "wide tiles are pair tiles");
   static_assert(MCH == 1 || (!PAIR && !GROUPED && KIND != TC_BF16X3 && CL == 1), "tall tiles: one CTA");
@@ -356,20 +349,6 @@ __global__ void __launch_bounds__(WIDE ? 320 : 192, 1) tc_gemm_kernel(const __gr
             }
             continue;
           }
-          if constexpr (TCONV) {
-            // A: 128 filters x 64 channels of tap `tap`; B: the tap's input window
-            // for the 256-pixel tile.
-            const ConvTile& c = p.cv;
-            ptx::mbar_arrive_expect_tx(full_bar(s), (uint32_t)(kBM * kRowBytes) + p.a_box_bytes);
-            const int tap = kb / c.cblocks, c0 = (kb % c.cblocks) * 64;
-            const int kh = tap / c.KW, kw = tap % c.KW;
-            const int tw = t.tm % c.tiles_w, th = (t.tm / c.tiles_w) % c.tiles_h;
-            const int tb = t.tm / (c.tiles_w * c.tiles_h);
-            ptx::tma_load_3d(a_smem(s, 0), &p.tmB, full_bar(s), c0, tap, t.tn * kBM);
-            ptx::tma_load_4d(b_smem(s, 0), &p.tmA, full_bar(s), c0, tw * c.Q * c.sw + kw * c.dw - c.pl,
-                             th * c.R * c.sh + kh * c.dh - c.pt, tb * c.NB);
-            continue;
-          }
           if constexpr (CONV) {
             // K block kb = (filter tap, 64-channel block); the A box is the
             // input window that tap sees, shifted and strided by TMA.
@@ -499,13 +478,6 @@ __global__ void __launch_bounds__(WIDE ? 320 : 192, 1) tc_gemm_kernel(const __gr
       const int row = CONV ? conv_row(p.cv, tmc, q * 32 + lane) : tmc * kBM + q * 32 + lane;
       const bool row_ok = CONV ? row >= 0 : row < t.M;
       // a wide tile has two warps per lane quarter, each draining one chain's 256 columns
-      // transposed conv: origin of this pixel tile and the pixel cursor
-      int tc_ow = 0, tc_oh = 0, tc_n = 0, cur_q = 0, cur_r = 0, cur_b = 0;
-      if constexpr (TCONV) {
-        tc_ow = (tmc % p.cv.tiles_w) * p.cv.Q;
-        tc_oh = ((tmc / p.cv.tiles_w) % p.cv.tiles_h) * p.cv.R;
-        tc_n = (tmc / (p.cv.tiles_w * p.cv.tiles_h)) * p.cv.NB;
-      }
       const int c_begin = WIDE ? ((warp - 2) / 4) * 256 : 0;
       const int c_end = WIDE ? c_begin + 256 : p.bn;
       for (int c0 = c_begin; c0 < c_end; c0 += 32) {
@@ -518,37 +490,6 @@ __global__ void __launch_bounds__(WIDE ? 320 : 192, 1) tc_gemm_kernel(const __gr
           ptx::tmem_ld32(ta + (uint32_t)p.bn, w);
 #pragma unroll
           for (int j = 0; j < 32; ++j) v[j] += w[j];
-        }
-        if constexpr (TCONV) {
-          // lane = filter f, column j = pixel c0 + j of the tile: for each j the
-          // warp writes 32 consecutive filters of one output row.  The pixel's
-          // (column, row, image) inside the tile advance as a cursor shared by
-          // all lanes; columns arrive in order, so it carries across chunks.
-          const int f = t.tn * kBM + q * 32 + lane;
-          const float bf = (p.bias && f < p.N) ? __ldg(p.bias + f) : 0.f;
-          const ConvTile& cv = p.cv;
-          for (int j = 0; j < 32; ++j) {
-            const int pix = c0 + j;
-            const bool inside = pix < cv.Q * cv.R * cv.NB && tc_ow + cur_q < cv.OW && tc_oh + cur_r < cv.OH &&
-                                tc_n + cur_b < cv.N;
-            const int orow = ((tc_n + cur_b) * cv.OH + tc_oh + cur_r) * cv.OW + tc_ow + cur_q;
-            if (++cur_q == cv.Q) {
-              cur_q = 0;
-              if (++cur_r == cv.R) { cur_r = 0; ++cur_b; }
-            }
-            if (!inside || f >= p.N) continue;
-            if (p.partial) {
-              p.partial[((int64_t)t.split * p.M + orow) * p.N + f] = v[j];
-              continue;
-            }
-            float* dst = p.C + (int64_t)orow * p.ldc + f;
-            float x = alpha * v[j];
-            if (p.beta != 0.f) x = fmaf(p.beta, *dst, x);
-            x += bf;
-            if (p.relu) x = (x > 0.f || x != x) ? x : 0.f;
-            *dst = x;
-          }
-          continue;
         }
         const int col0 = t.tn * p.bn + c0;
         if (!GROUPED && !CONV && p.c_tma) {
@@ -703,11 +644,19 @@ int smem_of(int kind, const nk_schedule& s) {
 }
 
 template <int KIND, int CL, bool GROUPED = false, bool CONV = false, bool PAIR = false, bool WIDE = false,
-          int MCH = 1, bool TCONV = false>
+          int MCH = 1>
 nk_status launch(const TcParams& p, int grid, int smem, cudaStream_t st) {
-  auto kern = tc_gemm_kernel<KIND, CL, GROUPED, CONV, PAIR, WIDE, MCH, TCONV>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(tc_gemm_kernel)");
+  auto kern = tc_gemm_kernel<KIND, CL, GROUPED, CONV, PAIR, WIDE, MCH>;
+  // the attribute is set once per device and size (it stays set on the function)
+  static int set_bytes[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64 || set_bytes[dev] < smem) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(tc_gemm_kernel)");
+    if (dev >= 0 && dev < 64) set_bytes[dev] = smem;
+  }
+  cudaError_t e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(WIDE ? 320 : kThreads);
@@ -919,7 +868,7 @@ namespace {
 
 // Output tile (Q columns x R rows x NB images, <= 128 GEMM rows) with the
 // fewest tiles; ties go to the widest rows.
-ConvTile choose_conv_tile(const ConvGeom& g, int maxrows = 128) {
+ConvTile search_conv_tile(const ConvGeom& g, int maxrows) {
   ConvTile best{};
   int64_t best_tiles = INT64_MAX;
   for (int Q = 1; Q <= maxrows && Q <= g.ow; ++Q) {
@@ -941,6 +890,20 @@ ConvTile choose_conv_tile(const ConvGeom& g, int maxrows = 128) {
   best.KW = g.kw;
   best.cblocks = (g.c + 63) / 64;
   return best;
+}
+
+// The search above runs per call; its answer is cached per geometry.
+std::mutex g_ctile_mu;
+std::vector<std::pair<ConvGeom, ConvTile>> g_ctile_cache;
+
+ConvTile choose_conv_tile(const ConvGeom& g) {
+  std::lock_guard<std::mutex> lk(g_ctile_mu);
+  for (auto& e : g_ctile_cache)
+    if (std::memcmp(&e.first, &g, sizeof g) == 0) return e.second;
+  const ConvTile t = search_conv_tile(g, 128);
+  if (g_ctile_cache.size() > 4096) g_ctile_cache.clear();
+  g_ctile_cache.push_back({g, t});
+  return t;
 }
 
 nk_status make_conv_maps(TcParams& p, const TcConv& c, const ConvTile& t, int bn_box) {
@@ -973,35 +936,47 @@ nk_status make_conv_maps(TcParams& p, const TcConv& c, const ConvTile& t, int bn
 
 }  // namespace
 
+bool tc_conv_schedule_valid(const ConvGeom& g, int F, const nk_schedule& s) {
+  if (halo_schedule(g, s)) return halo_schedule_valid(g, F, s);
+  if (g.sw > 8 || g.sh > 8 || s.tile_n == 512) return false;
+  return tc_schedule_valid(TC_BF16, s, g.n * g.oh * g.ow, F, g.kh * g.kw * g.c);
+}
+
+// The shared-window kernel where it wins (see tc_halo_default_schedule).
+// Otherwise one 128 x (64 or 128) tile per CTA -- more, narrower tiles keep
+// more independent MMA chains busy than 256-wide ones -- with as many stages
+// as leave room for two CTAs per SM (short K loops gain more from a second
+// CTA than from deeper rings), and split-K while the grid would leave half
+// the SMs idle.
 nk_schedule tc_conv_default_schedule(const ConvGeom& g, int F, int sms) {
+  bool ok = false;
+  nk_schedule h = tc_halo_default_schedule(g, F, sms, &ok);
+  if (ok) return h;
   nk_schedule s{};
   s.tile_m = 128;
   s.tile_k = 64;
-  s.tile_n = F <= 64 ? 64 : F <= 128 ? 128 : 256;
+  s.tile_n = F <= 64 ? 64 : 128;
   s.cluster = 1;
-  // Narrow filter counts: the transposed orientation (128 filters x 256 pixels).
-  if (F <= 128) { s.tile_m = 256; s.tile_n = 128; }
-  const bool tconv = s.tile_m == 256;
-  const ConvTile t = choose_conv_tile(g, tconv ? 256 : 128);
-  const int ctiles = t.tiles_w * t.tiles_h * ((g.n + t.NB - 1) / t.NB);
-  const int ntn = tconv ? (F + 127) / 128 : (F + s.tile_n - 1) / s.tile_n;
-  s.stages = 2;
   s.split_k = 1;
+  s.stages = 2;
+  const bool two = 4 * s.tile_n <= 512;   // two CTAs' double-buffered accumulators fit in TMEM
   for (;;) {
     nk_schedule n = s;
     n.stages = s.stages + 1;
-    const int need = tconv ? smem_bytes(TC_BF16, 256, n.stages) : smem_of(TC_BF16, n);
-    if (n.stages > 8 || need > kMaxSmem) break;
+    const int need = smem_of(TC_BF16, n);
+    if (n.stages > 8 || need > kMaxSmem || (two && 2 * (need + 1024) > kMaxSmem + 1024)) break;
     s = n;
   }
-  const int tiles = ctiles * ntn;
+  const ConvTile t = choose_conv_tile(g);
+  const int ctiles = t.tiles_w * t.tiles_h * ((g.n + t.NB - 1) / t.NB);
+  const int tiles = ctiles * ((F + s.tile_n - 1) / s.tile_n);
   const int nkb = g.kh * g.kw * t.cblocks;
   while (tiles * s.split_k * 2 <= sms && nkb / (s.split_k * 2) >= 4 && s.split_k < 16) s.split_k *= 2;
   return s;
 }
 
 size_t tc_conv_ws(const TcConv& c, const nk_schedule& s) {
-  if (s.split_k <= 1) return 0;
+  if (s.split_k <= 1 || halo_schedule(c.g, s)) return 0;
   return (size_t)s.split_k * c.g.n * c.g.oh * c.g.ow * c.F * sizeof(float);
 }
 
@@ -1010,32 +985,28 @@ nk_status tc_conv(const TcConv& c, const nk_schedule& s, void* ws, size_t ws_byt
   nk_status status = require_device(&sms);
   if (status != NK_OK) return status;
   const ConvGeom& g = c.g;
+  if (halo_schedule(g, s)) return tc_halo_conv(c, s, st);
   const int M = g.n * g.oh * g.ow;
-  if (!tc_schedule_valid(TC_BF16, s, M, c.F, g.kh * g.kw * g.c))
-    return fail(NK_ERR_NO_SCHEDULE, "illegal tensor-core schedule for conv");
+  if (g.sw > 8 || g.sh > 8) return fail(NK_ERR_UNSUPPORTED, "conv stride above 8");
+  if (!tc_conv_schedule_valid(g, c.F, s)) return fail(NK_ERR_NO_SCHEDULE, "illegal tensor-core schedule for conv");
   if ((c.sI_w * 2) % 16 || (c.sI_h * 2) % 16 || (c.sI_n * 2) % 16 || (c.ldw * 2) % 16 ||
       (reinterpret_cast<uintptr_t>(c.I) & 15) || (reinterpret_cast<uintptr_t>(c.Wt) & 15))
     return fail(NK_ERR_MISALIGNED, "conv operands need 16-byte aligned bases and strides");
-  // tile_m 256 on one CTA: the transposed orientation (128 filters x 256 pixels)
-  const bool tconv = s.tile_m == 256 && s.cluster == 1;
-  if (tconv && s.tile_n != 128) return fail(NK_ERR_NO_SCHEDULE, "transposed conv tiles use tile_n 128");
-  const ConvTile t = choose_conv_tile(g, tconv ? 256 : 128);
-  if (g.sw > 8 || g.sh > 8) return fail(NK_ERR_UNSUPPORTED, "conv stride above 8");
+  const ConvTile t = choose_conv_tile(g);
   TcParams p;
   memset(&p, 0, sizeof p);
   const int CL = s.cluster;
-  if (s.tile_n == 512) return fail(NK_ERR_NO_SCHEDULE, "wide 256 x 512 tiles are for matmul");
-  if ((status = make_conv_maps(p, c, t, tconv ? kBM : s.tile_n / CL)) != NK_OK) return status;
+  if ((status = make_conv_maps(p, c, t, s.tile_n / CL)) != NK_OK) return status;
   p.cv = t;
   p.a_box_bytes = (uint32_t)(t.Q * t.R * t.NB * kRowBytes);
   p.M = M; p.N = c.F; p.K = g.kh * g.kw * g.c;
-  p.bn = tconv ? 256 : s.tile_n;
+  p.bn = s.tile_n;
   p.stages = s.stages;
-  const int mch = tconv ? 1 : chains_of(s);
+  const int mch = chains_of(s);
   const int ctiles = t.tiles_w * t.tiles_h * ((g.n + t.NB - 1) / t.NB);
   const int tm = (ctiles + mch - 1) / mch;
   p.tiles_m = (tm + CL - 1) / CL * CL;
-  p.tiles_n = tconv ? (c.F + kBM - 1) / kBM : (c.F + s.tile_n - 1) / s.tile_n;
+  p.tiles_n = (c.F + s.tile_n - 1) / s.tile_n;
   p.nkb = g.kh * g.kw * t.cblocks;
   int splits = s.split_k > p.nkb ? p.nkb : s.split_k;
   p.kb_per_split = (p.nkb + splits - 1) / splits;
@@ -1056,15 +1027,13 @@ nk_status tc_conv(const TcConv& c, const nk_schedule& s, void* ws, size_t ws_byt
   p.budget = wait_budget();
   p.c_vec = ((reinterpret_cast<uintptr_t>(c.O) & 15) == 0 && c.F % 4 == 0 &&
              (splits == 1 || (reinterpret_cast<uintptr_t>(ws) & 15) == 0)) ? 1 : 0;
-  // the transposed tile keeps 256 rows of B (pixels) per stage and one chain
-  const int smem = tconv ? smem_bytes(TC_BF16, 256, s.stages) : smem_of(TC_BF16, s);
+  const int smem = smem_of(TC_BF16, s);
   if (smem > kMaxSmem) return fail(NK_ERR_NO_SCHEDULE, "conv schedule needs %d bytes of shared memory", smem);
   int grid = sms * ctas_per_sm(TC_BF16, s);
   grid = grid / CL * CL;
   if (grid > p.units * CL) grid = p.units * CL;
   if (grid < CL) grid = CL;
-  if (tconv) status = launch<TC_BF16, 1, false, false, false, false, 1, true>(p, grid, smem, st);
-  else if (mch == 2) status = launch<TC_BF16, 1, false, true, false, false, 2>(p, grid, smem, st);
+  if (mch == 2) status = launch<TC_BF16, 1, false, true, false, false, 2>(p, grid, smem, st);
   else if (mch == 4) status = launch<TC_BF16, 1, false, true, false, false, 4>(p, grid, smem, st);
   else if (s.tile_m == 256) status = launch<TC_BF16, 2, false, true, true>(p, grid, smem, st);
   else if (CL == 2) status = launch<TC_BF16, 2, false, true>(p, grid, smem, st);

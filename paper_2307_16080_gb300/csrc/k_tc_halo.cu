@@ -1,0 +1,586 @@
+// k_tc_halo.cu -- stride-1 linalg.conv_2d_nhwc_hwcf on the tensor cores from
+// one shared input window per tile.
+//
+// O[n,oh,ow,f] = sum_{kh,kw,c} I[n, oh+kh*dh-pt, ow+kw*dw-pl, c] W[kh,kw,c,f]
+// (Sec. 4.1, the conv loop nest, here in NHWC/HWCF with dilation and zero
+// padding).  As an implicit GEMM, filter tap (kh, kw) reads the input pixels
+// under the output tile shifted by (kh*dh, kw*dw).  With stride 1 those
+// shifted views nearly coincide: an output tile of R rows x Q columns only
+// ever reads a window of WR = R + (KH-1)*dh input rows by P = Q + (KW-1)*dw
+// input columns.  That window is brought into shared memory once per
+// 64-channel block by one 4-D TMA box -- one 128-byte swizzled row per input
+// pixel, P pixels per window row -- and all KH*KW taps read it in place.
+//
+// Row m of the tile's GEMM is window pixel m, i.e. output (y, x) of image b
+// is m = (b*WR + y)*P + x; the P - Q columns x >= Q of each row (and the
+// KH-1 halo rows after each image) are computed and discarded.  Tap (kh, kw)
+// is then the same window starting kh*dh*P + kw*dw rows later, which is just
+// a later start address in the MMA's shared-memory descriptor: the 128B
+// swizzle is a function of the address bits (each row keeps its phase), so a
+// start on any 128-byte row is valid.  The tap-by-tap path reloads a shifted
+// box per tap, KH*KW loads of nearly the same pixels.
+//
+// MCH stacked 128-row accumulator chains cover one window of up to
+// MCH*128 GEMM rows and share every weight tile.  The filter tiles
+// ([F][taps][C], K-major) stream through their own ring, or stay resident
+// for the whole launch when one N tile holds all filters and they fit.
+//
+//   warp 0      TMA producer: window slots (one per 64-channel block) and
+//               weight tiles (one per tap and channel block).
+//   warp 1      TMEM allocation; one thread issues tcgen05.mma, M = 128,
+//               N = BN, K = 16, MCH chains x 4 K steps per tap.
+//   warps 2..5  epilogue: tcgen05.ld, bias, beta*O, ReLU, FP32 stores of the
+//               valid rows, overlapped with the next tile through the second
+//               accumulator buffer.
+//
+// Every wait is bounded (tc_ptx.cuh); on expiry the CTA drains its copies and
+// MMAs, frees TMEM and exits, and the host reports NK_ERR_TIMEOUT.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <climits>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "nk_internal.cuh"
+#include "tc_ptx.cuh"
+
+namespace nk {
+
+__device__ unsigned int g_halo_err;
+
+uint32_t halo_read_and_clear_errors() {
+  unsigned int v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_halo_err, sizeof v) != cudaSuccess) return 0;
+  const unsigned int z = 0;
+  cudaMemcpyToSymbol(g_halo_err, &z, sizeof z);
+  return v;
+}
+
+namespace {
+
+constexpr int kThreads = 192;
+constexpr int kRow = 128;            // bytes per pixel row (64 BF16 channels) / per filter row
+constexpr int kMaxSmem = 232448;     // 227 KB opt-in limit
+constexpr int kBarBytes = 1024;      // barriers (at most 127), TMEM slot and abort flag
+
+struct HaloTile {
+  int Q, R, NB;          // output columns, rows and images of a tile
+  int P, WR;             // window row pitch (pixels) and window rows per image
+  int rows;              // pixels one window box writes: NB * WR * P
+  int slot_rows;         // rows reserved per window slot (>= rows and >= the last row any tap reads)
+  int tiles_w, tiles_h, tiles_b;
+  int N, OH, OW, KH, KW, dh, dw, pt, pl;
+  int cblocks;           // 64-channel blocks
+};
+
+struct HaloParams {
+  CUtensorMap tmI;       // 4-D input {C, W, H, N}, box {64, P, WR, NB}
+  CUtensorMap tmW;       // 3-D filters {C, taps, F}, box {64, 1, BN}
+  HaloTile t;
+  int F, bn;
+  int wslots, bslots;    // window ring depth, weight ring depth
+  int resident;          // weights loaded once (bslots == taps * cblocks, one N tile)
+  int tiles_m, tiles_n, units;
+  uint32_t slot_bytes;   // bytes per window slot (1024-aligned)
+  float* O;              // [N*OH*OW][F]
+  const float* bias;
+  int relu;
+  float beta;
+  int c_vec;
+  int64_t budget;
+};
+
+// First GEMM row a tap reads: tap (kh, kw) sees the window kh*dh rows down
+// and kw*dw columns right.
+__device__ __forceinline__ int tap_offset(const HaloTile& t, int tap) {
+  const int kh = tap / t.KW, kw = tap - kh * t.KW;
+  return kh * t.dh * t.P + kw * t.dw;
+}
+
+template <int MCH>
+__global__ void __launch_bounds__(kThreads, 1) halo_conv_kernel(const __grid_constant__ HaloParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = ptx::smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023) & ~1023u;
+  uint8_t* base_ptr = smem_raw + (base - raw);
+  const HaloTile& t = p.t;
+  const int WS = p.wslots, BS = p.bslots;
+  const int taps = t.KH * t.KW;
+  const uint32_t wbase = base;                                   // window slots
+  const uint32_t bbase = wbase + (uint32_t)WS * p.slot_bytes;    // weight slots
+  const uint32_t b_tile = (uint32_t)p.bn * kRow;
+  const uint32_t bar0 = bbase + (uint32_t)BS * b_tile;
+  auto wfull = [&](int s) { return bar0 + 8u * s; };
+  auto wempty = [&](int s) { return bar0 + 8u * (WS + s); };
+  auto bfull = [&](int s) { return bar0 + 8u * (2 * WS + s); };
+  auto bempty = [&](int s) { return bar0 + 8u * (2 * WS + BS + s); };
+  auto tfull = [&](int b) { return bar0 + 8u * (2 * WS + 2 * BS + b); };
+  auto tempty = [&](int b) { return bar0 + 8u * (2 * WS + 2 * BS + 2 + b); };
+  const uint32_t drain_bar = bar0 + 8u * (2 * WS + 2 * BS + 4);
+  const uint32_t nbars = (uint32_t)(2 * WS + 2 * BS + 5);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(base_ptr + (bar0 - base) + 8u * nbars);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  {
+    // The launch must have given this layout enough dynamic shared memory.
+    uint32_t dsz;
+    asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dsz));
+    const uint32_t need = (bar0 - raw) + 8u * nbars + 8u;
+    if (need > dsz || 8u * nbars + 8u > (uint32_t)kBarBytes) {
+      if (threadIdx.x == 0) atomicOr(&g_halo_err, 2u);
+      return;
+    }
+  }
+  const int warp = threadIdx.x / 32;
+  const int lane = threadIdx.x % 32;
+  const uint32_t acc_cols = (uint32_t)(MCH * p.bn);
+  const uint32_t tmem_cols = 2u * acc_cols;   // 128, 256 or 512: a power of two >= 32
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < WS; ++s) {
+      ptx::mbar_init(wfull(s), 1);
+      ptx::mbar_init(wempty(s), 1);
+    }
+    for (int s = 0; s < BS; ++s) {
+      ptx::mbar_init(bfull(s), 1);
+      ptx::mbar_init(bempty(s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      ptx::mbar_init(tfull(b), 1);
+      ptx::mbar_init(tempty(b), 4);   // one arrival per epilogue warp
+    }
+    ptx::mbar_init(drain_bar, 1);
+    *abort_flag = 0;
+    ptx::fence_mbar_init();
+  }
+  if (warp == 0 && lane == 0) {
+    ptx::tma_prefetch_desc(&p.tmI);
+    ptx::tma_prefetch_desc(&p.tmW);
+  }
+  if (warp == 1) {
+    ptx::tmem_alloc(ptx::smem_u32(tmem_slot), tmem_cols);
+    ptx::tmem_relinquish();
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      int wc = 0, bc = 0;   // window and weight copies issued
+      bool ok = true;
+      for (int u = blockIdx.x; u < p.units && ok; u += gridDim.x) {
+        const int tn = u / p.tiles_m, tm = u - tn * p.tiles_m;
+        const int tw = tm % t.tiles_w, th = (tm / t.tiles_w) % t.tiles_h, tb = tm / (t.tiles_w * t.tiles_h);
+        const bool load_w = !p.resident || u == (int)blockIdx.x;
+        for (int cb = 0; cb < t.cblocks && ok; ++cb) {
+          {
+            const int s = wc % WS;
+            const uint32_t ph = (uint32_t)(wc / WS) & 1u;
+            if (!ptx::mbar_wait(wempty(s), ph ^ 1u, p.budget, abort_flag, &g_halo_err)) { ok = false; break; }
+            ptx::mbar_arrive_expect_tx(wfull(s), (uint32_t)t.rows * kRow);
+            ptx::tma_load_4d(wbase + (uint32_t)s * p.slot_bytes, &p.tmI, wfull(s), cb * 64, tw * t.Q - t.pl,
+                             th * t.R - t.pt, tb * t.NB);
+            ++wc;
+          }
+          if (!load_w) continue;
+          for (int tap = 0; tap < taps; ++tap) {
+            const int s = bc % BS;
+            const uint32_t ph = (uint32_t)(bc / BS) & 1u;
+            if (!ptx::mbar_wait(bempty(s), ph ^ 1u, p.budget, abort_flag, &g_halo_err)) { ok = false; break; }
+            ptx::mbar_arrive_expect_tx(bfull(s), b_tile);
+            ptx::tma_load_3d(bbase + (uint32_t)s * b_tile, &p.tmW, bfull(s), cb * 64, tap, tn * p.bn);
+            ++bc;
+          }
+        }
+      }
+      // Drain: the last copy issued into each slot lands before exit.
+      for (int j = wc - 1; j >= 0 && j >= wc - WS; --j)
+        ptx::mbar_drain(wfull(j % WS), (uint32_t)(j / WS) & 1u, 100000000ull);
+      for (int j = bc - 1; j >= 0 && j >= bc - BS; --j)
+        ptx::mbar_drain(bfull(j % BS), (uint32_t)(j / BS) & 1u, 100000000ull);
+    }
+  } else if (warp == 1) {
+    // -------------------------------------------------------------- MMA
+    if (lane == 0) {
+      const uint32_t idesc = ptx::make_idesc(1, 128, p.bn);
+      int wc = 0, bc = 0, tc = 0;
+      bool ok = true;
+      for (int u = blockIdx.x; u < p.units && ok; u += gridDim.x, ++tc) {
+        const int acc = tc & 1;
+        const uint32_t aph = (uint32_t)(tc >> 1) & 1u;
+        if (!ptx::mbar_wait(tempty(acc), aph ^ 1u, p.budget, abort_flag, &g_halo_err)) break;
+        ptx::tc_fence_after();
+        const uint32_t d = tmem_base + (uint32_t)acc * acc_cols;
+        for (int cb = 0; cb < t.cblocks && ok; ++cb) {
+          const int ws = wc % WS;
+          if (!ptx::mbar_wait(wfull(ws), (uint32_t)(wc / WS) & 1u, p.budget, abort_flag, &g_halo_err)) {
+            ok = false;
+            break;
+          }
+          ptx::tc_fence_after();
+          const uint32_t win = wbase + (uint32_t)ws * p.slot_bytes;
+          for (int tap = 0; tap < taps; ++tap) {
+            // resident weights: slot = K block, phase 0 completed once and stays so
+            const int kb = cb * taps + tap;
+            const int bs = p.resident ? kb : bc % BS;
+            const uint32_t bph = p.resident ? 0u : (uint32_t)(bc / BS) & 1u;
+            if (!ptx::mbar_wait(bfull(bs), bph, p.budget, abort_flag, &g_halo_err)) { ok = false; break; }
+            ptx::tc_fence_after();
+            const uint32_t a0 = win + (uint32_t)tap_offset(t, tap) * kRow;
+            const uint32_t b0 = bbase + (uint32_t)bs * b_tile;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const uint64_t bd = ptx::sw128_desc(b0 + 32u * k);
+              const uint32_t accum = (kb > 0 || k > 0) ? 1u : 0u;
+#pragma unroll
+              for (int ch = 0; ch < MCH; ++ch)
+                ptx::tc_mma<0>(d + (uint32_t)(ch * p.bn), ptx::sw128_desc(a0 + (uint32_t)(ch * 128 * kRow) + 32u * k),
+                               bd, idesc, accum);
+            }
+            if (!p.resident) {
+              ptx::tc_commit(bempty(bs));
+              ++bc;
+            }
+          }
+          if (!ok) break;
+          ptx::tc_commit(wempty(ws));
+          ++wc;
+        }
+        if (!ok) break;
+        ptx::tc_commit(tfull(acc));
+      }
+      ptx::tc_commit(drain_bar);
+      ptx::mbar_drain(drain_bar, 0, 100000000ull);
+    }
+  } else {
+    // ---------------------------------------------------------- epilogue
+    const int q = warp & 3;   // TMEM lane quarter this warp may read
+    const int img_rows = t.WR * t.P;
+    int tc = 0;
+    for (int u = blockIdx.x; u < p.units; u += gridDim.x, ++tc) {
+      const int tn = u / p.tiles_m, tm = u - tn * p.tiles_m;
+      const int tw = tm % t.tiles_w, th = (tm / t.tiles_w) % t.tiles_h, tb = tm / (t.tiles_w * t.tiles_h);
+      const int acc = tc & 1;
+      if (!ptx::mbar_wait(tfull(acc), (uint32_t)(tc >> 1) & 1u, p.budget, abort_flag, &g_halo_err)) break;
+      ptx::tc_fence_after();
+      for (int ch = 0; ch < MCH; ++ch) {
+        // GEMM row m = window pixel (b, y, x); valid when it is an output pixel
+        const int m = ch * 128 + q * 32 + lane;
+        const int b = m / img_rows, r = m - b * img_rows;
+        const int y = r / t.P, x = r - y * t.P;
+        const int n = tb * t.NB + b, oh = th * t.R + y, ow = tw * t.Q + x;
+        const bool row_ok = b < t.NB && y < t.R && x < t.Q && n < t.N && oh < t.OH && ow < t.OW;
+        float* orow = p.O + ((int64_t)(n * t.OH + oh) * t.OW + ow) * p.F;
+        for (int c0 = 0; c0 < p.bn; c0 += 32) {
+          float v[32];
+          ptx::tmem_ld32(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)acc * acc_cols +
+                             (uint32_t)(ch * p.bn + c0),
+                         v);
+          const int col0 = tn * p.bn + c0;
+          if (!row_ok || col0 >= p.F) continue;
+          float* dst = orow + col0;
+          if (p.c_vec && col0 + 32 <= p.F) {
+#pragma unroll
+            for (int j = 0; j < 32; j += 4) {
+              float o[4];
+              float4 cin = make_float4(0.f, 0.f, 0.f, 0.f);
+              if (p.beta != 0.f) cin = *reinterpret_cast<const float4*>(dst + j);
+              const float ci[4] = {cin.x, cin.y, cin.z, cin.w};
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                float xv = v[j + e];
+                if (p.beta != 0.f) xv = fmaf(p.beta, ci[e], xv);
+                if (p.bias) xv += __ldg(p.bias + col0 + j + e);
+                if (p.relu) xv = (xv > 0.f || xv != xv) ? xv : 0.f;
+                o[e] = xv;
+              }
+              *reinterpret_cast<float4*>(dst + j) = make_float4(o[0], o[1], o[2], o[3]);
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              if (col0 + j >= p.F) continue;
+              float xv = v[j];
+              if (p.beta != 0.f) xv = fmaf(p.beta, dst[j], xv);
+              if (p.bias) xv += __ldg(p.bias + col0 + j);
+              if (p.relu) xv = (xv > 0.f || xv != xv) ? xv : 0.f;
+              dst[j] = xv;
+            }
+          }
+        }
+      }
+      ptx::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) ptx::mbar_arrive(tempty(acc));
+    }
+  }
+
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  if (warp == 1) ptx::tmem_dealloc(tmem_base, tmem_cols);
+}
+
+// ------------------------------------------------------------------ host
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+  });
+  return fn;
+}
+
+int taps_of(const ConvGeom& g) { return g.kh * g.kw; }
+int chains_of(const nk_schedule& s) { return s.tile_m / 128; }
+
+// Largest tap offset in GEMM rows.
+int max_offset(const ConvGeom& g, int P) { return (g.kh - 1) * g.dh * P + (g.kw - 1) * g.dw; }
+
+// Window tile for `mch` chains: the fewest tiles whose valid output rows
+// all fall inside the first mch*128 GEMM rows; ties go to the smaller window.
+// Returns false when no tile fits (box extents <= 256, slot within `max_slot_rows`).
+bool choose_halo_tile(const ConvGeom& g, int mch, int max_slot_rows, HaloTile* out) {
+  const int maxrows = mch * 128;
+  const int halo_w = (g.kw - 1) * g.dw, halo_h = (g.kh - 1) * g.dh;
+  bool found = false;
+  int64_t best_tiles = INT64_MAX;
+  int best_slot = INT_MAX;
+  HaloTile best{};
+  for (int Q = 1; Q <= g.ow && Q + halo_w <= 256; ++Q) {
+    const int P = Q + halo_w;
+    if (Q > maxrows) break;
+    for (int R = 1; R <= g.oh && R + halo_h <= 256; ++R) {
+      const int WR = R + halo_h;
+      const int last = (R - 1) * P + Q;   // rows one image's valid outputs span
+      if (last > maxrows) break;
+      int NB = 1 + (maxrows - last) / (WR * P);
+      NB = std::min(std::min(NB, g.n), 256);
+      const int rows = NB * WR * P;
+      const int slot = (std::max(rows, maxrows + max_offset(g, P)) + 7) / 8 * 8;
+      if (slot > max_slot_rows) continue;
+      const int64_t tiles = (int64_t)((g.n + NB - 1) / NB) * ((g.oh + R - 1) / R) * ((g.ow + Q - 1) / Q);
+      if (tiles < best_tiles || (tiles == best_tiles && slot < best_slot)) {
+        best_tiles = tiles;
+        best_slot = slot;
+        best.Q = Q; best.R = R; best.NB = NB; best.P = P; best.WR = WR;
+        best.rows = rows; best.slot_rows = slot;
+        found = true;
+      }
+    }
+  }
+  if (!found) return false;
+  best.tiles_w = (g.ow + best.Q - 1) / best.Q;
+  best.tiles_h = (g.oh + best.R - 1) / best.R;
+  best.tiles_b = (g.n + best.NB - 1) / best.NB;
+  best.N = g.n; best.OH = g.oh; best.OW = g.ow;
+  best.KH = g.kh; best.KW = g.kw; best.dh = g.dh; best.dw = g.dw; best.pt = g.pt; best.pl = g.pl;
+  best.cblocks = (g.c + 63) / 64;
+  *out = best;
+  return true;
+}
+
+// The tile choice is a search over (Q, R); it is cached per geometry so a
+// repeated call costs a lookup.
+struct TileKey {
+  ConvGeom g;
+  int mch;
+};
+std::mutex g_tile_mu;
+std::vector<std::pair<TileKey, std::pair<bool, HaloTile>>> g_tile_cache;
+
+bool cached_halo_tile(const ConvGeom& g, int mch, HaloTile* out) {
+  // The window slot may use at most what is left beside two weight tiles of
+  // 256 rows and the barriers; the real budget is checked per schedule.
+  const int max_slot_rows = (kMaxSmem - 1024 - kBarBytes) / kRow;
+  std::lock_guard<std::mutex> lk(g_tile_mu);
+  for (auto& e : g_tile_cache)
+    if (e.first.mch == mch && std::memcmp(&e.first.g, &g, sizeof g) == 0) {
+      *out = e.second.second;
+      return e.second.first;
+    }
+  HaloTile t{};
+  const bool ok = choose_halo_tile(g, mch, max_slot_rows, &t);
+  if (g_tile_cache.size() > 4096) g_tile_cache.clear();
+  TileKey k;
+  std::memset(&k, 0, sizeof k);
+  k.g = g;
+  k.mch = mch;
+  g_tile_cache.push_back({k, {ok, t}});
+  *out = t;
+  return ok;
+}
+
+struct HaloLayout {
+  HaloTile t;
+  int wslots, bslots, resident;
+  uint32_t slot_bytes;
+  int smem;
+};
+
+// CTAs of this layout that fit on one SM: shared memory (each CTA also
+// costs 1 KB of reserved space) and two accumulator buffers of MCH * BN
+// TMEM columns each.
+int halo_ctas(int smem, int mch, int bn) {
+  const bool tmem2 = 4 * mch * bn <= 512;
+  return (tmem2 && 2 * (smem + 1024) <= kMaxSmem + 1024) ? 2 : 1;
+}
+
+// Shared-memory layout of a schedule: stages = window slots.  The weights
+// stay resident when one N tile holds every filter and all K blocks fit;
+// otherwise they stream through a ring of up to 8 tiles (at least two).  Of
+// the two, the layout that lets more CTAs (independent MMA chains) share an
+// SM wins; on a tie, resident weights.
+bool halo_layout(const ConvGeom& g, int F, const nk_schedule& s, HaloLayout* L) {
+  const int mch = chains_of(s);
+  if (!cached_halo_tile(g, mch, &L->t)) return false;
+  L->slot_bytes = (uint32_t)((L->t.slot_rows * kRow + 1023) / 1024 * 1024);
+  L->wslots = s.stages;
+  const int fixed = 1024 + s.stages * (int)L->slot_bytes + kBarBytes;
+  const int b_tile = s.tile_n * kRow;
+  const int nkb = taps_of(g) * L->t.cblocks;
+  const int room = (kMaxSmem - fixed) / b_tile;
+  if (room < 2) return false;
+  // streamed ring: deepest ring that keeps the CTA count of a 2-slot ring
+  int ring = std::min(std::min(room, nkb < 2 ? 2 : nkb), 8);
+  const int want = halo_ctas(fixed + 2 * b_tile, mch, s.tile_n);
+  while (ring > 2 && halo_ctas(fixed + ring * b_tile, mch, s.tile_n) < want) --ring;
+  L->resident = 0;
+  L->bslots = ring;
+  const bool one_n = (F + s.tile_n - 1) / s.tile_n == 1;
+  if (one_n && room >= nkb && 8 * (2 * s.stages + 2 * nkb + 5) + 8 <= kBarBytes &&
+      halo_ctas(fixed + nkb * b_tile, mch, s.tile_n) >= halo_ctas(fixed + ring * b_tile, mch, s.tile_n)) {
+    L->resident = 1;
+    L->bslots = nkb;
+  }
+  L->smem = fixed + L->bslots * b_tile;
+  if (8 * (2 * L->wslots + 2 * L->bslots + 5) + 8 > kBarBytes) return false;
+  return L->smem <= kMaxSmem;
+}
+
+template <int MCH>
+nk_status launch(const HaloParams& p, int grid, int smem, cudaStream_t st) {
+  auto kern = halo_conv_kernel<MCH>;
+  static int set_bytes[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64 || set_bytes[dev] < smem) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(halo_conv_kernel)");
+    if (dev >= 0 && dev < 64) set_bytes[dev] = smem;
+  }
+  kern<<<grid, kThreads, smem, st>>>(p);
+  return check_launch("halo_conv_kernel");
+}
+
+}  // namespace
+
+bool halo_schedule(const ConvGeom& g, const nk_schedule& s) {
+  return taps_of(g) > 1 && s.tile_k == 64 * taps_of(g);
+}
+
+bool halo_schedule_valid(const ConvGeom& g, int F, const nk_schedule& s) {
+  if (!halo_schedule(g, s)) return false;
+  if (g.sh != 1 || g.sw != 1) return false;
+  if (s.tile_m != 128 && s.tile_m != 256 && s.tile_m != 512) return false;
+  if (s.tile_n != 64 && s.tile_n != 128 && s.tile_n != 256) return false;
+  if (chains_of(s) * s.tile_n > 256) return false;   // two accumulator buffers in 512 TMEM columns
+  if (s.cluster != 1 || s.split_k != 1) return false;
+  if (s.stages < 1 || s.stages > 4) return false;
+  HaloLayout L;
+  return halo_layout(g, F, s, &L);
+}
+
+// Measured on GB300 (ResNet layers, batch 1..32): the window path wins when
+// one 64-channel block covers C; deeper layers (C >= 128) stream so many
+// weight tiles per window that the per-tap path is faster.  One chain and one
+// window slot keep two CTAs (two independent MMA chains) per SM.
+nk_schedule tc_halo_default_schedule(const ConvGeom& g, int F, int sms, bool* ok) {
+  (void)sms;
+  nk_schedule best{};
+  *ok = false;
+  if (taps_of(g) <= 1 || g.sh != 1 || g.sw != 1 || g.c > 64) return best;
+  const int tn = F <= 64 ? 64 : F <= 128 ? 128 : 256;
+  for (int st = 1; st <= 2; ++st) {
+    nk_schedule s{128, tn, 64 * taps_of(g), 1, st, 1};
+    if (halo_schedule_valid(g, F, s)) {
+      *ok = true;
+      return s;
+    }
+  }
+  return best;
+}
+
+nk_status tc_halo_conv(const TcConv& c, const nk_schedule& s, cudaStream_t st) {
+  int sms = 0;
+  nk_status status = require_device(&sms);
+  if (status != NK_OK) return status;
+  const ConvGeom& g = c.g;
+  HaloLayout L;
+  if (!halo_schedule_valid(g, c.F, s) || !halo_layout(g, c.F, s, &L))
+    return fail(NK_ERR_NO_SCHEDULE, "illegal window-conv schedule");
+  if ((c.sI_w * 2) % 16 || (c.sI_h * 2) % 16 || (c.sI_n * 2) % 16 || (c.ldw * 2) % 16 ||
+      (reinterpret_cast<uintptr_t>(c.I) & 15) || (reinterpret_cast<uintptr_t>(c.Wt) & 15))
+    return fail(NK_ERR_MISALIGNED, "conv operands need 16-byte aligned rows");
+  auto fn = encode_fn();
+  if (!fn) return fail(NK_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+  HaloParams p{};
+  p.t = L.t;
+  const HaloTile& t = L.t;
+  {
+    cuuint64_t dims[4] = {(cuuint64_t)g.c, (cuuint64_t)g.w, (cuuint64_t)g.h, (cuuint64_t)g.n};
+    cuuint64_t strides[3] = {(cuuint64_t)c.sI_w * 2, (cuuint64_t)c.sI_h * 2, (cuuint64_t)c.sI_n * 2};
+    cuuint32_t box[4] = {64, (cuuint32_t)t.P, (cuuint32_t)t.WR, (cuuint32_t)t.NB};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    CUresult r = fn(&p.tmI, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(c.I), dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(NK_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d) for the conv window", (int)r);
+  }
+  {
+    const int taps = taps_of(g);
+    cuuint64_t dims[3] = {(cuuint64_t)g.c, (cuuint64_t)taps, (cuuint64_t)c.F};
+    cuuint64_t strides[2] = {(cuuint64_t)c.ldw * 2, (cuuint64_t)taps * c.ldw * 2};
+    cuuint32_t box[3] = {64, 1, (cuuint32_t)s.tile_n};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = fn(&p.tmW, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(c.Wt), dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(NK_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d) for the conv filters", (int)r);
+  }
+  p.F = c.F;
+  p.bn = s.tile_n;
+  p.wslots = L.wslots;
+  p.bslots = L.bslots;
+  p.resident = L.resident;
+  p.slot_bytes = L.slot_bytes;
+  p.tiles_m = t.tiles_w * t.tiles_h * t.tiles_b;
+  p.tiles_n = (c.F + s.tile_n - 1) / s.tile_n;
+  p.units = p.tiles_m * p.tiles_n;
+  p.O = c.O;
+  p.bias = c.bias;
+  p.relu = c.relu;
+  p.beta = c.beta;
+  p.c_vec = ((reinterpret_cast<uintptr_t>(c.O) & 15) == 0 && c.F % 4 == 0) ? 1 : 0;
+  p.budget = wait_budget();
+  if (p.units == 0) return NK_OK;
+  const int grid = std::min(p.units, sms * halo_ctas(L.smem, chains_of(s), s.tile_n));
+  switch (chains_of(s)) {
+    case 1: return launch<1>(p, grid, L.smem, st);
+    case 2: return launch<2>(p, grid, L.smem, st);
+    default: return launch<4>(p, grid, L.smem, st);
+  }
+}
+
+}  // namespace nk

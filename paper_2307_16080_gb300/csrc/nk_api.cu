@@ -75,7 +75,7 @@ int64_t wait_budget() {
 }
 
 nk_status collect_device_errors(uint32_t* flags) {
-  *flags = tc_read_and_clear_errors();
+  *flags = tc_read_and_clear_errors() | halo_read_and_clear_errors();
   return NK_OK;
 }
 
@@ -434,16 +434,17 @@ static nk_status plan_tc_conv(const nk_tensor* I, const nk_tensor* W, const nk_t
       cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
     sms = v;
   const int F = (int)W->shape[3];
-  nk_schedule d = tc_conv_default_schedule(g, F, sms);
   nk_schedule S = user ? *user : nk_schedule{0, 0, 0, 0, 0, 0};
-  if (S.tile_m == 0) S.tile_m = d.tile_m;
-  if (S.tile_n == 0) S.tile_n = d.tile_n;
-  if (S.tile_k == 0) S.tile_k = d.tile_k;
-  if (S.cluster == 0) S.cluster = d.cluster;
-  if (S.stages == 0) S.stages = d.stages;
-  if (S.split_k == 0) S.split_k = d.split_k;
-  if (!tc_schedule_valid(TC_BF16, S, g.n * g.oh * g.ow, F, g.kh * g.kw * g.c) || S.tile_n == 512)
-    return fail(NK_ERR_NO_SCHEDULE, "illegal conv schedule");
+  if (!S.tile_m || !S.tile_n || !S.tile_k || !S.cluster || !S.stages || !S.split_k) {
+    const nk_schedule d = tc_conv_default_schedule(g, F, sms);
+    if (S.tile_m == 0) S.tile_m = d.tile_m;
+    if (S.tile_n == 0) S.tile_n = d.tile_n;
+    if (S.tile_k == 0) S.tile_k = d.tile_k;
+    if (S.cluster == 0) S.cluster = d.cluster;
+    if (S.stages == 0) S.stages = d.stages;
+    if (S.split_k == 0) S.split_k = d.split_k;
+  }
+  if (!tc_conv_schedule_valid(g, F, S)) return fail(NK_ERR_NO_SCHEDULE, "illegal conv schedule");
   P.sched = S;
   P.Cp = (g.c + 7) / 8 * 8;
   P.cast_i = I->dtype == NK_F32;

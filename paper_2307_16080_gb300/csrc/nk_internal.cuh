@@ -146,9 +146,22 @@ struct TcConv {
   int relu;
   float beta;
 };
+// tc_conv dispatches a window schedule (see below) to tc_halo_conv.
 nk_status tc_conv(const TcConv& c, const nk_schedule& s, void* ws, size_t ws_bytes, cudaStream_t st);
 size_t tc_conv_ws(const TcConv& c, const nk_schedule& s);
 nk_schedule tc_conv_default_schedule(const ConvGeom& g, int F, int sms);
+bool tc_conv_schedule_valid(const ConvGeom& g, int F, const nk_schedule& s);
+
+// Stride-1 convolution from one shared input window per tile (k_tc_halo.cu).
+// A conv schedule with tile_k = 64 * KH * KW (one pipeline stage = one
+// 64-channel block of the window, read by every tap) selects it; tile_m =
+// 128 * chains (1, 2, 4), tile_n 64 / 128 / 256 with chains * tile_n <= 256,
+// stages = window slots (1..4), cluster 1, split_k 1.
+bool halo_schedule(const ConvGeom& g, const nk_schedule& s);
+bool halo_schedule_valid(const ConvGeom& g, int F, const nk_schedule& s);
+nk_status tc_halo_conv(const TcConv& c, const nk_schedule& s, cudaStream_t st);
+nk_schedule tc_halo_default_schedule(const ConvGeom& g, int F, int sms, bool* ok);
+uint32_t halo_read_and_clear_errors();
 size_t tc_gemm_ws(const TcGemm& g, const nk_schedule& s);
 // Fills unset fields of `s` with the built-in choice for this problem.
 nk_schedule tc_default_schedule(int kind, int M, int N, int K, int sms);

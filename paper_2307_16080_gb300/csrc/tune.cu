@@ -118,13 +118,23 @@ std::vector<nk_schedule> enumerate(const nk_problem* p) {
     for (int cl : {1, 2})
       for (int split : {1, 2, 4, 8, 16})
         for (int st = 2; st <= 8; ++st) {
-          if (tn == 512 && p->op == NK_OP_CONV2D) continue;
-          if (p->op == NK_OP_CONV2D && tm == 256 && cl == 1 && tn != 128) continue;   // transposed conv
           nk_schedule s{tm, tn, tk, cl, st, split};
           if (split > nkb) continue;
-          if (!tc_schedule_valid(kind, s, (int)M, (int)N, (int)K)) continue;
+          if (p->op == NK_OP_CONV2D ? !tc_conv_schedule_valid(geom_of(p), p->f, s)
+                                    : !tc_schedule_valid(kind, s, (int)M, (int)N, (int)K))
+            continue;
           out.push_back(s);
         }
+  // stride-1 convolutions: the shared-window kernel (tile_k = 64 * taps)
+  if (p->op == NK_OP_CONV2D && p->kh * p->kw > 1 && p->stride == 1) {
+    const ConvGeom g = geom_of(p);
+    for (int tm : {128, 256, 512})
+      for (int tn : {64, 128, 256})
+        for (int st = 1; st <= 4; ++st) {
+          nk_schedule s{tm, tn, 64 * p->kh * p->kw, 1, st, 1};
+          if (halo_schedule_valid(g, p->f, s)) out.push_back(s);
+        }
+  }
   return out;
 }
 
@@ -230,40 +240,128 @@ struct Runner {
   }
 };
 
-nk_status time_one(const nk_problem* p, const nk_schedule& s, int reps, float* ms, cudaStream_t st) {
+// Holds the GPU for `ns` nanoseconds of the global timer (at most 2^24
+// polls), so that the timed launches behind it are all queued before the
+// GPU reaches them and host-side launch work stays outside the timings.
+__global__ void hold_kernel(uint64_t ns) {
+  uint64_t t0, t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  for (int i = 0; i < (1 << 24); ++i) {
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    if (t - t0 >= ns) break;
+  }
+}
+
+nk_status device_flag_fail(uint32_t flags) {
+  if (flags & kErrTimeout) return fail(NK_ERR_TIMEOUT, "a bounded device wait expired while timing");
+  return fail(NK_ERR_CUDA, "a kernel reported a launch-configuration error (flags %u) while timing", flags);
+}
+
+cudaStream_t timing_stream() {
+  static cudaStream_t st[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return nullptr;
+  if (!st[dev]) cudaStreamCreateWithFlags(&st[dev], cudaStreamNonBlocking);
+  return st[dev];
+}
+
+// Captures `runs` back-to-back runs of one schedule into a graph.
+nk_status capture_runs(Runner& r, const nk_schedule& s, int runs, cudaStream_t st, cudaGraphExec_t* exec) {
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture(tune)");
+  nk_status status = NK_OK;
+  for (int i = 0; i < runs && status == NK_OK; ++i) status = r.run(s, st);
+  e = cudaStreamEndCapture(st, &graph);
+  if (status != NK_OK || e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return status != NK_OK ? status : cuda_fail(e, "cudaStreamEndCapture(tune)");
+  }
+  e = cudaGraphInstantiate(exec, graph, 0);
+  cudaGraphDestroy(graph);
+  return e == cudaSuccess ? NK_OK : cuda_fail(e, "cudaGraphInstantiate(tune)");
+}
+
+// Median device time of one schedule.  Two eager runs first (errors surface,
+// caches and kernel attributes warm).  The GPU's event clock ticks in steps
+// of about 2 us, so each timed sample is a graph of `inner` back-to-back runs
+// (inner chosen so a sample lasts about 400 us) between two events, and the
+// samples are queued behind hold_kernel: what is timed is the kernels alone,
+// not the host work of a call.
+nk_status time_one(const nk_problem* p, const nk_schedule& s, int reps, float* ms, cudaStream_t user) {
   Runner r(p, s);
   void* buf = nullptr;
   nk_status status = scratch(r.padded_total(), &buf);
   if (status != NK_OK) return status;
   r.bind(static_cast<char*>(buf));
   if ((status = fill(r.op_bytes + 1024)) != NK_OK) return status;
-  cudaError_t e = cudaDeviceSynchronize();
+  cudaError_t e = user ? cudaStreamSynchronize(user) : cudaSuccess;
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+  cudaStream_t st = timing_stream();
+  if (!st) return fail(NK_ERR_CUDA, "no timing stream");
   for (int i = 0; i < 2; ++i)
     if ((status = r.run(s, st)) != NK_OK) return status;
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize(tune)");
+  {
+    uint32_t flags = 0;
+    collect_device_errors(&flags);
+    if (flags) return device_flag_fail(flags);
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  // rough duration of one run: 8 eager runs between two events
+  cudaEventRecord(e0, st);
+  for (int i = 0; i < 8 && status == NK_OK; ++i) status = r.run(s, st);
+  cudaEventRecord(e1, st);
+  e = cudaStreamSynchronize(st);
+  float rough = 0.f;
+  cudaEventElapsedTime(&rough, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (status != NK_OK) return status;
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize(tune)");
+  rough = std::max(rough / 8.f, 0.002f);
+  const int inner = std::max(1, std::min(64, (int)std::ceil(0.4f / rough)));
+  cudaGraphExec_t exec = nullptr;
+  if ((status = capture_runs(r, s, inner, st, &exec)) != NK_OK) return status;
+
   reps = reps < 1 ? 1 : reps;
   std::vector<cudaEvent_t> ev(2 * reps);
   for (auto& x : ev) cudaEventCreate(&x);
-  for (int i = 0; i < reps && status == NK_OK; ++i) {
+  e = cudaGraphLaunch(exec, st);   // warm the graph
+  // about 20 us of host work per sample, so hold the GPU that long per sample
+  const uint64_t hold = std::min<uint64_t>(50000ull + 20000ull * (uint64_t)reps, 20000000ull);
+  hold_kernel<<<1, 1, 0, st>>>(hold);
+  for (int i = 0; i < reps && e == cudaSuccess; ++i) {
     cudaEventRecord(ev[2 * i], st);
-    status = r.run(s, st);
+    e = cudaGraphLaunch(exec, st);
     cudaEventRecord(ev[2 * i + 1], st);
   }
-  e = cudaStreamSynchronize(st);
+  cudaError_t e2 = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = e2;
   std::vector<float> t(reps, 0.f);
-  for (int i = 0; i < reps; ++i) cudaEventElapsedTime(&t[i], ev[2 * i], ev[2 * i + 1]);
+  for (int i = 0; i < reps; ++i) {
+    cudaEventElapsedTime(&t[i], ev[2 * i], ev[2 * i + 1]);
+    t[i] /= (float)inner;
+  }
   for (auto& x : ev) cudaEventDestroy(x);
-  if (status != NK_OK) return status;
-  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize(tune)");
-  uint32_t flags = tc_read_and_clear_errors();
-  if (flags & kErrTimeout) return fail(NK_ERR_TIMEOUT, "a bounded device wait expired while timing");
+  cudaGraphExecDestroy(exec);
+  if (e != cudaSuccess) return cuda_fail(e, "timed replays (tune)");
+  uint32_t flags = 0;
+  collect_device_errors(&flags);
+  if (flags) return device_flag_fail(flags);
   std::sort(t.begin(), t.end());
   *ms = t[reps / 2];
   return NK_OK;
 }
 
 // (1+1) evolution strategy on the schedule grid.  Coordinates: tile_m,
-// tile_n, cluster, stages, split_k, each an ordered list of levels.  A child
+// tile_n, cluster, stages, split_k and the conv path (tile_k: per-tap K
+// blocks or the shared window), each an ordered list of levels.  A child
 // moves one coordinate one level (or, with probability 1/4, to a random
 // level); illegal or already-timed children are redrawn; the child replaces
 // the parent when it is faster.  SplitMix64 seeded from the problem, so the
@@ -281,10 +379,12 @@ struct Rng {
 
 nk_status evolve(const nk_problem* p, const std::vector<nk_schedule>& cand, int budget, int reps,
                  cudaStream_t cs, int* best_i, float* best_ms) {
-  static const int L_TM[] = {128, 256, 512}, L_TN[] = {64, 128, 256, 512}, L_CL[] = {1, 2},
-                   L_ST[] = {2, 3, 4, 5, 6, 7, 8}, L_SK[] = {1, 2, 4, 8, 16};
-  static const int* LV[5] = {L_TM, L_TN, L_CL, L_ST, L_SK};
-  static const int NL[5] = {3, 4, 2, 7, 5};
+  const int tk0 = p->precision == NK_PREC_FP8 ? 128 : 64;
+  const int tk1 = p->op == NK_OP_CONV2D ? 64 * p->kh * p->kw : tk0;
+  const int L_TM[] = {128, 256, 512}, L_TN[] = {64, 128, 256, 512}, L_CL[] = {1, 2},
+            L_ST[] = {1, 2, 3, 4, 5, 6, 7, 8}, L_SK[] = {1, 2, 4, 8, 16}, L_TK[] = {tk0, tk1};
+  const int* LV[6] = {L_TM, L_TN, L_CL, L_ST, L_SK, L_TK};
+  const int NL[6] = {3, 4, 2, 8, 5, tk1 != tk0 ? 2 : 1};
   auto level_of = [&](int c, int v) {
     for (int i = 0; i < NL[c]; ++i)
       if (LV[c][i] == v) return i;
@@ -294,7 +394,7 @@ nk_status evolve(const nk_problem* p, const std::vector<nk_schedule>& cand, int 
     for (size_t i = 0; i < cand.size(); ++i) {
       const nk_schedule& s = cand[i];
       if (s.tile_m == LV[0][lv[0]] && s.tile_n == LV[1][lv[1]] && s.cluster == LV[2][lv[2]] &&
-          s.stages == LV[3][lv[3]] && s.split_k == LV[4][lv[4]])
+          s.stages == LV[3][lv[3]] && s.split_k == LV[4][lv[4]] && s.tile_k == LV[5][lv[5]])
         return (int)i;
     }
     return -1;
@@ -308,7 +408,7 @@ nk_status evolve(const nk_problem* p, const std::vector<nk_schedule>& cand, int 
   int cur = -1;
   for (size_t i = 0; i < cand.size(); ++i)
     if (cand[i].tile_m == d.tile_m && cand[i].tile_n == d.tile_n && cand[i].cluster == d.cluster &&
-        cand[i].stages == d.stages && cand[i].split_k == d.split_k)
+        cand[i].stages == d.stages && cand[i].split_k == d.split_k && cand[i].tile_k == d.tile_k)
       cur = (int)i;
   if (cur < 0) cur = 0;
   float cur_ms = 0.f;
@@ -318,14 +418,14 @@ nk_status evolve(const nk_problem* p, const std::vector<nk_schedule>& cand, int 
   int timed = 1;
   const int limit = budget < (int)cand.size() ? budget : (int)cand.size();
   while (timed < limit) {
-    int lv[5];
+    int lv[6];
     const nk_schedule& s = cand[cur];
-    const int base[5] = {level_of(0, s.tile_m), level_of(1, s.tile_n), level_of(2, s.cluster),
-                         level_of(3, s.stages), level_of(4, s.split_k)};
+    const int base[6] = {level_of(0, s.tile_m), level_of(1, s.tile_n), level_of(2, s.cluster),
+                         level_of(3, s.stages), level_of(4, s.split_k), level_of(5, s.tile_k)};
     int child = -1;
     for (int tries = 0; tries < 64 && child < 0; ++tries) {
-      for (int c = 0; c < 5; ++c) lv[c] = base[c];
-      const int c = rng.below(5);
+      for (int c = 0; c < 6; ++c) lv[c] = base[c];
+      const int c = rng.below(6);
       if (rng.below(4) == 0) lv[c] = rng.below(NL[c]);
       else lv[c] = lv[c] + (rng.below(2) ? 1 : -1);
       if (lv[c] < 0 || lv[c] >= NL[c]) continue;

@@ -99,11 +99,55 @@ def test_bf16_resnet_stack_layers(nk, batch):
         assert O.rel_frobenius(got, R) <= 1e-5, (li, L)
 
 
-@pytest.mark.parametrize("case", CASES)
-def test_bf16_conv_transposed_orientation_bitwise(nk, case):
-    """Tiles of 128 filters x 256 output pixels (O^T = W^T im2col)."""
-    N, H, Wd, C, F, KH, KW, st, dl, pad = case
-    I = synth.small_ints(85, H * 100 + C, (N, H, Wd, C))
-    W = synth.small_ints(85, F * 100 + KH, (KH, KW, C, F))
-    got = _conv(nk, I, W, st, dl, pad, schedule=(256, 128, 64, 1, 4, 1))
-    np.testing.assert_array_equal(got, O.conv2d_nhwc_hwcf(I, W, st, dl, pad))
+WINDOW_CASES = [
+    # N, H, W, C, F, KH, KW, dilation, pad  (stride 1)
+    (1, 8, 8, 64, 64, 3, 3, (1, 1), (1, 1, 1, 1)),
+    (2, 13, 11, 16, 24, 3, 3, (1, 2), (1, 0, 2, 1)),
+    (1, 12, 12, 5, 7, 3, 3, (1, 1), (0, 0, 0, 0)),       # C not a multiple of 8
+    (2, 9, 9, 200, 72, 3, 3, (1, 1), (1, 1, 1, 1)),      # partial channel block, weights streamed
+    (1, 20, 18, 32, 300, 5, 3, (2, 1), (2, 2, 1, 1)),    # several N tiles, dilation
+    (5, 7, 7, 64, 64, 3, 3, (1, 1), (1, 1, 1, 1)),       # several images per window
+    (1, 6, 140, 64, 64, 3, 3, (1, 1), (1, 1, 1, 1)),     # rows wider than one window
+    (2, 15, 17, 96, 160, 3, 3, (1, 1), (1, 1, 1, 1)),
+]
+WINDOW_SCHEDULES = [(128, 64, 1, 2), (128, 128, 1, 1), (128, 256, 1, 3), (256, 64, 1, 2), (256, 128, 1, 2),
+                    (512, 64, 1, 2), (512, 64, 1, 1), (128, 64, 1, 4)]
+
+
+@pytest.mark.parametrize("case", WINDOW_CASES)
+@pytest.mark.parametrize("ws", WINDOW_SCHEDULES)
+def test_bf16_conv_window_bitwise(nk, case, ws):
+    """Stride-1 conv from one shared input window per tile: every tap reads
+    the window from a row offset (tile_k = 64 * taps selects this path)."""
+    N, H, Wd, C, F, KH, KW, dl, pad = case
+    tm, tn, cl, stages = ws
+    I = synth.small_ints(86, H * 100 + C, (N, H, Wd, C))
+    W = synth.small_ints(86, F * 100 + KH, (KH, KW, C, F))
+    sched = (tm, tn, 64 * KH * KW, cl, stages, 1)
+    got = _conv(nk, I, W, (1, 1), dl, pad, schedule=sched)
+    np.testing.assert_array_equal(got, O.conv2d_nhwc_hwcf(I, W, (1, 1), dl, pad))
+
+
+def test_bf16_conv_window_epilogue(nk):
+    """Bias, ReLU and accumulate through the window kernel, BF16 input."""
+    N, H, Wd, C, F = 3, 19, 23, 64, 96
+    I = synth.normal(87, 0, (N, H, Wd, C))
+    W = synth.normal(87, 1, (3, 3, C, F), sigma=0.06)
+    bias = synth.uniform(87, 2, (F,), lo=-0.1, hi=0.1)
+    C0 = synth.uniform(87, 3, (N, H, Wd, F))
+    out = dev(C0)
+    nk.nk_conv2d_nhwc_hwcf(dev(I).to(torch.bfloat16), dev(W), out, pad=(1, 1, 1, 1), precision="bf16",
+                           bias=dev(bias), relu=True, accumulate=True, schedule=(256, 128, 576, 1, 2, 1))
+    nk.nk_sync_status()
+    R = O.epilogue(O.conv2d_nhwc_hwcf(O.bf16_rn(I), O.bf16_rn(W), pad=(1, 1, 1, 1)), c_in=C0, beta=1.0,
+                   bias=bias, relu=True)
+    assert O.rel_frobenius(host(out), R) <= 1e-5
+
+
+def test_bf16_conv_window_rejects_strided(nk):
+    """The window path is stride 1 only; a strided problem with its tile_k is
+    refused before launch."""
+    I = synth.small_ints(88, 0, (1, 9, 9, 64))
+    W = synth.small_ints(88, 1, (3, 3, 64, 64))
+    with pytest.raises(nk.NkError):
+        _conv(nk, I, W, (2, 2), (1, 1), (1, 1, 1, 1), schedule=(128, 64, 576, 1, 2, 1))
