@@ -187,6 +187,24 @@ def time_fn(torch, fn, reps, warm=2):
     return e0.elapsed_time(e1) / reps
 
 
+def graph_time(torch, fn, calls=10, reps=10):
+    """Device time of one call: `calls` back-to-back calls captured into a
+    CUDA graph, replayed `reps` times between CUDA events (no host work
+    between the kernels, several calls per sample against the event clock's
+    ~2 us granularity)."""
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        fn()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            for _ in range(calls):
+                fn()
+    torch.cuda.current_stream().wait_stream(s)
+    return time_fn(torch, g.replay, reps) / calls
+
+
 def sweep_report(torch, nk, dev, a32, b32, c, flop, kern_tflops):
     """GEMM kernel throughput of the other precisions on the same operands."""
     out = {"bf16": kern_tflops}
@@ -315,12 +333,25 @@ def conv_report(torch, nk, synth, dev):
     t32 = time_fn(torch, lambda: nk.nk_conv2d_nhwc_hwcf(i32, w32, out, pad=(1, 1, 1, 1), bias=b32, relu=True), 20)
     i16 = i32.to(torch.bfloat16)
     ws = nk.workspace(nk.nk_conv2d_workspace_size(i16, w32, out, pad=(1, 1, 1, 1), precision="bf16"), dev)
-    t16 = time_fn(torch, lambda: nk.nk_conv2d_nhwc_hwcf(i16, w32, out, pad=(1, 1, 1, 1), precision="bf16",
-                                                        bias=b32, relu=True, ws=ws), 20)
+    f16 = lambda: nk.nk_conv2d_nhwc_hwcf(i16, w32, out, pad=(1, 1, 1, 1), precision="bf16",  # noqa: E731
+                                         bias=b32, relu=True, ws=ws)
+    t16 = time_fn(torch, f16, 20)
+    g32 = graph_time(torch, lambda: nk.nk_conv2d_nhwc_hwcf(i32, w32, out, pad=(1, 1, 1, 1), bias=b32, relu=True))
+    g16 = graph_time(torch, f16)
+    wp = nk.nk_conv2d_pack_weights(w32)
+    ws_p = nk.workspace(nk.nk_conv2d_workspace_size(i16, wp, out, pad=(1, 1, 1, 1), precision="bf16"), dev)
+    gp = graph_time(torch, lambda: nk.nk_conv2d_nhwc_hwcf(i16, wp, out, pad=(1, 1, 1, 1), precision="bf16",
+                                                          bias=b32, relu=True, ws=ws_p))
     nk.nk_sync_status()
     return {"f32_ms": t32, "f32_tflops": flop / (t32 * 1e-3) / 1e12, "bf16_ms": t16,
             "bf16_tflops": flop / (t16 * 1e-3) / 1e12, "bf16_over_f32": t32 / t16,
-            "note": "bf16 time includes the per-call FP32 -> BF16 weight cast"}
+            "graph_f32_ms": g32, "graph_bf16_ms": g16, "graph_bf16_tflops": flop / (g16 * 1e-3) / 1e12,
+            "graph_bf16_over_f32": g32 / g16,
+            "graph_bf16_packed_ms": gp, "graph_bf16_packed_tflops": flop / (gp * 1e-3) / 1e12,
+            "graph_bf16_packed_over_f32": g32 / gp,
+            "note": "per call: host overhead included; graph: device time of calls replayed from a CUDA graph; "
+                    "bf16 includes the per-call FP32 -> BF16 weight cast, bf16_packed takes weights packed once "
+                    "by nk_conv2d_pack_weights"}
 
 
 def resnet_report(torch, synth, dev):
@@ -338,10 +369,12 @@ def resnet_report(torch, synth, dev):
     for b in (1, 8, 32):
         tot = {"default_ms": 0.0, "model_top5_ms": 0.0, "evolution5_ms": 0.0, "exhaustive_ms": 0.0, "flop": 0.0}
         timed = {"model": 0, "evolution": 0, "exhaustive": 0}
+        picks = []
         for L in synth.resnet_stack(b):
             p = nt.conv_problem(L["N"], L["H"], L["W"], L["C"], L["F"], L["KH"], L["KW"], L["stride"], L["pad"])
             _, ex = nt.nk_tune(p, nt.NK_TUNE_EXHAUSTIVE, reps=3)
-            _, mo = nt.nk_tune(p, nt.NK_TUNE_MODEL_TOPK, topk=5, params=P, reps=3)
+            pick, mo = nt.nk_tune(p, nt.NK_TUNE_MODEL_TOPK, topk=5, params=P, reps=3)
+            picks.append(pick)
             _, es = nt.nk_tune(p, nt.NK_TUNE_EVOLUTION, topk=5, reps=3)
             tot["default_ms"] += ex.default_ms
             tot["exhaustive_ms"] += ex.best_ms
@@ -357,9 +390,38 @@ def resnet_report(torch, synth, dev):
         tot["evolution_regret"] = tot["evolution5_ms"] / tot["exhaustive_ms"] - 1
         tot["model_tflops"] = tot["flop"] / (tot["model_top5_ms"] * 1e-3) / 1e12
         tot["schedules_timed"] = timed
+        tot["stack_graph"] = stack_graph(torch, synth, dev, b, picks, tot["flop"])
         out[f"batch{b}"] = tot
     nt.nk_tune_release()
     return out
+
+
+def stack_graph(torch, synth, dev, batch, picks, flop):
+    """The whole 20-layer stack through the public API, as a user deploys it:
+    weights packed to BF16 once (nk_conv2d_pack_weights), then each layer an
+    nk_conv2d_nhwc_hwcf call (BF16 input, bias + ReLU, the cost model's pick
+    as schedule), all 20 captured into one CUDA graph and replayed."""
+    import paper_2307_16080_gb300.nk as nk
+    calls = []
+    for li, (L, sched) in enumerate(zip(synth.resnet_stack(batch), picks)):
+        oh = (L["H"] + 2 * L["pad"] - L["KH"]) // L["stride"] + 1
+        i = torch.empty(L["N"], L["H"], L["W"], L["C"], device=dev).uniform_(0, 1).to(torch.bfloat16)
+        w = nk.nk_conv2d_pack_weights(torch.empty(L["KH"], L["KW"], L["C"], L["F"], device=dev).normal_(
+            0, (2.0 / (L["KH"] * L["KW"] * L["C"])) ** 0.5))
+        bias = torch.empty(L["F"], device=dev).uniform_(-0.1, 0.1)
+        o = torch.empty(L["N"], oh, oh, L["F"], device=dev)
+        st, pad = (L["stride"],) * 2, (L["pad"],) * 4
+        ws = nk.workspace(nk.nk_conv2d_workspace_size(i, w, o, st, (1, 1), pad, "bf16", sched), dev)
+        calls.append((i, w, o, st, pad, bias, sched, ws))
+
+    def forward():
+        for (i, w, o, st, pad, bias, sched, ws) in calls:
+            nk.nk_conv2d_nhwc_hwcf(i, w, o, st, (1, 1), pad, "bf16", bias=bias, relu=True, schedule=sched, ws=ws)
+    ms = graph_time(torch, forward, calls=2, reps=10)
+    nk.nk_sync_status()
+    kernels = sum(2 if sched[5] > 1 else 1 for sched in picks)   # split-K adds its reduce
+    return {"ms": ms, "tflops": flop / (ms * 1e-3) / 1e12, "kernels_per_forward": kernels,
+            "how": "20 nk_conv2d calls on packed BF16 weights (one conv kernel each) in one CUDA graph, device time"}
 
 
 def main():

@@ -101,7 +101,8 @@ typedef struct {
  * CTAs along M that share B tiles through TMA multicast), tile_k reduction
  * depth per pipeline stage, stages = shared-memory ring depth, split_k =
  * number of K slices reduced by a separate fixed-order pass.  Any field 0
- * means "choose".                                                          */
+ * means "choose".  For the shared-window convolution (tile_k = 64*KH*KW,
+ * see nk_conv2d_nhwc_hwcf) stages counts window slots and split_k is 1.    */
 typedef struct {
   int32_t tile_m, tile_n, tile_k, cluster, stages, split_k;
 } nk_schedule;
@@ -169,11 +170,19 @@ nk_status nk_grouped_workspace_size(int32_t G, const nk_gemm_group* groups,
 /* ------------------------------------------------------------------ conv */
 
 /* linalg.conv_2d_nhwc_hwcf with zero padding and the epilogue.
- * I: [N,H,W,C], W: [KH,KW,C,F], O: [N,OH,OW,F] FP32, all with unit stride in
- * the last dimension.  OH = (H + pt + pb - dh*(KH-1) - 1)/sh + 1 (same for OW).
- * stride = {sh, sw}, dilation = {dh, dw}, pad = {top, bottom, left, right}.
- * I and W dtype: F32 (any precision; BF16 converts into the workspace) or
- * BF16 with NK_PREC_BF16.                                                   */
+ * I: [N,H,W,C], W: [KH,KW,C,F], O: [N,OH,OW,F] FP32; I and O with unit
+ * stride in the last dimension.  OH = (H + pt + pb - dh*(KH-1) - 1)/sh + 1
+ * (same for OW).  stride = {sh, sw}, dilation = {dh, dw},
+ * pad = {top, bottom, left, right}.
+ * I dtype: F32 (any precision; BF16 converts it into the workspace) or BF16
+ * with NK_PREC_BF16.  W dtype: F32 contiguous HWCF (converted per call into
+ * the workspace at NK_PREC_BF16), or -- NK_PREC_BF16 only -- BF16 already
+ * packed by nk_conv2d_pack_weights, described as [KH,KW,C,F] with strides
+ * {KW*ldw, ldw, 1, sF} (ldw >= C, sF >= KH*KW*ldw, multiples of 8; 16-byte
+ * aligned base): no per-call conversion.
+ * At NK_PREC_BF16 a stride-1 schedule with tile_k = 64*KH*KW selects the
+ * shared-window kernel (each tile's input window is loaded once and read by
+ * every tap); tile_k = 64 selects the per-tap implicit GEMM.              */
 nk_status nk_conv2d_nhwc_hwcf(const nk_tensor* I, const nk_tensor* W,
                               nk_tensor* O, const int64_t stride[2],
                               const int64_t dilation[2], const int64_t pad[4],
@@ -185,6 +194,16 @@ nk_status nk_conv2d_workspace_size(const nk_tensor* I, const nk_tensor* W,
                                    const int64_t dilation[2],
                                    const int64_t pad[4], int32_t precision,
                                    const nk_schedule* sched, size_t* bytes);
+
+/* Converts FP32 HWCF weights W [KH,KW,C,F] (contiguous) to the BF16 layout
+ * the tensor-core convolution reads: element (kh,kw,c,f) at
+ * Wp + f*(KH*KW*ldw) + (kh*KW + kw)*ldw + c, with ldw >= C a multiple of 8
+ * (channels c >= C of a row are never read).  Wp: device memory of
+ * F*KH*KW*ldw*2 bytes, 16-byte aligned, owned by the caller.  Asynchronous
+ * on `stream`; pass the result to nk_conv2d_nhwc_hwcf as a BF16 W with
+ * strides {KW*ldw, ldw, 1, KH*KW*ldw} so repeated calls skip the cast.   */
+nk_status nk_conv2d_pack_weights(const nk_tensor* W, void* Wp, int64_t ldw,
+                                 void* stream);
 
 /* The convolution exactly as Sec. 4.1 Listing "2dnchwconv" lays it out:
  * I: [N,CI,H,W] (NCHW), K: [CO,CI,KH,KW] (FCHW, contiguous), O: [N,CO,OH,OW],

@@ -923,7 +923,7 @@ nk_status make_conv_maps(TcParams& p, const TcConv& c, const ConvTile& t, int bn
   {
     const int taps = g.kh * g.kw;
     cuuint64_t dims[3] = {(cuuint64_t)g.c, (cuuint64_t)taps, (cuuint64_t)c.F};
-    cuuint64_t strides[2] = {(cuuint64_t)c.ldw * 2, (cuuint64_t)c.ldw * taps * 2};
+    cuuint64_t strides[2] = {(cuuint64_t)c.ldw * 2, (cuuint64_t)c.sW_f * 2};
     cuuint32_t box[3] = {64, 1, (cuuint32_t)bn_box};
     cuuint32_t es[3] = {1, 1, 1};
     CUresult r = fn(&p.tmB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(c.Wt), dims, strides, box,
@@ -989,7 +989,7 @@ nk_status tc_conv(const TcConv& c, const nk_schedule& s, void* ws, size_t ws_byt
   const int M = g.n * g.oh * g.ow;
   if (g.sw > 8 || g.sh > 8) return fail(NK_ERR_UNSUPPORTED, "conv stride above 8");
   if (!tc_conv_schedule_valid(g, c.F, s)) return fail(NK_ERR_NO_SCHEDULE, "illegal tensor-core schedule for conv");
-  if ((c.sI_w * 2) % 16 || (c.sI_h * 2) % 16 || (c.sI_n * 2) % 16 || (c.ldw * 2) % 16 ||
+  if ((c.sI_w * 2) % 16 || (c.sI_h * 2) % 16 || (c.sI_n * 2) % 16 || (c.ldw * 2) % 16 || (c.sW_f * 2) % 16 ||
       (reinterpret_cast<uintptr_t>(c.I) & 15) || (reinterpret_cast<uintptr_t>(c.Wt) & 15))
     return fail(NK_ERR_MISALIGNED, "conv operands need 16-byte aligned bases and strides");
   const ConvTile t = choose_conv_tile(g);

@@ -432,8 +432,8 @@ struct HaloLayout {
 // CTAs of this layout that fit on one SM: shared memory (each CTA also
 // costs 1 KB of reserved space) and two accumulator buffers of MCH * BN
 // TMEM columns each.
-int halo_ctas(int smem, int mch, int bn) {
-  const bool tmem2 = 4 * mch * bn <= 512;
+int halo_ctas(int smem, int chains, int bn) {
+  const bool tmem2 = 4 * chains * bn <= 512;
   return (tmem2 && 2 * (smem + 1024) <= kMaxSmem + 1024) ? 2 : 1;
 }
 
@@ -444,6 +444,7 @@ int halo_ctas(int smem, int mch, int bn) {
 // SM wins; on a tie, resident weights.
 bool halo_layout(const ConvGeom& g, int F, const nk_schedule& s, HaloLayout* L) {
   const int mch = chains_of(s);
+  const int chains = mch;
   if (!cached_halo_tile(g, mch, &L->t)) return false;
   L->slot_bytes = (uint32_t)((L->t.slot_rows * kRow + 1023) / 1024 * 1024);
   L->wslots = s.stages;
@@ -454,13 +455,13 @@ bool halo_layout(const ConvGeom& g, int F, const nk_schedule& s, HaloLayout* L) 
   if (room < 2) return false;
   // streamed ring: deepest ring that keeps the CTA count of a 2-slot ring
   int ring = std::min(std::min(room, nkb < 2 ? 2 : nkb), 8);
-  const int want = halo_ctas(fixed + 2 * b_tile, mch, s.tile_n);
-  while (ring > 2 && halo_ctas(fixed + ring * b_tile, mch, s.tile_n) < want) --ring;
+  const int want = halo_ctas(fixed + 2 * b_tile, chains, s.tile_n);
+  while (ring > 2 && halo_ctas(fixed + ring * b_tile, chains, s.tile_n) < want) --ring;
   L->resident = 0;
   L->bslots = ring;
   const bool one_n = (F + s.tile_n - 1) / s.tile_n == 1;
   if (one_n && room >= nkb && 8 * (2 * s.stages + 2 * nkb + 5) + 8 <= kBarBytes &&
-      halo_ctas(fixed + nkb * b_tile, mch, s.tile_n) >= halo_ctas(fixed + ring * b_tile, mch, s.tile_n)) {
+      halo_ctas(fixed + nkb * b_tile, chains, s.tile_n) >= halo_ctas(fixed + ring * b_tile, chains, s.tile_n)) {
     L->resident = 1;
     L->bslots = nkb;
   }
@@ -530,7 +531,7 @@ nk_status tc_halo_conv(const TcConv& c, const nk_schedule& s, cudaStream_t st) {
   HaloLayout L;
   if (!halo_schedule_valid(g, c.F, s) || !halo_layout(g, c.F, s, &L))
     return fail(NK_ERR_NO_SCHEDULE, "illegal window-conv schedule");
-  if ((c.sI_w * 2) % 16 || (c.sI_h * 2) % 16 || (c.sI_n * 2) % 16 || (c.ldw * 2) % 16 ||
+  if ((c.sI_w * 2) % 16 || (c.sI_h * 2) % 16 || (c.sI_n * 2) % 16 || (c.ldw * 2) % 16 || (c.sW_f * 2) % 16 ||
       (reinterpret_cast<uintptr_t>(c.I) & 15) || (reinterpret_cast<uintptr_t>(c.Wt) & 15))
     return fail(NK_ERR_MISALIGNED, "conv operands need 16-byte aligned rows");
   auto fn = encode_fn();
@@ -551,7 +552,7 @@ nk_status tc_halo_conv(const TcConv& c, const nk_schedule& s, cudaStream_t st) {
   {
     const int taps = taps_of(g);
     cuuint64_t dims[3] = {(cuuint64_t)g.c, (cuuint64_t)taps, (cuuint64_t)c.F};
-    cuuint64_t strides[2] = {(cuuint64_t)c.ldw * 2, (cuuint64_t)taps * c.ldw * 2};
+    cuuint64_t strides[2] = {(cuuint64_t)c.ldw * 2, (cuuint64_t)c.sW_f * 2};
     cuuint32_t box[3] = {64, 1, (cuuint32_t)s.tile_n};
     cuuint32_t es[3] = {1, 1, 1};
     CUresult r = fn(&p.tmW, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(c.Wt), dims, strides, box, es,

@@ -380,17 +380,26 @@ nk_status nk_matmul(const nk_tensor* A, const nk_tensor* B, nk_tensor* C, int32_
 }
 
 // ------------------------------------------------------------------ conv
+// BF16 weights in the tensor-core layout: W[kh,kw,c,f] at
+// f*sF + (kh*KW + kw)*ldw + c, ldw >= C, sF >= KH*KW*ldw, both multiples of 8
+// elements (16-byte rows for TMA).
+static bool packed_weights(const nk_tensor* W) {
+  const int64_t ldw = W->stride[1], sF = W->stride[3];
+  return W->stride[2] == 1 && ldw >= W->shape[2] && ldw % 8 == 0 && W->stride[0] == W->shape[1] * ldw &&
+         sF % 8 == 0 && sF >= W->shape[0] * W->shape[1] * ldw;
+}
+
 static nk_status plan_conv(const nk_tensor* I, const nk_tensor* W, const nk_tensor* O,
                            const int64_t stride[2], const int64_t dilation[2], const int64_t pad[4],
                            ConvGeom& g) {
   if (!I || !W || !O) return fail(NK_ERR_INVALID_ARG, "I, W and O must be non-NULL");
   if (!stride || !dilation || !pad) return fail(NK_ERR_INVALID_ARG, "stride, dilation, pad must be non-NULL");
   if (I->rank != 4 || W->rank != 4 || O->rank != 4) return fail(NK_ERR_INVALID_ARG, "I, W, O must have rank 4");
-  if (I->stride[3] != 1 || W->stride[3] != 1 || O->stride[3] != 1)
-    return fail(NK_ERR_UNSUPPORTED, "the last dimension of I, W and O must have unit stride");
+  if (I->stride[3] != 1 || O->stride[3] != 1)
+    return fail(NK_ERR_UNSUPPORTED, "the last dimension of I and O must have unit stride");
   if (O->dtype != NK_F32) return fail(NK_ERR_UNSUPPORTED, "O must be FP32");
-  if (I->dtype != W->dtype && !(I->dtype == NK_BF16 && W->dtype == NK_F32))
-    return fail(NK_ERR_INVALID_ARG, "I and W must share a dtype (or BF16 I with FP32 W)");
+  if ((I->dtype != NK_F32 && I->dtype != NK_BF16) || (W->dtype != NK_F32 && W->dtype != NK_BF16))
+    return fail(NK_ERR_INVALID_ARG, "I and W must be FP32 or BF16");
   for (int i = 0; i < 2; ++i)
     if (stride[i] < 1 || dilation[i] < 1) return fail(NK_ERR_INVALID_ARG, "stride and dilation must be >= 1");
   for (int i = 0; i < 4; ++i)
@@ -408,9 +417,17 @@ static nk_status plan_conv(const nk_tensor* I, const nk_tensor* W, const nk_tens
                 (long long)oh, (long long)ow, (long long)W->shape[3]);
   g.oh = (int)oh; g.ow = (int)ow;
   g.sin_n = I->stride[0]; g.sin_h = I->stride[1]; g.sin_w = I->stride[2];
-  if (W->stride[2] != W->shape[3] || W->stride[1] != W->shape[2] * W->shape[3] ||
-      W->stride[0] != W->shape[1] * W->shape[2] * W->shape[3])
-    return fail(NK_ERR_UNSUPPORTED, "W must be contiguous HWCF");
+  if (W->dtype == NK_BF16) {
+    // packed for the tensor cores (nk_conv2d_pack_weights): channels
+    // contiguous per filter tap, taps at a uniform stride
+    if (!packed_weights(W))
+      return fail(NK_ERR_UNSUPPORTED,
+                  "a BF16 W must be packed: strides {KW*ldw, ldw, 1, sF} with ldw >= C and sF >= KH*KW*ldw, "
+                  "both multiples of 8 (see nk_conv2d_pack_weights)");
+  } else if (W->stride[3] != 1 || W->stride[2] != W->shape[3] || W->stride[1] != W->shape[2] * W->shape[3] ||
+             W->stride[0] != W->shape[1] * W->shape[2] * W->shape[3]) {
+    return fail(NK_ERR_UNSUPPORTED, "an FP32 W must be contiguous HWCF");
+  }
   if ((int64_t)g.n * g.oh * g.ow > INT32_MAX) return fail(NK_ERR_UNSUPPORTED, "output too large");
   return NK_OK;
 }
@@ -421,14 +438,14 @@ static nk_status plan_conv(const nk_tensor* I, const nk_tensor* W, const nk_tens
 struct ConvPlan {
   nk_schedule sched{};
   int Cp = 0;
-  bool cast_i = false;
+  bool cast_i = false, cast_w = false;
   size_t off_i = 0, off_w = 0, off_k = 0, kern = 0, total = 0;
 };
 
 static nk_status plan_tc_conv(const nk_tensor* I, const nk_tensor* W, const nk_tensor* O, const ConvGeom& g,
                               const nk_schedule* user, ConvPlan& P) {
-  if (W->dtype != NK_F32) return fail(NK_ERR_UNSUPPORTED, "tensor-core conv takes FP32 HWCF weights");
-  if (I->dtype != NK_F32 && I->dtype != NK_BF16) return fail(NK_ERR_UNSUPPORTED, "conv input must be FP32 or BF16");
+  if (W->dtype == NK_BF16 && (reinterpret_cast<uintptr_t>(W->ptr) & 15))
+    return fail(NK_ERR_MISALIGNED, "packed BF16 weights must be 16-byte aligned");
   int sms = 152, dev = 0, v = 0;
   if (cudaGetDevice(&dev) == cudaSuccess &&
       cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
@@ -452,12 +469,26 @@ static nk_status plan_tc_conv(const nk_tensor* I, const nk_tensor* W, const nk_t
     return fail(NK_ERR_UNSUPPORTED, "an FP32 conv input must be contiguous NHWC for the BF16 path");
   size_t off = 0;
   if (P.cast_i) { P.off_i = off; off += align_up((size_t)g.n * g.h * g.w * P.Cp * 2); }
-  P.off_w = off; off += align_up((size_t)F * g.kh * g.kw * P.Cp * 2);
+  P.cast_w = W->dtype == NK_F32;
+  if (P.cast_w) { P.off_w = off; off += align_up((size_t)F * g.kh * g.kw * P.Cp * 2); }
   TcConv c{};
   c.g = g; c.F = F;
   P.kern = tc_conv_ws(c, S);
   P.off_k = off; off += align_up(P.kern);
   P.total = off;
+  return NK_OK;
+}
+
+// FP32 HWCF weights [taps*C, F] -> BF16 [F][taps][ldw] (ldw >= C, a
+// multiple of 8): one transposing cast when ldw == C, else one per tap.
+static nk_status pack_weights(const float* Wf, int taps, int C, int F, int64_t ldw, void* out, cudaStream_t st) {
+  char* wt = static_cast<char*>(out);
+  if (ldw == C) return prep_cast(0, Wf, (int64_t)taps * C, F, F, nullptr, wt, nullptr, (int64_t)taps * C, 1, nullptr, st);
+  for (int tap = 0; tap < taps; ++tap) {
+    nk_status s = prep_cast(0, Wf + (int64_t)tap * C * F, C, F, F, nullptr, wt + (size_t)tap * ldw * 2, nullptr,
+                            (int64_t)taps * ldw, 1, nullptr, st);
+    if (s != NK_OK) return s;
+  }
   return NK_OK;
 }
 
@@ -519,28 +550,27 @@ nk_status nk_conv2d_nhwc_hwcf(const nk_tensor* I, const nk_tensor* W, nk_tensor*
       c.I = I->ptr;
       c.sI_w = g.sin_w; c.sI_h = g.sin_h; c.sI_n = g.sin_n;
     }
-    const float* Wf = static_cast<const float*>(W->ptr);
-    char* wt = w + P.off_w;
-    if (P.Cp == g.c) {   // [taps*C, F] -> [F, taps*C] in one transposing cast
-      s = prep_cast(0, Wf, (int64_t)taps * g.c, F, F, nullptr, wt, nullptr, (int64_t)taps * g.c, 1, nullptr, st);
-      if (s != NK_OK) return s;
-    } else {             // one tap at a time into rows padded to Cp channels
-      for (int tap = 0; tap < taps; ++tap) {
-        s = prep_cast(0, Wf + (int64_t)tap * g.c * F, g.c, F, F, nullptr, wt + (size_t)tap * P.Cp * 2, nullptr,
-                      (int64_t)taps * P.Cp, 1, nullptr, st);
-        if (s != NK_OK) return s;
-      }
+    if (P.cast_w) {
+      char* wt = w + P.off_w;
+      if ((s = pack_weights(static_cast<const float*>(W->ptr), g.kh * g.kw, g.c, F, P.Cp, wt, st)) != NK_OK)
+        return s;
+      c.Wt = wt;
+      c.ldw = P.Cp;
+      c.sW_f = (int64_t)taps * P.Cp;
+    } else {
+      c.Wt = W->ptr;
+      c.ldw = W->stride[1];
+      c.sW_f = W->stride[3];
     }
-    c.Wt = wt;
-    c.ldw = P.Cp;
     c.O = static_cast<float*>(O->ptr);
     c.bias = E.bias;
     c.relu = E.relu;
     c.beta = E.accumulate ? 1.f : 0.f;
     return tc_conv(c, P.sched, w + P.off_k, P.kern, st);
   }
-  if (precision != NK_PREC_F32 || I->dtype != NK_F32)
-    return fail(NK_ERR_UNSUPPORTED, "conv precision %d / dtype %d not available", precision, I->dtype);
+  if (precision != NK_PREC_F32 || I->dtype != NK_F32 || W->dtype != NK_F32)
+    return fail(NK_ERR_UNSUPPORTED, "conv precision %d with I dtype %d / W dtype %d not available", precision,
+                I->dtype, W->dtype);
   SimtGemm p{};
   p.A = static_cast<const float*>(I->ptr);
   p.B = static_cast<const float*>(W->ptr);
@@ -553,6 +583,22 @@ nk_status nk_conv2d_nhwc_hwcf(const nk_tensor* I, const nk_tensor* W, nk_tensor*
   int tile = sched && sched->tile_m > 0 ? sched->tile_m : 64;
   int split = sched && sched->split_k > 0 ? sched->split_k : 1;
   return simt_gemm(p, tile, split, ws, ws_bytes, static_cast<cudaStream_t>(stream));
+}
+
+nk_status nk_conv2d_pack_weights(const nk_tensor* W, void* Wp, int64_t ldw, void* stream) {
+  if (!W || !Wp) return fail(NK_ERR_INVALID_ARG, "W and Wp must be non-NULL");
+  if (W->rank != 4 || W->dtype != NK_F32) return fail(NK_ERR_INVALID_ARG, "W must be a rank-4 FP32 tensor");
+  if (W->stride[3] != 1 || W->stride[2] != W->shape[3] || W->stride[1] != W->shape[2] * W->shape[3] ||
+      W->stride[0] != W->shape[1] * W->shape[2] * W->shape[3])
+    return fail(NK_ERR_UNSUPPORTED, "W must be contiguous HWCF");
+  for (int i = 0; i < 4; ++i)
+    if (W->shape[i] < 1) return fail(NK_ERR_INVALID_ARG, "W extents must be positive");
+  if (ldw < W->shape[2] || ldw % 8) return fail(NK_ERR_INVALID_ARG, "ldw must be >= C and a multiple of 8");
+  if (!aligned16(Wp)) return fail(NK_ERR_MISALIGNED, "Wp must be 16-byte aligned");
+  nk_status s = require_device();
+  if (s != NK_OK) return s;
+  return pack_weights(static_cast<const float*>(W->ptr), (int)(W->shape[0] * W->shape[1]), (int)W->shape[2],
+                      (int)W->shape[3], ldw, Wp, static_cast<cudaStream_t>(stream));
 }
 
 // ------------------------------------------------------------- operand prep

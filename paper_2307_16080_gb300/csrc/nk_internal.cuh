@@ -132,13 +132,15 @@ nk_status tc_gemm(const TcGemm& g, const nk_schedule& s, void* ws, size_t ws_byt
 
 // Implicit-GEMM convolution on the tensor cores (BF16 operands).
 // I: NHWC BF16 with channel stride 1 and element strides sI_n, sI_h, sI_w
-// (16-byte multiples); Wt: BF16 [F][KH*KW][ldw] (K-major per filter tap);
+// (16-byte multiples); Wt: BF16, filter f / tap t / channel c at
+// f*sW_f + t*ldw + c (K-major per filter tap; ldw, sW_f multiples of 8);
 // O: FP32 [N*OH*OW, F] row-major.
 struct TcConv {
   const void* I;
   int64_t sI_n, sI_h, sI_w;
   const void* Wt;
   int64_t ldw;
+  int64_t sW_f;
   ConvGeom g;
   int F;
   float* O;

@@ -203,7 +203,7 @@ struct Runner {
       const size_t wb = (size_t)p->f * p->kh * p->kw * cp * 2;
       op_bytes = ib + wb;
       total = op_bytes + (size_t)M * N * 4 + split_bytes + 4096;
-      c.g = geo; c.F = p->f; c.ldw = cp;
+      c.g = geo; c.F = p->f; c.ldw = cp; c.sW_f = (int64_t)p->kh * p->kw * cp;
       c.sI_w = geo.sin_w; c.sI_h = geo.sin_h; c.sI_n = geo.sin_n;
     }
   }

@@ -73,6 +73,7 @@ SIGNATURES = {
                                    ctypes.POINTER(_I64), _I32, _PE, _PS, _P, _SZ, _P]),
     "nk_conv2d_workspace_size": (_I32, [_PT, _PT, _PT, ctypes.POINTER(_I64), ctypes.POINTER(_I64),
                                         ctypes.POINTER(_I64), _I32, _PS, ctypes.POINTER(_SZ)]),
+    "nk_conv2d_pack_weights": (_I32, [_PT, _P, _I64, _P]),
     "nk_conv2d_nchw_fchw": (_I32, [_PT, _PT, _PT, ctypes.POINTER(_I64), ctypes.POINTER(_I64),
                                    ctypes.POINTER(_I64), _PE, _P]),
     "nk_amax": (_I32, [_P, _I64, _P, _P, _SZ, _P]),
@@ -214,6 +215,18 @@ def nk_conv2d_nhwc_hwcf(I, W, O, stride=(1, 1), dilation=(1, 1), pad=(0, 0, 0, 0
                                      ws.data_ptr() if ws is not None else None,
                                      ws.numel() if ws is not None else 0, _stream(stream)))
     return O
+
+
+def nk_conv2d_pack_weights(W, ldw=None, stream=None) -> torch.Tensor:
+    """FP32 HWCF W [KH,KW,C,F] -> the BF16 packed layout, returned as a
+    [KH,KW,C,F] strided view (strides {KW*ldw, ldw, 1, KH*KW*ldw}) that
+    nk_conv2d_nhwc_hwcf takes as W without a per-call cast."""
+    KH, KW, C, F = W.shape
+    ldw = (C + 7) // 8 * 8 if ldw is None else int(ldw)
+    buf = torch.empty(F * KH * KW * ldw, dtype=torch.bfloat16, device=W.device)
+    tw = as_nk_tensor(W)
+    _check(lib().nk_conv2d_pack_weights(ctypes.byref(tw), buf.data_ptr(), ldw, _stream(stream)))
+    return buf.as_strided((KH, KW, C, F), (KW * ldw, ldw, 1, KH * KW * ldw))
 
 
 def nk_conv2d_nchw_fchw(I, K, O, stride=(1, 1), dilation=(1, 1), pad=(0, 0, 0, 0), bias=None, relu=False,

@@ -9,10 +9,13 @@ CASE:
   amax      max |x| over 8192 x 8192 FP32
   direct    NCHW conv, Ci = 1, Co = 3, 3 x 3 on 1280 x 1280 images, batch 1
             (the tuning experiment's shape) and batch 16 (larger than L2)
-  conv      BF16 implicit-GEMM conv, batch 32 x 56 x 56 x 64, 3 x 3 x 64 x 64
+  conv      BF16 conv, batch 32 x 56 x 56 x 64, 3 x 3 x 64 x 64, built-in schedule (the
+            shared-window kernel)
+  conv_tap  the same layer on the per-tap implicit-GEMM kernel, schedule (128, 64, 64, 1, 3, 1)
   grouped   512 uneven BF16 GEMMs, one persistent launch
   splitk    FP32 1024 x 1024 x 16384 with split-K 8 (partials + fixed-order reduce)
-Prints one JSON line per measurement.
+Prints one JSON line per measurement.  Times are device times: `calls`
+back-to-back calls captured into a CUDA graph, replayed between CUDA events.
 """
 from __future__ import annotations
 
@@ -35,18 +38,28 @@ def _peaks():
         return 6800.0, 1900.0
 
 
-def _time(fn, reps):
-    for _ in range(3):
-        fn()
+def _time(fn, reps, calls=4):
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            for _ in range(calls):
+                fn()
+    torch.cuda.current_stream().wait_stream(s)
+    g.replay()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(reps):
-        fn()
+        g.replay()
     e1.record()
     torch.cuda.synchronize()
     nk.nk_sync_status()
-    return e0.elapsed_time(e1) / reps
+    return e0.elapsed_time(e1) / (reps * calls)
 
 
 def _emit(case, ms, bytes_=None, flop=None):
@@ -88,15 +101,24 @@ def case_direct(reps):
               _time(lambda: nk.nk_conv2d_nchw_fchw(i, k, o), reps), bytes_=b, flop=f)
 
 
-def case_conv(reps):
+def _conv_layer(reps, sched, name):
     N, H, C, F = 32, 56, 64, 64
     i = torch.randn(N, H, H, C, device="cuda").abs().to(torch.bfloat16)
     w = torch.randn(3, 3, C, F, device="cuda") * 0.06
     o = torch.empty(N, H, H, F, device="cuda")
-    ws = nk.workspace(nk.nk_conv2d_workspace_size(i, w, o, pad=(1, 1, 1, 1), precision="bf16"))
+    ws = nk.workspace(nk.nk_conv2d_workspace_size(i, w, o, pad=(1, 1, 1, 1), precision="bf16", schedule=sched))
     f = 2.0 * N * H * H * F * 9 * C
-    _emit("bf16 conv 32x56x56x64 3x3", _time(
-        lambda: nk.nk_conv2d_nhwc_hwcf(i, w, o, pad=(1, 1, 1, 1), precision="bf16", ws=ws), reps), flop=f)
+    b = N * H * H * (C * 2 + F * 4) + 9 * C * F * 4   # BF16 input, FP32 output, FP32 weights
+    _emit(name, _time(lambda: nk.nk_conv2d_nhwc_hwcf(i, w, o, pad=(1, 1, 1, 1), precision="bf16", schedule=sched,
+                                                     ws=ws), reps), bytes_=b, flop=f)
+
+
+def case_conv(reps):
+    _conv_layer(reps, None, "bf16 conv 32x56x56x64 3x3 (built-in schedule)")
+
+
+def case_conv_tap(reps):
+    _conv_layer(reps, (128, 64, 64, 1, 3, 1), "bf16 conv 32x56x56x64 3x3 (per-tap kernel)")
 
 
 def case_grouped(reps):
@@ -122,7 +144,7 @@ def case_splitk(reps):
         lambda: nk.nk_matmul(a, b, c, precision="f32", schedule=sched, ws=ws), reps), flop=2.0 * M * N * K)
 
 
-CASES = {"cast": case_cast, "amax": case_amax, "direct": case_direct, "conv": case_conv,
+CASES = {"cast": case_cast, "amax": case_amax, "direct": case_direct, "conv": case_conv, "conv_tap": case_conv_tap,
          "grouped": case_grouped, "splitk": case_splitk}
 
 

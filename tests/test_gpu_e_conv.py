@@ -110,8 +110,9 @@ WINDOW_CASES = [
     (1, 6, 140, 64, 64, 3, 3, (1, 1), (1, 1, 1, 1)),     # rows wider than one window
     (2, 15, 17, 96, 160, 3, 3, (1, 1), (1, 1, 1, 1)),
 ]
-WINDOW_SCHEDULES = [(128, 64, 1, 2), (128, 128, 1, 1), (128, 256, 1, 3), (256, 64, 1, 2), (256, 128, 1, 2),
-                    (512, 64, 1, 2), (512, 64, 1, 1), (128, 64, 1, 4)]
+WINDOW_SCHEDULES = [  # tile_m, tile_n, stages
+    (128, 64, 2), (128, 128, 1), (128, 256, 3), (256, 64, 2), (256, 128, 2), (512, 64, 2), (512, 64, 1),
+    (128, 64, 4), (128, 64, 1), (256, 64, 1)]
 
 
 @pytest.mark.parametrize("case", WINDOW_CASES)
@@ -120,10 +121,10 @@ def test_bf16_conv_window_bitwise(nk, case, ws):
     """Stride-1 conv from one shared input window per tile: every tap reads
     the window from a row offset (tile_k = 64 * taps selects this path)."""
     N, H, Wd, C, F, KH, KW, dl, pad = case
-    tm, tn, cl, stages = ws
+    tm, tn, stages = ws
     I = synth.small_ints(86, H * 100 + C, (N, H, Wd, C))
     W = synth.small_ints(86, F * 100 + KH, (KH, KW, C, F))
-    sched = (tm, tn, 64 * KH * KW, cl, stages, 1)
+    sched = (tm, tn, 64 * KH * KW, 1, stages, 1)
     got = _conv(nk, I, W, (1, 1), dl, pad, schedule=sched)
     np.testing.assert_array_equal(got, O.conv2d_nhwc_hwcf(I, W, (1, 1), dl, pad))
 
@@ -151,3 +152,39 @@ def test_bf16_conv_window_rejects_strided(nk):
     W = synth.small_ints(88, 1, (3, 3, 64, 64))
     with pytest.raises(nk.NkError):
         _conv(nk, I, W, (2, 2), (1, 1), (1, 1, 1, 1), schedule=(128, 64, 576, 1, 2, 1))
+
+
+@pytest.mark.parametrize("case", [(2, 11, 13, 64, 96, 3, 3, 1), (1, 9, 9, 20, 40, 3, 3, 1), (2, 10, 10, 72, 64, 3, 3, 2),
+                                  (1, 7, 7, 128, 80, 1, 1, 1)])
+@pytest.mark.parametrize("path", ["window", "tap"])
+def test_bf16_conv_packed_weights_bitwise(nk, case, path):
+    """Weights packed once by nk_conv2d_pack_weights (BF16, channels
+    contiguous per filter tap) give the same bits as FP32 weights converted
+    per call, on both kernels."""
+    N, H, Wd, C, F, KH, KW, s = case
+    if path == "window" and (s != 1 or KH * KW == 1):
+        pytest.skip("the window kernel is for stride-1 multi-tap convolutions")
+    I = synth.small_ints(89, H * 100 + C, (N, H, Wd, C))
+    W = synth.small_ints(89, F * 100 + KH, (KH, KW, C, F))
+    sched = (128, 64, 64 * KH * KW if path == "window" else 64, 1, 2, 1)
+    pad = (KH // 2,) * 4
+    ref = _conv(nk, I, W, (s, s), (1, 1), pad, schedule=sched)
+    Wp = nk.nk_conv2d_pack_weights(dev(W))
+    assert Wp.dtype == torch.bfloat16 and Wp.stride(2) == 1 and Wp.stride(1) % 8 == 0
+    N_, OH, OW = N, ref.shape[1], ref.shape[2]
+    out = torch.empty(N_, OH, OW, F, device=DEV)
+    # FP32 I: converted (channels padded to 8) in the workspace, beside the packed BF16 W
+    nk.nk_conv2d_nhwc_hwcf(dev(I), Wp, out, stride=(s, s), pad=pad, precision="bf16", schedule=sched)
+    nk.nk_sync_status()
+    np.testing.assert_array_equal(host(out), ref)
+    np.testing.assert_array_equal(ref, O.conv2d_nhwc_hwcf(I, W, (s, s), (1, 1), pad))
+
+
+def test_bf16_conv_rejects_unpacked_bf16_weights(nk):
+    """A BF16 W in plain HWCF order (F innermost) is not the packed layout."""
+    I = synth.small_ints(90, 0, (1, 8, 8, 64))
+    W = synth.small_ints(90, 1, (3, 3, 64, 64))
+    out = torch.empty(1, 8, 8, 64, device=DEV)
+    with pytest.raises(nk.NkError):
+        nk.nk_conv2d_nhwc_hwcf(dev(I).to(torch.bfloat16), dev(W).to(torch.bfloat16), out, pad=(1, 1, 1, 1),
+                               precision="bf16")
