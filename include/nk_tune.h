@@ -82,6 +82,18 @@ nk_status nk_tune_release(void);
 nk_status nk_tune(const nk_problem* p, int32_t mode, int32_t topk, const float* mlp_params,
                   int32_t reps, nk_schedule* best, nk_tune_report* rep, void* stream);
 
+/* Grouped GEMM: the tile of a grouped plan (nk_grouped_plan_create) for this
+ * set of groups.  Times every legal grouped schedule (tile_m 128, cluster 1,
+ * split_k 1; tile_n 64 / 128 / 256; stages 2..8 within shared memory) as a
+ * persistent launch on the caller's operands and returns the fastest in
+ * *best (ties to the earlier candidate).  While timing, every group's C is
+ * overwritten (accumulate flags are ignored); its contents afterwards are
+ * unspecified.  Synchronises `stream`; allocates plan tables while it runs.
+ * `rep` may be NULL (default_ms: the schedule nk_grouped_plan_create picks
+ * for sched = NULL).                                                       */
+nk_status nk_grouped_tune(int32_t G, const nk_gemm_group* groups, int32_t precision, int32_t reps,
+                          nk_schedule* best, nk_tune_report* rep, void* stream);
+
 /* ------------------------------------------------------- the cost model */
 /* Parameters: one FP32 device buffer of nk_mlp_param_count() values laid out
  * W1 [128][16], b1 [128], W2 [128][128], b2 [128], W3 [128], b3 [1].

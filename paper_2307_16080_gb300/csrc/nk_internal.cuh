@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
 #include <string>
 
 #include "../../include/nk.h"
@@ -33,6 +34,13 @@ int64_t wait_budget();
 
 // Reads and clears the failure words of every translation unit.
 nk_status collect_device_errors(uint32_t* flags);
+
+// Median device time (ms) of one call of `run` (which enqueues its kernels
+// on the stream it is given): graph replays of back-to-back calls on a
+// library stream, behind a hold kernel, so host call overhead is not timed
+// (tune.cu).
+using RunFn = std::function<nk_status(cudaStream_t)>;
+nk_status time_device(const RunFn& run, int reps, float* ms);
 uint32_t tc_read_and_clear_errors();   // tcgen05 GEMM / conv units
 
 // ----------------------------------------------------------- SIMT (FP32)

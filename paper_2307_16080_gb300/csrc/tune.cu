@@ -266,13 +266,13 @@ cudaStream_t timing_stream() {
   return st[dev];
 }
 
-// Captures `runs` back-to-back runs of one schedule into a graph.
-nk_status capture_runs(Runner& r, const nk_schedule& s, int runs, cudaStream_t st, cudaGraphExec_t* exec) {
+// Captures `runs` back-to-back calls of `run` into a graph.
+nk_status capture_runs(const RunFn& run, int runs, cudaStream_t st, cudaGraphExec_t* exec) {
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture(tune)");
   nk_status status = NK_OK;
-  for (int i = 0; i < runs && status == NK_OK; ++i) status = r.run(s, st);
+  for (int i = 0; i < runs && status == NK_OK; ++i) status = run(st);
   e = cudaStreamEndCapture(st, &graph);
   if (status != NK_OK || e != cudaSuccess) {
     if (graph) cudaGraphDestroy(graph);
@@ -284,27 +284,22 @@ nk_status capture_runs(Runner& r, const nk_schedule& s, int runs, cudaStream_t s
   return e == cudaSuccess ? NK_OK : cuda_fail(e, "cudaGraphInstantiate(tune)");
 }
 
-// Median device time of one schedule.  Two eager runs first (errors surface,
-// caches and kernel attributes warm).  The GPU's event clock ticks in steps
-// of about 2 us, so each timed sample is a graph of `inner` back-to-back runs
-// (inner chosen so a sample lasts about 400 us) between two events, and the
-// samples are queued behind hold_kernel: what is timed is the kernels alone,
-// not the host work of a call.
-nk_status time_one(const nk_problem* p, const nk_schedule& s, int reps, float* ms, cudaStream_t user) {
-  Runner r(p, s);
-  void* buf = nullptr;
-  nk_status status = scratch(r.padded_total(), &buf);
-  if (status != NK_OK) return status;
-  r.bind(static_cast<char*>(buf));
-  if ((status = fill(r.op_bytes + 1024)) != NK_OK) return status;
-  cudaError_t e = user ? cudaStreamSynchronize(user) : cudaSuccess;
-  if (e == cudaSuccess) e = cudaDeviceSynchronize();
-  if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+}  // namespace
+
+// Median device time of one call of `run`.  Two eager calls first (errors
+// surface, caches and kernel attributes warm).  The GPU's event clock ticks
+// in steps of about 2 us, so each timed sample is a graph of `inner`
+// back-to-back calls (inner chosen so a sample lasts about 400 us) between
+// two events, and the samples are queued behind hold_kernel: what is timed is
+// the kernels alone, not the host work of a call.
+nk_status time_device(const RunFn& run, int reps, float* ms) {
   cudaStream_t st = timing_stream();
   if (!st) return fail(NK_ERR_CUDA, "no timing stream");
+  nk_status status = NK_OK;
   for (int i = 0; i < 2; ++i)
-    if ((status = r.run(s, st)) != NK_OK) return status;
-  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize(tune)");
+    if ((status = run(st)) != NK_OK) return status;
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize(tune)");
   {
     uint32_t flags = 0;
     collect_device_errors(&flags);
@@ -313,9 +308,9 @@ nk_status time_one(const nk_problem* p, const nk_schedule& s, int reps, float* m
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  // rough duration of one run: 8 eager runs between two events
+  // rough duration of one call: 8 eager calls between two events
   cudaEventRecord(e0, st);
-  for (int i = 0; i < 8 && status == NK_OK; ++i) status = r.run(s, st);
+  for (int i = 0; i < 8 && status == NK_OK; ++i) status = run(st);
   cudaEventRecord(e1, st);
   e = cudaStreamSynchronize(st);
   float rough = 0.f;
@@ -327,7 +322,7 @@ nk_status time_one(const nk_problem* p, const nk_schedule& s, int reps, float* m
   rough = std::max(rough / 8.f, 0.002f);
   const int inner = std::max(1, std::min(64, (int)std::ceil(0.4f / rough)));
   cudaGraphExec_t exec = nullptr;
-  if ((status = capture_runs(r, s, inner, st, &exec)) != NK_OK) return status;
+  if ((status = capture_runs(run, inner, st, &exec)) != NK_OK) return status;
 
   reps = reps < 1 ? 1 : reps;
   std::vector<cudaEvent_t> ev(2 * reps);
@@ -357,6 +352,22 @@ nk_status time_one(const nk_problem* p, const nk_schedule& s, int reps, float* m
   std::sort(t.begin(), t.end());
   *ms = t[reps / 2];
   return NK_OK;
+}
+
+namespace {
+
+// Device time of one schedule on synthetic operands of the problem's shape.
+nk_status time_one(const nk_problem* p, const nk_schedule& s, int reps, float* ms, cudaStream_t user) {
+  Runner r(p, s);
+  void* buf = nullptr;
+  nk_status status = scratch(r.padded_total(), &buf);
+  if (status != NK_OK) return status;
+  r.bind(static_cast<char*>(buf));
+  if ((status = fill(r.op_bytes + 1024)) != NK_OK) return status;
+  cudaError_t e = user ? cudaStreamSynchronize(user) : cudaSuccess;
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+  return time_device([&](cudaStream_t st) { return r.run(s, st); }, reps, ms);
 }
 
 // (1+1) evolution strategy on the schedule grid.  Coordinates: tile_m,
@@ -480,6 +491,57 @@ nk_status nk_schedule_features(const nk_problem* p, const nk_schedule* s, int32_
   if (count < 0 || (count > 0 && (!s || !f))) return fail(NK_ERR_INVALID_ARG, "bad feature arguments");
   const int sms = sm_count();
   for (int i = 0; i < count; ++i) features(p, s[i], sms, f + (size_t)i * NK_TUNE_FEATURES);
+  return NK_OK;
+}
+
+nk_status nk_grouped_tune(int32_t G, const nk_gemm_group* groups, int32_t precision, int32_t reps,
+                          nk_schedule* best, nk_tune_report* rep, void* stream) {
+  if (!best) return fail(NK_ERR_INVALID_ARG, "best is NULL");
+  if (G < 1 || !groups) return fail(NK_ERR_INVALID_ARG, "need at least one group");
+  nk_status st = require_device();
+  if (st != NK_OK) return st;
+  std::lock_guard<std::mutex> lk(g_mu);
+  cudaStream_t user = static_cast<cudaStream_t>(stream);
+  cudaError_t e = user ? cudaStreamSynchronize(user) : cudaSuccess;
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+  std::vector<nk_gemm_group> gs(groups, groups + G);
+  for (auto& q : gs) q.accumulate = 0;   // repeated runs must not pile up into C
+  auto time_plan = [&](const nk_schedule* s, float* ms) -> nk_status {
+    nk_grouped_plan* plan = nullptr;
+    nk_status r = nk_grouped_plan_create(G, gs.data(), precision, s, &plan);
+    if (r != NK_OK) return r;
+    r = time_device([&](cudaStream_t cs) { return nk_grouped_plan_run(plan, cs); }, reps, ms);
+    nk_grouped_plan_destroy(plan);
+    return r;
+  };
+  float dms = 0.f;
+  if ((st = time_plan(nullptr, &dms)) != NK_OK) return st;
+  int cands = 0, timed = 0;
+  float best_ms = 0.f;
+  for (int tn : {64, 128, 256})
+    for (int stages = 2; stages <= 8; ++stages) {
+      const nk_schedule s{128, tn, 64, 1, stages, 1};
+      nk_grouped_plan* probe = nullptr;
+      nk_status r = nk_grouped_plan_create(G, gs.data(), precision, &s, &probe);
+      if (r == NK_ERR_NO_SCHEDULE) continue;   // does not fit shared memory
+      if (r != NK_OK) return r;
+      nk_grouped_plan_destroy(probe);
+      ++cands;
+      float ms = 0.f;
+      if ((st = time_plan(&s, &ms)) != NK_OK) return st;
+      ++timed;
+      if (timed == 1 || ms < best_ms) {
+        best_ms = ms;
+        *best = s;
+      }
+    }
+  if (rep) {
+    rep->candidates = cands;
+    rep->timed = timed;
+    rep->best_ms = best_ms;
+    rep->default_ms = dms;
+  }
   return NK_OK;
 }
 

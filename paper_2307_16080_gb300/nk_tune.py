@@ -35,6 +35,7 @@ SIGNATURES = {
     "nk_time_schedule": (_I32, [_PP, _PS, _I32, ctypes.POINTER(ctypes.c_float), _P]),
     "nk_tune_release": (_I32, []),
     "nk_tune": (_I32, [_PP, _I32, _I32, _P, _I32, _PS, ctypes.POINTER(nk_tune_report), _P]),
+    "nk_grouped_tune": (_I32, [_I32, _P, _I32, _I32, _PS, ctypes.POINTER(nk_tune_report), _P]),
     "nk_mlp_param_count": (_SZ, []),
     "nk_mlp_forward": (_I32, [_P, _P, _I64, _P, _P]),
     "nk_mlp_workspace_size": (_SZ, [_I64]),
@@ -106,6 +107,16 @@ def nk_tune(p: nk_problem, mode=NK_TUNE_EXHAUSTIVE, topk=5, params: torch.Tensor
     rep = nk_tune_report()
     _check(lib().nk_tune(ctypes.byref(p), mode, topk, params.data_ptr() if params is not None else None, reps,
                          ctypes.byref(best), ctypes.byref(rep), _stream(stream)))
+    return best.as_tuple(), rep
+
+
+def nk_grouped_tune(groups, G, precision="bf16", reps=3, stream=None):
+    """Fastest grouped-plan schedule for these groups (from nk.make_groups);
+    overwrites every group's C while timing."""
+    best = nk_schedule()
+    rep = nk_tune_report()
+    _check(lib().nk_grouped_tune(G, ctypes.cast(groups, ctypes.c_void_p), nk.PREC[precision], reps,
+                                 ctypes.byref(best), ctypes.byref(rep), _stream(stream)))
     return best.as_tuple(), rep
 
 

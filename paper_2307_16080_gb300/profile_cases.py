@@ -12,7 +12,7 @@ CASE:
   conv      BF16 conv, batch 32 x 56 x 56 x 64, 3 x 3 x 64 x 64, built-in schedule (the
             shared-window kernel)
   conv_tap  the same layer on the per-tap implicit-GEMM kernel, schedule (128, 64, 64, 1, 3, 1)
-  grouped   512 uneven BF16 GEMMs, one persistent launch
+  grouped   512 uneven BF16 GEMMs, one persistent launch, tile chosen by nk_grouped_tune
   splitk    FP32 1024 x 1024 x 16384 with split-K 8 (partials + fixed-order reduce)
 Prints one JSON line per measurement.  Times are device times: `calls`
 back-to-back calls captured into a CUDA graph, replayed between CUDA events.
@@ -127,7 +127,9 @@ def case_grouped(reps):
     bt = [torch.empty(N, K, device="cuda").uniform_(-1, 1).to(torch.bfloat16) for (M, N, K) in shapes]
     c = [torch.empty(M, N, device="cuda") for (M, N, K) in shapes]
     groups, G = nk.make_groups(a, bt, c)
-    plan = nk.nk_grouped_plan_create(groups, G)
+    from . import nk_tune as nt
+    best, _ = nt.nk_grouped_tune(groups, G, reps=3)
+    plan = nk.nk_grouped_plan_create(groups, G, schedule=best)
     f = float(sum(2.0 * M * N * K for (M, N, K) in shapes))
     _emit("grouped 512 bf16 gemms", _time(lambda: nk.nk_grouped_plan_run(plan), reps), flop=f)
     nk.nk_grouped_plan_destroy(plan)

@@ -132,3 +132,23 @@ def test_grouped_rejects_bad_groups(nk):
     with pytest.raises(nk.NkError) as e:
         nk.nk_batch_matmul_grouped(groups, G)
     assert e.value.status == -3
+
+
+def test_grouped_tune_picks_a_legal_fast_schedule_and_stays_exact(nk):
+    """nk_grouped_tune times every legal grouped schedule on the caller's
+    groups; the winner is no slower than the built-in choice (it is one of
+    the candidates) and a plan built with it is still exact."""
+    from paper_2307_16080_gb300 import nk_tune as nt
+    As, Bs, a, bt, c = _operands(SMALL, 71, ints=True)
+    groups, G = nk.make_groups(a, bt, c, accumulate=True)   # accumulate is ignored while tuning
+    best, rep = nt.nk_grouped_tune(groups, G, reps=3)
+    assert rep.timed == rep.candidates >= 10
+    assert best[0] == 128 and best[1] in (64, 128, 256) and best[3] == 1 and best[5] == 1 and 2 <= best[4] <= 8
+    assert 0 < rep.best_ms <= rep.default_ms * 1.05
+    groups, G = nk.make_groups(a, bt, c)
+    plan = nk.nk_grouped_plan_create(groups, G, schedule=best)
+    nk.nk_grouped_plan_run(plan)
+    nk.nk_sync_status()
+    nk.nk_grouped_plan_destroy(plan)
+    for g in range(G):
+        np.testing.assert_array_equal(host(c[g]), O.matmul(As[g], Bs[g]))
