@@ -327,6 +327,23 @@ def grouped_report(torch, nk, synth, dev):
             "launches": {"persistent": 1, "per_gemm": G}}
 
 
+def layer_roofline(N, H, W, C, F, KH, KW, stride, pad, ms):
+    """min(tensor peak, HBM x arithmetic intensity) for one BF16 conv layer:
+    2 B per input element (BF16 NHWC), 4 B per output element (FP32), 2 B per
+    packed weight; achieved = FLOP / measured time."""
+    bf16_peak, hbm, src = peaks()
+    oh = (H + 2 * pad - KH) // stride + 1
+    ow = (W + 2 * pad - KW) // stride + 1
+    flop = 2.0 * N * oh * ow * F * KH * KW * C
+    nbytes = 2.0 * N * H * W * C + 4.0 * N * oh * ow * F + 2.0 * KH * KW * C * F
+    ai = flop / nbytes
+    roof = min(bf16_peak, hbm * 1e-3 * ai)    # TFLOP/s
+    achieved = flop / (ms * 1e-3) / 1e12
+    return {"flop": flop, "bytes": nbytes, "ai_flop_per_byte": ai, "bound": "hbm" if roof < bf16_peak else "tensor",
+            "roofline_tflops": roof, "achieved_tflops": achieved, "frac": achieved / roof,
+            "peak_source": f"{src} (MEASURED_PEAKS.json)"}
+
+
 def conv_report(torch, nk, synth, dev):
     """FP32 conv config (8x56x56x64, 3x3x64x64, s1 p1, bias + ReLU) on the
     CUDA cores, and the same layer in BF16 on the tensor cores."""
@@ -353,6 +370,7 @@ def conv_report(torch, nk, synth, dev):
             "graph_bf16_over_f32": g32 / g16,
             "graph_bf16_packed_ms": gp, "graph_bf16_packed_tflops": flop / (gp * 1e-3) / 1e12,
             "graph_bf16_packed_over_f32": g32 / gp,
+            "roofline_bf16_packed": layer_roofline(8, 56, 56, 64, 64, 3, 3, 1, 1, gp),
             "note": "per call: host overhead included; graph: device time of calls replayed from a CUDA graph; "
                     "bf16 includes the per-call FP32 -> BF16 weight cast, bf16_packed takes weights packed once "
                     "by nk_conv2d_pack_weights"}
@@ -424,7 +442,13 @@ def stack_graph(torch, synth, dev, batch, picks, flop):
     ms = graph_time(torch, forward, calls=2, reps=10)
     nk.nk_sync_status()
     kernels = sum(2 if sched[5] > 1 else 1 for sched in picks)   # split-K adds its reduce
+    # the stack's roofline time: each layer at min(tensor peak, HBM x its arithmetic intensity)
+    roof_ms = 0.0
+    for L in synth.resnet_stack(batch):
+        r = layer_roofline(L["N"], L["H"], L["W"], L["C"], L["F"], L["KH"], L["KW"], L["stride"], L["pad"], 1.0)
+        roof_ms += r["flop"] / (r["roofline_tflops"] * 1e12) * 1e3
     return {"ms": ms, "tflops": flop / (ms * 1e-3) / 1e12, "kernels_per_forward": kernels,
+            "roofline_ms": roof_ms, "frac_of_roofline": roof_ms / ms,
             "how": "20 nk_conv2d calls on packed BF16 weights (one conv kernel each) in one CUDA graph, device time"}
 
 

@@ -68,6 +68,34 @@ def test_variants_small_ints_bitwise(nk, case):
     np.testing.assert_array_equal(got, R)
 
 
+@pytest.mark.parametrize("case", [
+    # stride 1, dilation 1, 1x1 / 3x3 / 5x5: the register-streaming kernel
+    ((1, 1, 21, 1283), (3, 1, 3, 3), (1, 1), (1, 1), (0, 0, 0, 0)),     # odd widths: 8-byte-aligned rows
+    ((2, 3, 13, 37), (10, 3, 3, 3), (1, 1), (1, 1), (1, 2, 0, 1)),      # 3 channel groups, uneven padding
+    ((1, 2, 19, 45), (5, 2, 5, 5), (1, 1), (1, 1), (2, 2, 2, 2)),
+    ((2, 4, 7, 530), (6, 4, 1, 1), (1, 1), (1, 1), (0, 0, 0, 0)),       # rows wider than one CTA
+    ((1, 1, 6, 6), (3, 1, 3, 3), (1, 1), (1, 1), (3, 3, 3, 3)),         # output mostly padding
+    # one input channel: the rotating-accumulator kernel
+    ((2, 1, 30, 77), (7, 1, 5, 5), (1, 1), (1, 1), (2, 1, 2, 0)),       # 2 channel groups, 5x5
+    ((1, 1, 9, 300), (5, 1, 1, 1), (1, 1), (1, 1), (0, 0, 0, 0)),
+    ((3, 1, 2, 9), (3, 1, 3, 3), (1, 1), (1, 1), (1, 1, 1, 1)),         # fewer rows than taps
+])
+def test_streaming_kernel_small_ints_bitwise(nk, case):
+    ish, ksh, st, dl, pad = case
+    I = synth.small_ints(95, ish[3], ish)
+    K = synth.small_ints(95, ksh[0], ksh)
+    got, R = _run(nk, I, K, st, dl, pad)
+    np.testing.assert_array_equal(got, R)
+
+
+def test_paper_workload_batch16(nk):
+    """16 images of the tuning experiment's shape (larger than L2)."""
+    I = synth.normal(96, 0, (16, 1, 1280, 1280))
+    K = synth.normal(96, 1, (3, 1, 3, 3))
+    got, R = _run(nk, I, K)
+    assert O.rel_frobenius(got, R) <= 1e-6
+
+
 def test_epilogue_bias_relu_accumulate(nk):
     I = synth.normal(93, 0, (2, 3, 30, 90))
     K = synth.normal(93, 1, (6, 3, 3, 3))
