@@ -359,6 +359,9 @@ def conv_report(torch, nk, synth, dev):
     t16 = time_fn(torch, f16, 20)
     g32 = graph_time(torch, lambda: nk.nk_conv2d_nhwc_hwcf(i32, w32, out, pad=(1, 1, 1, 1), bias=b32, relu=True))
     g16 = graph_time(torch, f16)
+    ws8 = nk.workspace(nk.nk_conv2d_workspace_size(i32, w32, out, pad=(1, 1, 1, 1), precision="fp8"), dev)
+    g8 = graph_time(torch, lambda: nk.nk_conv2d_nhwc_hwcf(i32, w32, out, pad=(1, 1, 1, 1), precision="fp8",
+                                                          bias=b32, relu=True, ws=ws8))
     wp = nk.nk_conv2d_pack_weights(w32)
     ws_p = nk.workspace(nk.nk_conv2d_workspace_size(i16, wp, out, pad=(1, 1, 1, 1), precision="bf16"), dev)
     gp = graph_time(torch, lambda: nk.nk_conv2d_nhwc_hwcf(i16, wp, out, pad=(1, 1, 1, 1), precision="bf16",
@@ -371,9 +374,10 @@ def conv_report(torch, nk, synth, dev):
             "graph_bf16_packed_ms": gp, "graph_bf16_packed_tflops": flop / (gp * 1e-3) / 1e12,
             "graph_bf16_packed_over_f32": g32 / gp,
             "roofline_bf16_packed": layer_roofline(8, 56, 56, 64, 64, 3, 3, 1, 1, gp),
+            "graph_fp8_ms": g8, "graph_fp8_tflops": flop / (g8 * 1e-3) / 1e12, "graph_fp8_over_f32": g32 / g8,
             "note": "per call: host overhead included; graph: device time of calls replayed from a CUDA graph; "
                     "bf16 includes the per-call FP32 -> BF16 weight cast, bf16_packed takes weights packed once "
-                    "by nk_conv2d_pack_weights"}
+                    "by nk_conv2d_pack_weights, fp8 includes the per-call amax and E4M3 quantisation of I and W"}
 
 
 def resnet_report(torch, synth, dev):

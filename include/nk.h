@@ -174,9 +174,12 @@ nk_status nk_grouped_workspace_size(int32_t G, const nk_gemm_group* groups,
  * stride in the last dimension.  OH = (H + pt + pb - dh*(KH-1) - 1)/sh + 1
  * (same for OW).  stride = {sh, sw}, dilation = {dh, dw},
  * pad = {top, bottom, left, right}.
- * I dtype: F32 (any precision; BF16 converts it into the workspace) or BF16
- * with NK_PREC_BF16.  W dtype: F32 contiguous HWCF (converted per call into
- * the workspace at NK_PREC_BF16), or -- NK_PREC_BF16 only -- BF16 already
+ * Precisions: NK_PREC_F32 (CUDA cores), NK_PREC_BF16, NK_PREC_FP8 (E4M3
+ * with per-tensor scales s = 448/amax(|x|) of I and of W, computed on the
+ * device and undone by 1/(s_i*s_w) in the epilogue; I and W FP32).
+ * I dtype: F32 (any precision; BF16 / E4M3 convert it into the workspace)
+ * or BF16 with NK_PREC_BF16.  W dtype: F32 contiguous HWCF (converted per
+ * call into the workspace), or -- NK_PREC_BF16 only -- BF16 already
  * packed by nk_conv2d_pack_weights, described as [KH,KW,C,F] with strides
  * {KW*ldw, ldw, 1, sF} (ldw >= C, sF >= KH*KW*ldw, multiples of 8; 16-byte
  * aligned base): no per-call conversion.

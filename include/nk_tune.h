@@ -29,7 +29,7 @@ typedef enum { NK_TUNE_EXHAUSTIVE = 0, NK_TUNE_MODEL_TOPK = 1, NK_TUNE_EVOLUTION
 /* A tensor-core problem: matmul (M, N, K) or conv (n, h, w, c -> f with a
  * kh x kw filter, equal stride and padding on both axes, dilation 1).
  * precision: NK_PREC_BF16 / NK_PREC_FP8 / NK_PREC_BF16X3 (matmul),
- * NK_PREC_BF16 (conv).                                                     */
+ * NK_PREC_BF16 / NK_PREC_FP8 (conv).                                       */
 typedef struct {
   int32_t op;
   int32_t precision;

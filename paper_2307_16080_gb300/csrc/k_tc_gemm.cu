@@ -64,6 +64,7 @@ struct ConvTile {
   int N, OH, OW;
   int sh, sw, dh, dw, pt, pl;
   int KW, cblocks;
+  int cblk;               // channels per K block: one 128-byte row (64 BF16, 128 E4M3)
 };
 
 struct TcParams {
@@ -324,7 +325,7 @@ __global__ void __launch_bounds__(WIDE ? 320 : 192, 1) tc_gemm_kernel(const __gr
             if constexpr (CONV) {
               const ConvTile& c = p.cv;
               if (rank == 0) ptx::mbar_arrive_expect_tx(full_bar(s), 2u * (p.a_box_bytes + (uint32_t)b_bytes));
-              const int tap = kb / c.cblocks, c0 = (kb % c.cblocks) * 64;
+              const int tap = kb / c.cblocks, c0 = (kb % c.cblocks) * c.cblk;
               const int kh = tap / c.KW, kw = tap % c.KW;
               const int tw = t.tm % c.tiles_w, th = (t.tm / c.tiles_w) % c.tiles_h;
               const int tb = t.tm / (c.tiles_w * c.tiles_h);
@@ -354,7 +355,7 @@ __global__ void __launch_bounds__(WIDE ? 320 : 192, 1) tc_gemm_kernel(const __gr
             // input window that tap sees, shifted and strided by TMA.
             const ConvTile& c = p.cv;
             ptx::mbar_arrive_expect_tx(full_bar(s), MCH * p.a_box_bytes + (uint32_t)b_bytes);
-            const int tap = kb / c.cblocks, c0 = (kb % c.cblocks) * 64;
+            const int tap = kb / c.cblocks, c0 = (kb % c.cblocks) * c.cblk;
             const int kh = tap / c.KW, kw = tap % c.KW;
             for (int ch = 0; ch < MCH; ++ch) {
               const int ct = t.tm * MCH + ch;   // conv tile of this chain
@@ -888,6 +889,7 @@ ConvTile search_conv_tile(const ConvGeom& g, int maxrows) {
   best.N = g.n; best.OH = g.oh; best.OW = g.ow;
   best.sh = g.sh; best.sw = g.sw; best.dh = g.dh; best.dw = g.dw; best.pt = g.pt; best.pl = g.pl;
   best.KW = g.kw;
+  best.cblk = 64;
   best.cblocks = (g.c + 63) / 64;
   return best;
 }
@@ -896,7 +898,7 @@ ConvTile search_conv_tile(const ConvGeom& g, int maxrows) {
 std::mutex g_ctile_mu;
 std::vector<std::pair<ConvGeom, ConvTile>> g_ctile_cache;
 
-ConvTile choose_conv_tile(const ConvGeom& g) {
+ConvTile cached_conv_tile(const ConvGeom& g) {
   std::lock_guard<std::mutex> lk(g_ctile_mu);
   for (auto& e : g_ctile_cache)
     if (std::memcmp(&e.first, &g, sizeof g) == 0) return e.second;
@@ -906,16 +908,27 @@ ConvTile choose_conv_tile(const ConvGeom& g) {
   return t;
 }
 
+// The tile of a geometry, with K blocks of one 128-byte row of channels.
+ConvTile choose_conv_tile(const ConvGeom& g, int kind) {
+  ConvTile t = cached_conv_tile(g);
+  t.cblk = kind == TC_FP8 ? 128 : 64;
+  t.cblocks = (g.c + t.cblk - 1) / t.cblk;
+  return t;
+}
+
 nk_status make_conv_maps(TcParams& p, const TcConv& c, const ConvTile& t, int bn_box) {
   auto fn = encode_fn();
   if (!fn) return fail(NK_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
   const ConvGeom& g = c.g;
+  const bool fp8 = c.kind == TC_FP8;
+  const int esz = fp8 ? 1 : 2;
+  const CUtensorMapDataType dt = fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   {
     cuuint64_t dims[4] = {(cuuint64_t)g.c, (cuuint64_t)g.w, (cuuint64_t)g.h, (cuuint64_t)g.n};
-    cuuint64_t strides[3] = {(cuuint64_t)c.sI_w * 2, (cuuint64_t)c.sI_h * 2, (cuuint64_t)c.sI_n * 2};
-    cuuint32_t box[4] = {64, (cuuint32_t)(t.Q * g.sw), (cuuint32_t)(t.R * g.sh), (cuuint32_t)t.NB};
+    cuuint64_t strides[3] = {(cuuint64_t)c.sI_w * esz, (cuuint64_t)c.sI_h * esz, (cuuint64_t)c.sI_n * esz};
+    cuuint32_t box[4] = {(cuuint32_t)t.cblk, (cuuint32_t)(t.Q * g.sw), (cuuint32_t)(t.R * g.sh), (cuuint32_t)t.NB};
     cuuint32_t es[4] = {1, (cuuint32_t)g.sw, (cuuint32_t)g.sh, 1};
-    CUresult r = fn(&p.tmA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(c.I), dims, strides, box,
+    CUresult r = fn(&p.tmA, dt, 4, const_cast<void*>(c.I), dims, strides, box,
                     es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(NK_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d) for the conv input", (int)r);
@@ -923,10 +936,10 @@ nk_status make_conv_maps(TcParams& p, const TcConv& c, const ConvTile& t, int bn
   {
     const int taps = g.kh * g.kw;
     cuuint64_t dims[3] = {(cuuint64_t)g.c, (cuuint64_t)taps, (cuuint64_t)c.F};
-    cuuint64_t strides[2] = {(cuuint64_t)c.ldw * 2, (cuuint64_t)c.sW_f * 2};
-    cuuint32_t box[3] = {64, 1, (cuuint32_t)bn_box};
+    cuuint64_t strides[2] = {(cuuint64_t)c.ldw * esz, (cuuint64_t)c.sW_f * esz};
+    cuuint32_t box[3] = {(cuuint32_t)t.cblk, 1, (cuuint32_t)bn_box};
     cuuint32_t es[3] = {1, 1, 1};
-    CUresult r = fn(&p.tmB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(c.Wt), dims, strides, box,
+    CUresult r = fn(&p.tmB, dt, 3, const_cast<void*>(c.Wt), dims, strides, box,
                     es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(NK_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d) for the conv weights", (int)r);
@@ -936,10 +949,13 @@ nk_status make_conv_maps(TcParams& p, const TcConv& c, const ConvTile& t, int bn
 
 }  // namespace
 
-bool tc_conv_schedule_valid(const ConvGeom& g, int F, const nk_schedule& s) {
-  if (halo_schedule(g, s)) return halo_schedule_valid(g, F, s);
+bool tc_conv_schedule_valid(const ConvGeom& g, int F, const nk_schedule& s, int kind) {
+  if (kind == TC_BF16 && halo_schedule(g, s)) return halo_schedule_valid(g, F, s);
+  if (kind != TC_BF16 && kind != TC_FP8) return false;
   if (g.sw > 8 || g.sh > 8 || s.tile_n == 512) return false;
-  return tc_schedule_valid(TC_BF16, s, g.n * g.oh * g.ow, F, g.kh * g.kw * g.c);
+  // E4M3 convolutions: one CTA or a multicast cluster, tall tiles (no CTA pairs)
+  if (kind == TC_FP8 && s.tile_m == 256 && s.cluster == 2) return false;
+  return tc_schedule_valid(kind, s, g.n * g.oh * g.ow, F, g.kh * g.kw * g.c);
 }
 
 // The shared-window kernel where it wins (see tc_halo_default_schedule).
@@ -948,13 +964,15 @@ bool tc_conv_schedule_valid(const ConvGeom& g, int F, const nk_schedule& s) {
 // as leave room for two CTAs per SM (short K loops gain more from a second
 // CTA than from deeper rings), and split-K while the grid would leave half
 // the SMs idle.
-nk_schedule tc_conv_default_schedule(const ConvGeom& g, int F, int sms) {
+nk_schedule tc_conv_default_schedule(const ConvGeom& g, int F, int sms, int kind) {
   bool ok = false;
-  nk_schedule h = tc_halo_default_schedule(g, F, sms, &ok);
-  if (ok) return h;
+  if (kind == TC_BF16) {
+    nk_schedule h = tc_halo_default_schedule(g, F, sms, &ok);
+    if (ok) return h;
+  }
   nk_schedule s{};
   s.tile_m = 128;
-  s.tile_k = 64;
+  s.tile_k = kind == TC_FP8 ? 128 : 64;
   s.tile_n = F <= 64 ? 64 : 128;
   s.cluster = 1;
   s.split_k = 1;
@@ -963,11 +981,11 @@ nk_schedule tc_conv_default_schedule(const ConvGeom& g, int F, int sms) {
   for (;;) {
     nk_schedule n = s;
     n.stages = s.stages + 1;
-    const int need = smem_of(TC_BF16, n);
+    const int need = smem_of(kind, n);
     if (n.stages > 8 || need > kMaxSmem || (two && 2 * (need + 1024) > kMaxSmem + 1024)) break;
     s = n;
   }
-  const ConvTile t = choose_conv_tile(g);
+  const ConvTile t = choose_conv_tile(g, kind);
   const int ctiles = t.tiles_w * t.tiles_h * ((g.n + t.NB - 1) / t.NB);
   const int tiles = ctiles * ((F + s.tile_n - 1) / s.tile_n);
   const int nkb = g.kh * g.kw * t.cblocks;
@@ -976,7 +994,7 @@ nk_schedule tc_conv_default_schedule(const ConvGeom& g, int F, int sms) {
 }
 
 size_t tc_conv_ws(const TcConv& c, const nk_schedule& s) {
-  if (s.split_k <= 1 || halo_schedule(c.g, s)) return 0;
+  if (s.split_k <= 1 || (c.kind == TC_BF16 && halo_schedule(c.g, s))) return 0;
   return (size_t)s.split_k * c.g.n * c.g.oh * c.g.ow * c.F * sizeof(float);
 }
 
@@ -985,14 +1003,17 @@ nk_status tc_conv(const TcConv& c, const nk_schedule& s, void* ws, size_t ws_byt
   nk_status status = require_device(&sms);
   if (status != NK_OK) return status;
   const ConvGeom& g = c.g;
-  if (halo_schedule(g, s)) return tc_halo_conv(c, s, st);
+  const int kind = c.kind;
+  if (kind == TC_BF16 && halo_schedule(g, s)) return tc_halo_conv(c, s, st);
   const int M = g.n * g.oh * g.ow;
   if (g.sw > 8 || g.sh > 8) return fail(NK_ERR_UNSUPPORTED, "conv stride above 8");
-  if (!tc_conv_schedule_valid(g, c.F, s)) return fail(NK_ERR_NO_SCHEDULE, "illegal tensor-core schedule for conv");
-  if ((c.sI_w * 2) % 16 || (c.sI_h * 2) % 16 || (c.sI_n * 2) % 16 || (c.ldw * 2) % 16 || (c.sW_f * 2) % 16 ||
-      (reinterpret_cast<uintptr_t>(c.I) & 15) || (reinterpret_cast<uintptr_t>(c.Wt) & 15))
+  if (!tc_conv_schedule_valid(g, c.F, s, kind))
+    return fail(NK_ERR_NO_SCHEDULE, "illegal tensor-core schedule for conv");
+  const int esz = kind == TC_FP8 ? 1 : 2;
+  if ((c.sI_w * esz) % 16 || (c.sI_h * esz) % 16 || (c.sI_n * esz) % 16 || (c.ldw * esz) % 16 ||
+      (c.sW_f * esz) % 16 || (reinterpret_cast<uintptr_t>(c.I) & 15) || (reinterpret_cast<uintptr_t>(c.Wt) & 15))
     return fail(NK_ERR_MISALIGNED, "conv operands need 16-byte aligned bases and strides");
-  const ConvTile t = choose_conv_tile(g);
+  const ConvTile t = choose_conv_tile(g, kind);
   TcParams p;
   memset(&p, 0, sizeof p);
   const int CL = s.cluster;
@@ -1024,16 +1045,23 @@ nk_status tc_conv(const TcConv& c, const nk_schedule& s, void* ws, size_t ws_byt
   p.relu = c.relu;
   p.beta = c.beta;
   p.alpha = 1.f;
+  p.scale_a = c.scale_i;   // E4M3: alpha = 1 / (s_i * s_w), read on the device
+  p.scale_b = c.scale_w;
   p.budget = wait_budget();
   p.c_vec = ((reinterpret_cast<uintptr_t>(c.O) & 15) == 0 && c.F % 4 == 0 &&
              (splits == 1 || (reinterpret_cast<uintptr_t>(ws) & 15) == 0)) ? 1 : 0;
-  const int smem = smem_of(TC_BF16, s);
+  const int smem = smem_of(kind, s);
   if (smem > kMaxSmem) return fail(NK_ERR_NO_SCHEDULE, "conv schedule needs %d bytes of shared memory", smem);
-  int grid = sms * ctas_per_sm(TC_BF16, s);
+  int grid = sms * ctas_per_sm(kind, s);
   grid = grid / CL * CL;
   if (grid > p.units * CL) grid = p.units * CL;
   if (grid < CL) grid = CL;
-  if (mch == 2) status = launch<TC_BF16, 1, false, true, false, false, 2>(p, grid, smem, st);
+  if (kind == TC_FP8) {
+    if (mch == 2) status = launch<TC_FP8, 1, false, true, false, false, 2>(p, grid, smem, st);
+    else if (mch == 4) status = launch<TC_FP8, 1, false, true, false, false, 4>(p, grid, smem, st);
+    else if (CL == 2) status = launch<TC_FP8, 2, false, true>(p, grid, smem, st);
+    else status = launch<TC_FP8, 1, false, true>(p, grid, smem, st);
+  } else if (mch == 2) status = launch<TC_BF16, 1, false, true, false, false, 2>(p, grid, smem, st);
   else if (mch == 4) status = launch<TC_BF16, 1, false, true, false, false, 4>(p, grid, smem, st);
   else if (s.tile_m == 256) status = launch<TC_BF16, 2, false, true, true>(p, grid, smem, st);
   else if (CL == 2) status = launch<TC_BF16, 2, false, true>(p, grid, smem, st);
@@ -1051,6 +1079,8 @@ nk_status tc_conv(const TcConv& c, const nk_schedule& s, void* ws, size_t ws_byt
   r.alpha = 1.f;
   r.beta = c.beta;
   r.relu = c.relu;
+  r.scale_a = c.scale_i;
+  r.scale_b = c.scale_w;
   return splitk_reduce(r, st);
 }
 

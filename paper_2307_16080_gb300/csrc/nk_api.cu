@@ -437,13 +437,17 @@ static nk_status plan_conv(const nk_tensor* I, const nk_tensor* W, const nk_tens
 // [F][taps][Cp], then the split-K partials.
 struct ConvPlan {
   nk_schedule sched{};
-  int Cp = 0;
+  int kind = TC_BF16;     // TC_BF16 or TC_FP8 operands
+  int Cp = 0;             // channels per row of a converted operand (16-byte rows)
   bool cast_i = false, cast_w = false;
-  size_t off_i = 0, off_w = 0, off_k = 0, kern = 0, total = 0;
+  size_t off_i = 0, off_w = 0, off_scal = 0, off_amax = 0, off_k = 0, kern = 0, total = 0;
 };
 
 static nk_status plan_tc_conv(const nk_tensor* I, const nk_tensor* W, const nk_tensor* O, const ConvGeom& g,
-                              const nk_schedule* user, ConvPlan& P) {
+                              int precision, const nk_schedule* user, ConvPlan& P) {
+  P.kind = precision == NK_PREC_FP8 ? TC_FP8 : TC_BF16;
+  if (P.kind == TC_FP8 && (I->dtype != NK_F32 || W->dtype != NK_F32))
+    return fail(NK_ERR_UNSUPPORTED, "an E4M3 convolution takes FP32 I and W (quantised with per-tensor scales)");
   if (W->dtype == NK_BF16 && (reinterpret_cast<uintptr_t>(W->ptr) & 15))
     return fail(NK_ERR_MISALIGNED, "packed BF16 weights must be 16-byte aligned");
   int sms = 152, dev = 0, v = 0;
@@ -453,7 +457,7 @@ static nk_status plan_tc_conv(const nk_tensor* I, const nk_tensor* W, const nk_t
   const int F = (int)W->shape[3];
   nk_schedule S = user ? *user : nk_schedule{0, 0, 0, 0, 0, 0};
   if (!S.tile_m || !S.tile_n || !S.tile_k || !S.cluster || !S.stages || !S.split_k) {
-    const nk_schedule d = tc_conv_default_schedule(g, F, sms);
+    const nk_schedule d = tc_conv_default_schedule(g, F, sms, P.kind);
     if (S.tile_m == 0) S.tile_m = d.tile_m;
     if (S.tile_n == 0) S.tile_n = d.tile_n;
     if (S.tile_k == 0) S.tile_k = d.tile_k;
@@ -461,32 +465,42 @@ static nk_status plan_tc_conv(const nk_tensor* I, const nk_tensor* W, const nk_t
     if (S.stages == 0) S.stages = d.stages;
     if (S.split_k == 0) S.split_k = d.split_k;
   }
-  if (!tc_conv_schedule_valid(g, F, S)) return fail(NK_ERR_NO_SCHEDULE, "illegal conv schedule");
+  if (!tc_conv_schedule_valid(g, F, S, P.kind)) return fail(NK_ERR_NO_SCHEDULE, "illegal conv schedule");
   P.sched = S;
-  P.Cp = (g.c + 7) / 8 * 8;
+  const int esz = P.kind == TC_FP8 ? 1 : 2;
+  const int per16 = 16 / esz;   // elements per 16-byte step
+  P.Cp = (g.c + per16 - 1) / per16 * per16;
   P.cast_i = I->dtype == NK_F32;
   if (P.cast_i && !(g.sin_w == g.c && g.sin_h == (int64_t)g.w * g.c && g.sin_n == (int64_t)g.h * g.w * g.c))
-    return fail(NK_ERR_UNSUPPORTED, "an FP32 conv input must be contiguous NHWC for the BF16 path");
+    return fail(NK_ERR_UNSUPPORTED, "an FP32 conv input must be contiguous NHWC for the tensor-core path");
   size_t off = 0;
-  if (P.cast_i) { P.off_i = off; off += align_up((size_t)g.n * g.h * g.w * P.Cp * 2); }
+  if (P.cast_i) { P.off_i = off; off += align_up((size_t)g.n * g.h * g.w * P.Cp * esz); }
   P.cast_w = W->dtype == NK_F32;
-  if (P.cast_w) { P.off_w = off; off += align_up((size_t)F * g.kh * g.kw * P.Cp * 2); }
+  if (P.cast_w) { P.off_w = off; off += align_up((size_t)F * g.kh * g.kw * P.Cp * esz); }
+  if (P.kind == TC_FP8) {
+    P.off_scal = off; off += kAlign;                      // amax_i, amax_w, s_i, s_w
+    P.off_amax = off; off += align_up(prep_amax_ws(0));
+  }
   TcConv c{};
-  c.g = g; c.F = F;
+  c.kind = P.kind; c.g = g; c.F = F;
   P.kern = tc_conv_ws(c, S);
   P.off_k = off; off += align_up(P.kern);
   P.total = off;
   return NK_OK;
 }
 
-// FP32 HWCF weights [taps*C, F] -> BF16 [F][taps][ldw] (ldw >= C, a
-// multiple of 8): one transposing cast when ldw == C, else one per tap.
-static nk_status pack_weights(const float* Wf, int taps, int C, int F, int64_t ldw, void* out, cudaStream_t st) {
+// FP32 HWCF weights [taps*C, F] -> [F][taps][ldw] (ldw >= C with 16-byte
+// rows): one transposing cast when ldw == C, else one per tap.  ck: 0 BF16,
+// 1 E4M3 scaled by 448 / *amax (the scale written to *scale_out).
+static nk_status pack_weights(int ck, const float* Wf, int taps, int C, int F, int64_t ldw, void* out,
+                              const float* amax, float* scale_out, cudaStream_t st) {
   char* wt = static_cast<char*>(out);
-  if (ldw == C) return prep_cast(0, Wf, (int64_t)taps * C, F, F, nullptr, wt, nullptr, (int64_t)taps * C, 1, nullptr, st);
+  const int esz = ck == 1 ? 1 : 2;
+  if (ldw == C)
+    return prep_cast(ck, Wf, (int64_t)taps * C, F, F, amax, wt, nullptr, (int64_t)taps * C, 1, scale_out, st);
   for (int tap = 0; tap < taps; ++tap) {
-    nk_status s = prep_cast(0, Wf + (int64_t)tap * C * F, C, F, F, nullptr, wt + (size_t)tap * ldw * 2, nullptr,
-                            (int64_t)taps * ldw, 1, nullptr, st);
+    nk_status s = prep_cast(ck, Wf + (int64_t)tap * C * F, C, F, F, amax, wt + (size_t)tap * ldw * esz, nullptr,
+                            (int64_t)taps * ldw, 1, scale_out, st);
     if (s != NK_OK) return s;
   }
   return NK_OK;
@@ -506,9 +520,9 @@ nk_status nk_conv2d_workspace_size(const nk_tensor* I, const nk_tensor* W, const
   nk_status s = plan_conv(I, W, O, stride, dilation, pad, g);
   if (s != NK_OK) return s;
   const int M = g.n * g.oh * g.ow, N = (int)W->shape[3];
-  if (precision == NK_PREC_BF16) {
+  if (precision == NK_PREC_BF16 || precision == NK_PREC_FP8) {
     ConvPlan P;
-    if ((s = plan_tc_conv(I, W, O, g, sched, P)) != NK_OK) return s;
+    if ((s = plan_tc_conv(I, W, O, g, precision, sched, P)) != NK_OK) return s;
     *bytes = P.total;
     return NK_OK;
   }
@@ -529,20 +543,35 @@ nk_status nk_conv2d_nhwc_hwcf(const nk_tensor* I, const nk_tensor* W, nk_tensor*
   const nk_epilogue e0{nullptr, 0, 0, 1.f, 1.f};
   const nk_epilogue& E = epi ? *epi : e0;
   if (!o_dense(O)) return fail(NK_ERR_UNSUPPORTED, "O must be contiguous NHWC");
-  if (precision == NK_PREC_BF16) {
+  if (precision == NK_PREC_BF16 || precision == NK_PREC_FP8) {
     ConvPlan P;
-    if ((s = plan_tc_conv(I, W, O, g, sched, P)) != NK_OK) return s;
+    if ((s = plan_tc_conv(I, W, O, g, precision, sched, P)) != NK_OK) return s;
     if (P.total > 0 && (!ws || ws_bytes < P.total))
       return fail(NK_ERR_WORKSPACE, "conv needs %zu bytes of workspace (got %zu)", P.total, ws_bytes);
     if (ws && !aligned16(ws)) return fail(NK_ERR_MISALIGNED, "workspace must be 16-byte aligned");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     char* w = static_cast<char*>(ws);
     const int F = (int)W->shape[3], taps = g.kh * g.kw;
+    const int ck = P.kind == TC_FP8 ? 1 : 0;
     TcConv c{};
-    c.g = g; c.F = F;
+    c.kind = P.kind; c.g = g; c.F = F;
+    // E4M3: per-tensor amax of I and W, then s = 448 / amax in the casts
+    float* scal = P.kind == TC_FP8 ? reinterpret_cast<float*>(w + P.off_scal) : nullptr;
+    if (P.kind == TC_FP8) {
+      void* aw = w + P.off_amax;
+      const size_t awb = prep_amax_ws(0);
+      if ((s = prep_amax(static_cast<const float*>(I->ptr), (int64_t)g.n * g.h * g.w, g.c, g.c, scal + 0, aw, awb,
+                         st)) != NK_OK)
+        return s;
+      if ((s = prep_amax(static_cast<const float*>(W->ptr), (int64_t)taps * g.c, F, F, scal + 1, aw, awb, st)) !=
+          NK_OK)
+        return s;
+      c.scale_i = scal + 2;
+      c.scale_w = scal + 3;
+    }
     if (P.cast_i) {
-      s = prep_cast(0, static_cast<const float*>(I->ptr), (int64_t)g.n * g.h * g.w, g.c, g.c, nullptr,
-                    w + P.off_i, nullptr, P.Cp, 0, nullptr, st);
+      s = prep_cast(ck, static_cast<const float*>(I->ptr), (int64_t)g.n * g.h * g.w, g.c, g.c,
+                    scal ? scal + 0 : nullptr, w + P.off_i, nullptr, P.Cp, 0, scal ? scal + 2 : nullptr, st);
       if (s != NK_OK) return s;
       c.I = w + P.off_i;
       c.sI_w = P.Cp; c.sI_h = (int64_t)g.w * P.Cp; c.sI_n = (int64_t)g.h * g.w * P.Cp;
@@ -552,7 +581,8 @@ nk_status nk_conv2d_nhwc_hwcf(const nk_tensor* I, const nk_tensor* W, nk_tensor*
     }
     if (P.cast_w) {
       char* wt = w + P.off_w;
-      if ((s = pack_weights(static_cast<const float*>(W->ptr), g.kh * g.kw, g.c, F, P.Cp, wt, st)) != NK_OK)
+      if ((s = pack_weights(ck, static_cast<const float*>(W->ptr), g.kh * g.kw, g.c, F, P.Cp, wt,
+                            scal ? scal + 1 : nullptr, scal ? scal + 3 : nullptr, st)) != NK_OK)
         return s;
       c.Wt = wt;
       c.ldw = P.Cp;
@@ -597,8 +627,8 @@ nk_status nk_conv2d_pack_weights(const nk_tensor* W, void* Wp, int64_t ldw, void
   if (!aligned16(Wp)) return fail(NK_ERR_MISALIGNED, "Wp must be 16-byte aligned");
   nk_status s = require_device();
   if (s != NK_OK) return s;
-  return pack_weights(static_cast<const float*>(W->ptr), (int)(W->shape[0] * W->shape[1]), (int)W->shape[2],
-                      (int)W->shape[3], ldw, Wp, static_cast<cudaStream_t>(stream));
+  return pack_weights(0, static_cast<const float*>(W->ptr), (int)(W->shape[0] * W->shape[1]), (int)W->shape[2],
+                      (int)W->shape[3], ldw, Wp, nullptr, nullptr, static_cast<cudaStream_t>(stream));
 }
 
 // ------------------------------------------------------------- operand prep

@@ -138,12 +138,15 @@ struct TcGemm {
 nk_status tc_gemm(const TcGemm& g, const nk_schedule& s, void* ws, size_t ws_bytes,
                   cudaStream_t st);
 
-// Implicit-GEMM convolution on the tensor cores (BF16 operands).
-// I: NHWC BF16 with channel stride 1 and element strides sI_n, sI_h, sI_w
-// (16-byte multiples); Wt: BF16, filter f / tap t / channel c at
-// f*sW_f + t*ldw + c (K-major per filter tap; ldw, sW_f multiples of 8);
-// O: FP32 [N*OH*OW, F] row-major.
+// Implicit-GEMM convolution on the tensor cores, BF16 or E4M3 operands
+// (kind TC_BF16 / TC_FP8).  I: NHWC with channel stride 1 and element
+// strides sI_n, sI_h, sI_w (16-byte multiples); Wt: filter f / tap t /
+// channel c at f*sW_f + t*ldw + c (K-major per filter tap; ldw, sW_f 16-byte
+// multiples); O: FP32 [N*OH*OW, F] row-major.  E4M3: scale_i, scale_w are
+// the device scalars s_i, s_w the operands were quantised with (the epilogue
+// multiplies by 1/(s_i*s_w)); null for BF16.
 struct TcConv {
+  int kind;
   const void* I;
   int64_t sI_n, sI_h, sI_w;
   const void* Wt;
@@ -155,12 +158,14 @@ struct TcConv {
   const float* bias;
   int relu;
   float beta;
+  const float* scale_i;
+  const float* scale_w;
 };
 // tc_conv dispatches a window schedule (see below) to tc_halo_conv.
 nk_status tc_conv(const TcConv& c, const nk_schedule& s, void* ws, size_t ws_bytes, cudaStream_t st);
 size_t tc_conv_ws(const TcConv& c, const nk_schedule& s);
-nk_schedule tc_conv_default_schedule(const ConvGeom& g, int F, int sms);
-bool tc_conv_schedule_valid(const ConvGeom& g, int F, const nk_schedule& s);
+nk_schedule tc_conv_default_schedule(const ConvGeom& g, int F, int sms, int kind = TC_BF16);
+bool tc_conv_schedule_valid(const ConvGeom& g, int F, const nk_schedule& s, int kind = TC_BF16);
 
 // Stride-1 convolution from one shared input window per tile (k_tc_halo.cu).
 // A conv schedule with tile_k = 64 * KH * KW (one pipeline stage = one

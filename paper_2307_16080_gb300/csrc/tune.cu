@@ -77,7 +77,8 @@ nk_status check_problem(const nk_problem* p) {
     if (p->n < 1 || p->h < 1 || p->w < 1 || p->c < 1 || p->f < 1 || p->kh < 1 || p->kw < 1 || p->stride < 1 ||
         p->pad < 0)
       return fail(NK_ERR_INVALID_ARG, "conv extents must be positive");
-    if (p->precision != NK_PREC_BF16) return fail(NK_ERR_UNSUPPORTED, "conv tuning covers BF16");
+    if (p->precision != NK_PREC_BF16 && p->precision != NK_PREC_FP8)
+      return fail(NK_ERR_UNSUPPORTED, "conv tuning covers BF16 and FP8");
     if ((p->h + 2 * p->pad - p->kh) / p->stride + 1 < 1 || (p->w + 2 * p->pad - p->kw) / p->stride + 1 < 1)
       return fail(NK_ERR_INVALID_ARG, "empty conv output");
     return NK_OK;
@@ -112,7 +113,7 @@ std::vector<nk_schedule> enumerate(const nk_problem* p) {
   int64_t M, N, K;
   gemm_view(p, M, N, K);
   const int tk = kind == TC_FP8 ? 128 : 64;
-  const int64_t nkb = p->op == NK_OP_CONV2D ? (int64_t)p->kh * p->kw * ((p->c + 63) / 64) : (K + tk - 1) / tk;
+  const int64_t nkb = p->op == NK_OP_CONV2D ? (int64_t)p->kh * p->kw * ((p->c + tk - 1) / tk) : (K + tk - 1) / tk;
   for (int tm : {128, 256, 512})
   for (int tn : {64, 128, 256, 512})
     for (int cl : {1, 2})
@@ -120,13 +121,13 @@ std::vector<nk_schedule> enumerate(const nk_problem* p) {
         for (int st = 2; st <= 8; ++st) {
           nk_schedule s{tm, tn, tk, cl, st, split};
           if (split > nkb) continue;
-          if (p->op == NK_OP_CONV2D ? !tc_conv_schedule_valid(geom_of(p), p->f, s)
+          if (p->op == NK_OP_CONV2D ? !tc_conv_schedule_valid(geom_of(p), p->f, s, kind)
                                     : !tc_schedule_valid(kind, s, (int)M, (int)N, (int)K))
             continue;
           out.push_back(s);
         }
   // stride-1 convolutions: the shared-window kernel (tile_k = 64 * taps)
-  if (p->op == NK_OP_CONV2D && p->kh * p->kw > 1 && p->stride == 1) {
+  if (p->op == NK_OP_CONV2D && p->kh * p->kw > 1 && p->stride == 1 && kind == TC_BF16) {
     const ConvGeom g = geom_of(p);
     for (int tm : {128, 256, 512})
       for (int tn : {64, 128, 256})
@@ -139,7 +140,7 @@ std::vector<nk_schedule> enumerate(const nk_problem* p) {
 }
 
 nk_schedule default_of(const nk_problem* p, int sms) {
-  if (p->op == NK_OP_CONV2D) return tc_conv_default_schedule(geom_of(p), p->f, sms);
+  if (p->op == NK_OP_CONV2D) return tc_conv_default_schedule(geom_of(p), p->f, sms, kind_of(p->precision));
   return tc_default_schedule(kind_of(p->precision), p->M, p->N, p->K, sms);
 }
 
@@ -197,14 +198,16 @@ struct Runner {
       g.kind = kind; g.M = (int)M; g.N = (int)N; g.K = (int)K;
       g.lda = ld; g.ldb = ld; g.ldc = N; g.alpha = 1.f;
     } else {
+      const int kind = kind_of(p->precision);
+      const int esz = kind == TC_FP8 ? 1 : 2;
       const ConvGeom geo = geom_of(p);
-      const int64_t cp = (p->c + 7) / 8 * 8;
-      const size_t ib = (size_t)p->n * p->h * p->w * cp * 2;
-      const size_t wb = (size_t)p->f * p->kh * p->kw * cp * 2;
+      const int64_t cp = (p->c + 16 / esz - 1) / (16 / esz) * (16 / esz);
+      const size_t ib = (size_t)p->n * p->h * p->w * cp * esz;
+      const size_t wb = (size_t)p->f * p->kh * p->kw * cp * esz;
       op_bytes = ib + wb;
       total = op_bytes + (size_t)M * N * 4 + split_bytes + 4096;
-      c.g = geo; c.F = p->f; c.ldw = cp; c.sW_f = (int64_t)p->kh * p->kw * cp;
-      c.sI_w = geo.sin_w; c.sI_h = geo.sin_h; c.sI_n = geo.sin_n;
+      c.kind = kind; c.g = geo; c.F = p->f; c.ldw = cp; c.sW_f = (int64_t)p->kh * p->kw * cp;
+      c.sI_w = cp; c.sI_h = (int64_t)p->w * cp; c.sI_n = (int64_t)p->h * p->w * cp;
     }
   }
   void bind(char* b) {
@@ -217,10 +220,11 @@ struct Runner {
       if (g.kind == TC_BF16X3) { g.A2 = b + a + bb; g.B2 = b + 2 * a + bb; }
       g.C = reinterpret_cast<float*>(b + (g.kind == TC_BF16X3 ? 2 : 1) * (a + bb));
     } else {
-      const size_t ib = al((size_t)p->n * p->h * p->w * c.ldw * 2);
+      const int esz = c.kind == TC_FP8 ? 1 : 2;
+      const size_t ib = al((size_t)p->n * p->h * p->w * c.ldw * esz);
       c.I = b;
       c.Wt = b + ib;
-      c.O = reinterpret_cast<float*>(b + ib + al((size_t)p->f * p->kh * p->kw * c.ldw * 2));
+      c.O = reinterpret_cast<float*>(b + ib + al((size_t)p->f * p->kh * p->kw * c.ldw * esz));
     }
   }
   size_t padded_total() const { return total + 4 * 256; }

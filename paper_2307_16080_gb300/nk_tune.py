@@ -63,8 +63,8 @@ def matmul_problem(M, N, K, precision="bf16") -> nk_problem:
     return nk_problem(NK_OP_MATMUL, nk.PREC[precision], M, N, K, 0, 0, 0, 0, 0, 0, 0, 0, 0)
 
 
-def conv_problem(n, h, w, c, f, kh, kw, stride, pad) -> nk_problem:
-    return nk_problem(NK_OP_CONV2D, nk.PREC["bf16"], 0, 0, 0, n, h, w, c, f, kh, kw, stride, pad)
+def conv_problem(n, h, w, c, f, kh, kw, stride, pad, precision="bf16") -> nk_problem:
+    return nk_problem(NK_OP_CONV2D, nk.PREC[precision], 0, 0, 0, n, h, w, c, f, kh, kw, stride, pad)
 
 
 def nk_enumerate_schedules(p: nk_problem):

@@ -188,3 +188,66 @@ def test_bf16_conv_rejects_unpacked_bf16_weights(nk):
     with pytest.raises(nk.NkError):
         nk.nk_conv2d_nhwc_hwcf(dev(I).to(torch.bfloat16), dev(W).to(torch.bfloat16), out, pad=(1, 1, 1, 1),
                                precision="bf16")
+
+
+def _half_ints(seed, stream, shape, edge):
+    """Half-integers in [-2, 2] with one entry = edge (|edge| = 3.5 = amax):
+    the E4M3 scale 448 / 3.5 = 128 is exact and every value x*128 is an
+    E4M3 code, so the quantised convolution is exact."""
+    x = synth.small_ints(seed, stream, shape) / 2
+    x.flat[0] = edge
+    return x
+
+
+FP8_CASES = [
+    # N, H, W, C, F, KH, KW, stride, dilation, pad
+    (1, 8, 8, 64, 64, 3, 3, (1, 1), (1, 1), (1, 1, 1, 1)),
+    (2, 13, 11, 20, 24, 3, 3, (2, 1), (1, 2), (1, 0, 2, 1)),     # C = 20: rows padded to 32 bytes
+    (2, 9, 9, 200, 72, 3, 3, (2, 2), (1, 1), (1, 1, 1, 1)),     # two 128-channel K blocks per tap
+    (3, 7, 7, 128, 96, 1, 1, (1, 1), (1, 1), (0, 0, 0, 0)),
+]
+
+
+@pytest.mark.parametrize("case", FP8_CASES)
+@pytest.mark.parametrize("sched", [None, (128, 64, 128, 1, 3, 1), (128, 128, 128, 2, 3, 1), (256, 64, 128, 1, 3, 1),
+                                   (512, 64, 128, 1, 2, 1), (128, 128, 128, 1, 3, 3)])
+def test_fp8_conv_exact_codes_bitwise(nk, case, sched):
+    """E4M3 convolution with per-tensor amax scales (s_i, s_w), dequantised by
+    1/(s_i*s_w) in the epilogue; on exactly representable inputs it equals
+    the FP64 oracle bit for bit."""
+    N, H, Wd, C, F, KH, KW, st, dl, pad = case
+    I = _half_ints(97, H * 100 + C, (N, H, Wd, C), 3.5)
+    W = _half_ints(97, F * 100 + KH, (KH, KW, C, F), -3.5)
+    OH = O.conv_out_size(H, KH, st[0], dl[0], pad[0], pad[1])
+    OW = O.conv_out_size(Wd, KW, st[1], dl[1], pad[2], pad[3])
+    out = torch.empty(N, OH, OW, F, device=DEV)
+    nk.nk_conv2d_nhwc_hwcf(dev(I), dev(W), out, stride=st, dilation=dl, pad=pad, precision="fp8", schedule=sched)
+    nk.nk_sync_status()
+    np.testing.assert_array_equal(host(out), O.conv2d_nhwc_hwcf(I, W, st, dl, pad))
+
+
+def test_fp8_conv_resnet_block_tolerance(nk):
+    """The FP32 conv config in E4M3: within 6e-2 of the FP32 result, and
+    within 1e-5 of the exact convolution of the dequantised E4M3 operands."""
+    I, W, bias = synth.conv_resnet_block()
+    out = torch.empty(8, 56, 56, 64, device=DEV)
+    nk.nk_conv2d_nhwc_hwcf(dev(I), dev(W), out, pad=(1, 1, 1, 1), precision="fp8", bias=dev(bias), relu=True)
+    nk.nk_sync_status()
+    got = host(out)
+    R32 = O.epilogue(O.conv2d_nhwc_hwcf(I, W, pad=(1, 1, 1, 1)), bias=bias, relu=True)
+    assert O.rel_frobenius(got, R32) <= 6e-2
+    si, sw = O.fp8_scale(I), O.fp8_scale(W)
+    Rq = O.conv2d_nhwc_hwcf(O.fp8_quantize(I, si), O.fp8_quantize(W, sw), pad=(1, 1, 1, 1))
+    Rq = O.epilogue(Rq / (np.float64(si) * np.float64(sw)), bias=bias, relu=True)
+    assert O.rel_frobenius(got, Rq) <= 1e-5
+
+
+def test_fp8_conv_rejects_pairs_and_bf16_input(nk):
+    I = synth.small_ints(98, 0, (1, 8, 8, 64))
+    W = synth.small_ints(98, 1, (3, 3, 64, 64))
+    out = torch.empty(1, 8, 8, 64, device=DEV)
+    with pytest.raises(nk.NkError):
+        nk.nk_conv2d_nhwc_hwcf(dev(I), dev(W), out, pad=(1, 1, 1, 1), precision="fp8",
+                               schedule=(256, 64, 128, 2, 3, 1))
+    with pytest.raises(nk.NkError):
+        nk.nk_conv2d_nhwc_hwcf(dev(I).to(torch.bfloat16), dev(W), out, pad=(1, 1, 1, 1), precision="fp8")
