@@ -55,6 +55,14 @@ nk_status nk_enumerate_schedules(const nk_problem* p, nk_schedule* out, int32_t 
 /* The built-in schedule (used when nk_matmul / nk_conv2d get sched = NULL). */
 nk_status nk_default_schedule(const nk_problem* p, nk_schedule* out);
 
+/* Workspace bytes the call for this problem needs at its precision and
+ * schedule (NULL = built-in choice), with FP32 operands as the plain case
+ * takes them: nk_matmul with A [M,K], B [K,N], C [M,N] row-major, or
+ * nk_conv2d_nhwc_hwcf with contiguous NHWC I, HWCF W and NHWC O (pad on
+ * all four sides, dilation 1).  The same number the operand-based
+ * nk_matmul_workspace_size / nk_conv2d_workspace_size return.             */
+nk_status nk_workspace_size(const nk_problem* p, const nk_schedule* sched, size_t* bytes);
+
 /* Model features of `count` schedules for one problem, host array
  * [count][NK_TUNE_FEATURES]: log2 M, N, K; is_conv; taps; stride; precision
  * one-hot (BF16, FP8, BF16x3); log2 tile_m, tile_n, tile_k; cluster; stages;

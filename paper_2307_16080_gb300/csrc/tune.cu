@@ -498,6 +498,45 @@ nk_status nk_schedule_features(const nk_problem* p, const nk_schedule* s, int32_
   return NK_OK;
 }
 
+nk_status nk_workspace_size(const nk_problem* p, const nk_schedule* sched, size_t* bytes) {
+  if (!bytes) return fail(NK_ERR_INVALID_ARG, "bytes is NULL");
+  if (!p) return fail(NK_ERR_INVALID_ARG, "problem is NULL");
+  // Descriptors only: planning reads shapes and strides, never the memory.
+  void* const dummy = reinterpret_cast<void*>(static_cast<uintptr_t>(4096));
+  auto dense = [&](nk_tensor& t, int rank, const int64_t* shape) {
+    t = nk_tensor{};
+    t.ptr = dummy;
+    t.dtype = NK_F32;
+    t.rank = rank;
+    int64_t st = 1;
+    for (int d = rank - 1; d >= 0; --d) {
+      t.shape[d] = shape[d];
+      t.stride[d] = st;
+      st *= shape[d];
+    }
+  };
+  if (p->op == NK_OP_MATMUL) {
+    if (p->M < 1 || p->N < 1 || p->K < 1) return fail(NK_ERR_INVALID_ARG, "matmul extents must be positive");
+    nk_tensor A, B, C;
+    const int64_t sa[2] = {p->M, p->K}, sb[2] = {p->K, p->N}, sc[2] = {p->M, p->N};
+    dense(A, 2, sa); dense(B, 2, sb); dense(C, 2, sc);
+    return nk_matmul_workspace_size(&A, &B, &C, p->precision, sched, bytes);
+  }
+  if (p->op == NK_OP_CONV2D) {
+    if (p->n < 1 || p->h < 1 || p->w < 1 || p->c < 1 || p->f < 1 || p->kh < 1 || p->kw < 1 || p->stride < 1 ||
+        p->pad < 0)
+      return fail(NK_ERR_INVALID_ARG, "conv extents must be positive");
+    const int64_t oh = (p->h + 2 * p->pad - p->kh) / p->stride + 1, ow = (p->w + 2 * p->pad - p->kw) / p->stride + 1;
+    if (oh < 1 || ow < 1) return fail(NK_ERR_INVALID_ARG, "empty conv output");
+    nk_tensor I, W, O;
+    const int64_t si[4] = {p->n, p->h, p->w, p->c}, sw[4] = {p->kh, p->kw, p->c, p->f}, so[4] = {p->n, oh, ow, p->f};
+    dense(I, 4, si); dense(W, 4, sw); dense(O, 4, so);
+    const int64_t stride[2] = {p->stride, p->stride}, dil[2] = {1, 1}, pad[4] = {p->pad, p->pad, p->pad, p->pad};
+    return nk_conv2d_workspace_size(&I, &W, &O, stride, dil, pad, p->precision, sched, bytes);
+  }
+  return fail(NK_ERR_INVALID_ARG, "unknown op %d", p->op);
+}
+
 nk_status nk_grouped_tune(int32_t G, const nk_gemm_group* groups, int32_t precision, int32_t reps,
                           nk_schedule* best, nk_tune_report* rep, void* stream) {
   if (!best) return fail(NK_ERR_INVALID_ARG, "best is NULL");

@@ -31,6 +31,7 @@ _PS = ctypes.POINTER(nk_schedule)
 SIGNATURES = {
     "nk_enumerate_schedules": (_I32, [_PP, _PS, _I32, ctypes.POINTER(_I32)]),
     "nk_default_schedule": (_I32, [_PP, _PS]),
+    "nk_workspace_size": (_I32, [_PP, _PS, ctypes.POINTER(_SZ)]),
     "nk_schedule_features": (_I32, [_PP, _PS, _I32, ctypes.POINTER(ctypes.c_float)]),
     "nk_time_schedule": (_I32, [_PP, _PS, _I32, ctypes.POINTER(ctypes.c_float), _P]),
     "nk_tune_release": (_I32, []),
@@ -79,6 +80,13 @@ def nk_default_schedule(p: nk_problem):
     s = nk_schedule()
     _check(lib().nk_default_schedule(ctypes.byref(p), ctypes.byref(s)))
     return s.as_tuple()
+
+
+def nk_workspace_size(p: nk_problem, schedule=None) -> int:
+    n = ctypes.c_size_t(0)
+    s = ctypes.byref(nk_schedule(*schedule)) if schedule is not None else None
+    _check(lib().nk_workspace_size(ctypes.byref(p), s, ctypes.byref(n)))
+    return n.value
 
 
 def nk_schedule_features(p: nk_problem, schedules) -> np.ndarray:

@@ -59,3 +59,21 @@ def test_no_device_means_error_not_fallback(libpath):
     sms = nk.ctypes.c_int32()
     st = nk.lib().nk_device_info(nk.ctypes.byref(sms), None, None)
     assert st == -5 and "cuda" in nk.last_error().lower() or st == -5
+
+
+def test_workspace_size_from_problem_matches_operand_form(libpath):
+    """nk_workspace_size(problem, schedule) is the operand-based query on
+    dense FP32 operands of that problem (planning only: no device needed)."""
+    import torch
+    import paper_2307_16080_gb300.nk as nk
+    import paper_2307_16080_gb300.nk_tune as nt
+    for (M, N, K, prec, sched) in [(1000, 900, 700, "bf16", None), (512, 512, 512, "fp8", (128, 128, 128, 1, 4, 4)),
+                                   (300, 200, 96, "bf16x3", None), (64, 64, 64, "f32", (64, 64, 16, 1, 2, 3))]:
+        a, b, c = torch.empty(M, K), torch.empty(K, N), torch.empty(M, N)
+        want = nk.nk_matmul_workspace_size(a, b, c, prec, sched)
+        assert nt.nk_workspace_size(nt.matmul_problem(M, N, K, prec), sched) == want
+    for (n, h, c_, f, k, s, prec) in [(8, 56, 64, 64, 3, 1, "bf16"), (2, 15, 20, 40, 3, 2, "fp8"), (1, 7, 512, 512, 1, 1, "bf16")]:
+        oh = (h + 2 * (k // 2) - k) // s + 1
+        i, w, o = torch.empty(n, h, h, c_), torch.empty(k, k, c_, f), torch.empty(n, oh, oh, f)
+        want = nk.nk_conv2d_workspace_size(i, w, o, (s, s), (1, 1), (k // 2,) * 4, prec)
+        assert nt.nk_workspace_size(nt.conv_problem(n, h, h, c_, f, k, k, s, k // 2, prec)) == want

@@ -251,3 +251,34 @@ def test_fp8_conv_rejects_pairs_and_bf16_input(nk):
                                schedule=(256, 64, 128, 2, 3, 1))
     with pytest.raises(nk.NkError):
         nk.nk_conv2d_nhwc_hwcf(dev(I).to(torch.bfloat16), dev(W), out, pad=(1, 1, 1, 1), precision="fp8")
+
+
+@pytest.mark.parametrize("case", [(2, 9, 11, 64, 40, 3, 3, (1, 1), (1, 1), (1, 1, 1, 1)),
+                                  (1, 12, 10, 24, 72, 3, 3, (2, 1), (1, 2), (0, 1, 2, 0))])
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+def test_gpu_conv_equals_gpu_gemm_on_explicit_im2col(nk, case, prec):
+    """The GPU convolution equals the GPU GEMM on an explicit im2col matrix
+    (built by the oracle's separate patch code) and the FP64 definition."""
+    N, H, Wd, C, F, KH, KW, st, dl, pad = case
+    if prec == "fp8":
+        I = _half_ints(99, H + C, (N, H, Wd, C), 3.5)
+        W = _half_ints(99, F + KH, (KH, KW, C, F), 3.5)
+    else:
+        I = synth.small_ints(99, H + C, (N, H, Wd, C))
+        W = synth.small_ints(99, F + KH, (KH, KW, C, F))
+    conv = _conv(nk, I, W, st, dl, pad) if prec == "bf16" else None
+    if conv is None:
+        OH = O.conv_out_size(H, KH, st[0], dl[0], pad[0], pad[1])
+        OW = O.conv_out_size(Wd, KW, st[1], dl[1], pad[2], pad[3])
+        out = torch.empty(N, OH, OW, F, device=DEV)
+        nk.nk_conv2d_nhwc_hwcf(dev(I), dev(W), out, stride=st, dilation=dl, pad=pad, precision="fp8")
+        nk.nk_sync_status()
+        conv = host(out)
+    P = O.im2col(I, KH, KW, st, dl, pad).astype(np.float32)
+    Wm = W.reshape(KH * KW * C, F)
+    c = torch.empty(P.shape[0], F, device=DEV)
+    nk.nk_matmul(dev(P), dev(Wm), c, precision=prec)
+    nk.nk_sync_status()
+    gemm = host(c).reshape(conv.shape)
+    np.testing.assert_array_equal(conv, gemm)
+    np.testing.assert_array_equal(conv, O.conv2d_nhwc_hwcf(I, W, st, dl, pad))
