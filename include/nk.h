@@ -149,7 +149,11 @@ typedef struct {
 typedef struct nk_grouped_plan nk_grouped_plan;
 
 /* Build a plan for G groups (host array `groups`, copied) at `precision`
- * (NK_PREC_BF16 with BF16 operands, or NK_PREC_F32 with FP32 operands).    */
+ * NK_PREC_BF16 (BF16 operands; other precisions return NK_ERR_UNSUPPORTED).
+ * sched (NULL = 128 x 128 tiles, deepest ring): tile_m 128 with cluster 1,
+ * or tile_m 256 with cluster 2 (a CTA pair computes 256 x tile_n tiles with
+ * cta_group::2 MMAs, each CTA loading half of B); tile_n 64 / 128 / 256;
+ * split_k 1.  nk_grouped_tune (nk_tune.h) picks one by timing.            */
 nk_status nk_grouped_plan_create(int32_t G, const nk_gemm_group* groups,
                                  int32_t precision, const nk_schedule* sched,
                                  nk_grouped_plan** plan);

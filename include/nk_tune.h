@@ -91,8 +91,9 @@ nk_status nk_tune(const nk_problem* p, int32_t mode, int32_t topk, const float* 
                   int32_t reps, nk_schedule* best, nk_tune_report* rep, void* stream);
 
 /* Grouped GEMM: the tile of a grouped plan (nk_grouped_plan_create) for this
- * set of groups.  Times every legal grouped schedule (tile_m 128, cluster 1,
- * split_k 1; tile_n 64 / 128 / 256; stages 2..8 within shared memory) as a
+ * set of groups.  Times every legal grouped schedule (tile_m 128 on one CTA
+ * or 256 on a CTA pair with cluster 2; tile_n 64 / 128 / 256; split_k 1;
+ * stages 2..8 within shared memory) as a
  * persistent launch on the caller's operands and returns the fastest in
  * *best (ties to the earlier candidate).  While timing, every group's C is
  * overwritten (accumulate flags are ignored); its contents afterwards are

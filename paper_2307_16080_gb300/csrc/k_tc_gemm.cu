@@ -160,7 +160,7 @@ __device__ __forceinline__ UnitView view_unit(const TcParams& p, int u, int cl, 
     }
     const GroupDesc& g = p.groups[lo];
     const int t = u - __ldg(p.tile_start + lo);
-    v.tm = t / g.tiles_n;
+    v.tm = (t / g.tiles_n) * cl + rank;   // a pair's tile: its two 128-row halves
     v.tn = t % g.tiles_n;
     v.split = 0;
     v.kb0 = 0;
@@ -1095,6 +1095,7 @@ nk_status tc_conv(const TcConv& c, const nk_schedule& s, void* ws, size_t ws_byt
 struct nk_grouped_plan {
   void* dev = nullptr;     // device table (owned when built by nk_grouped_plan_create)
   bool owned = false;
+  bool pair = false;       // 256-row tiles on CTA pairs (cta_group::2)
   int units = 0;
   int grid = 0;
   int smem = 0;
@@ -1137,8 +1138,14 @@ nk_status build_grouped(int G, const nk_gemm_group* groups, int precision, const
   if (precision != NK_PREC_BF16)
     return fail(NK_ERR_UNSUPPORTED, "grouped GEMM runs BF16 operands (NK_PREC_BF16) only");
   const nk_schedule s = grouped_schedule(user);
-  if (s.cluster != 1 || s.split_k != 1 || s.tile_m != 128 || !tc_schedule_valid(TC_BF16, s, 1, 1, 1))
-    return fail(NK_ERR_NO_SCHEDULE, "grouped schedule needs cluster 1, split_k 1 and a legal tile");
+  // tile_m 128 on one CTA, or tile_m 256 on a CTA pair (each CTA holds its
+  // 128 rows of A and half of the B tile)
+  const bool pair = s.tile_m == 256 && s.cluster == 2;
+  if (s.split_k != 1 || s.tile_n == 512 || !(pair || (s.tile_m == 128 && s.cluster == 1)) ||
+      !tc_schedule_valid(TC_BF16, s, 1, 1, 1))
+    return fail(NK_ERR_NO_SCHEDULE,
+                "grouped schedule needs split_k 1 and tile_m 128 on one CTA or 256 on a CTA pair");
+  const int rows = pair ? 2 * kBM : kBM;   // GEMM rows of one unit
   int sms = 0;
   nk_status st = require_device(&sms);
   if (st != NK_OK) return st;
@@ -1173,7 +1180,9 @@ nk_status build_grouped(int G, const nk_gemm_group* groups, int precision, const
     nk_gemm_group q = groups[order[i]];
     q.lda = ld_a(q); q.ldb = ld_b(q); q.ldc = ld_c(q);
     if ((st = make_kmajor_map(&maps[2 * i], false, q.A, q.M, q.K, q.lda, kBM)) != NK_OK) return st;
-    if ((st = make_kmajor_map(&maps[2 * i + 1], false, q.Bt, q.N, q.K, q.ldb, s.tile_n)) != NK_OK) return st;
+    if ((st = make_kmajor_map(&maps[2 * i + 1], false, q.Bt, q.N, q.K, q.ldb, pair ? s.tile_n / 2 : s.tile_n)) !=
+        NK_OK)
+      return st;
     GroupDesc& d = descs[i];
     d.M = q.M; d.N = q.N; d.K = q.K;
     d.tiles_n = (q.N + s.tile_n - 1) / s.tile_n;
@@ -1181,7 +1190,7 @@ nk_status build_grouped(int G, const nk_gemm_group* groups, int precision, const
     d.ldc = q.ldc;
     d.beta = q.accumulate ? 1.f : 0.f;
     starts[i] = (int)total;
-    total += (int64_t)((q.M + kBM - 1) / kBM) * d.tiles_n;
+    total += (int64_t)((q.M + rows - 1) / rows) * d.tiles_n;
     if (total > INT32_MAX) return fail(NK_ERR_UNSUPPORTED, "too many tiles");
     cvec = cvec && ((reinterpret_cast<uintptr_t>(q.C) & 15) == 0) && (q.ldc % 4 == 0);
   }
@@ -1201,9 +1210,12 @@ nk_status build_grouped(int G, const nk_gemm_group* groups, int precision, const
   p.groups = reinterpret_cast<const GroupDesc*>(db + off_desc);
   p.tile_start = reinterpret_cast<const int*>(db + off_start);
   plan.units = (int)total;
+  plan.pair = pair;
   plan.smem = smem_of(TC_BF16, s);
-  int grid = sms * ctas_per_sm(TC_BF16, s);
-  plan.grid = grid < plan.units ? grid : plan.units;
+  const int CL = pair ? 2 : 1;
+  int grid = sms * ctas_per_sm(TC_BF16, s) / CL * CL;
+  if (grid > plan.units * CL) grid = plan.units * CL;
+  plan.grid = grid < CL ? CL : grid;
   return NK_OK;
 }
 
@@ -1248,6 +1260,8 @@ nk_status nk_grouped_plan_create(int32_t G, const nk_gemm_group* groups, int32_t
 nk_status nk_grouped_plan_run(const nk_grouped_plan* plan, void* stream) {
   if (!plan) return fail(NK_ERR_INVALID_ARG, "plan is NULL");
   if (plan->units == 0) return NK_OK;
+  if (plan->pair)
+    return launch<TC_BF16, 2, true, false, true>(plan->p, plan->grid, plan->smem, static_cast<cudaStream_t>(stream));
   return launch<TC_BF16, 1, true>(plan->p, plan->grid, plan->smem, static_cast<cudaStream_t>(stream));
 }
 
@@ -1273,6 +1287,7 @@ nk_status nk_batch_matmul_grouped(int32_t G, const nk_gemm_group* groups, int32_
   cudaError_t e = cudaMemcpyAsync(ws, host.data(), bytes, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(grouped table)");
   // a pageable source is staged before cudaMemcpyAsync returns, so `host` may go
+  if (plan.pair) return launch<TC_BF16, 2, true, false, true>(plan.p, plan.grid, plan.smem, st);
   return launch<TC_BF16, 1, true>(plan.p, plan.grid, plan.smem, st);
 }
 

@@ -562,9 +562,10 @@ nk_status nk_grouped_tune(int32_t G, const nk_gemm_group* groups, int32_t precis
   if ((st = time_plan(nullptr, &dms)) != NK_OK) return st;
   int cands = 0, timed = 0;
   float best_ms = 0.f;
+  for (int tm : {128, 256})   // 256: CTA pairs
   for (int tn : {64, 128, 256})
     for (int stages = 2; stages <= 8; ++stages) {
-      const nk_schedule s{128, tn, 64, 1, stages, 1};
+      const nk_schedule s{tm, tn, 64, tm == 256 ? 2 : 1, stages, 1};
       nk_grouped_plan* probe = nullptr;
       nk_status r = nk_grouped_plan_create(G, gs.data(), precision, &s, &probe);
       if (r == NK_ERR_NO_SCHEDULE) continue;   // does not fit shared memory
