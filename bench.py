@@ -237,32 +237,36 @@ def sweep_report(torch, nk, dev, a32, b32, c, flop, kern_tflops):
     return out
 
 
-def e2e_report(torch, nk, dev, A, B, reps):
+def e2e_report(torch, nk, dev, A, B, reps, nbuf=2):
     """Pinned host FP32 A, B in and host FP32 C out every step through the
     public API, with uploads, compute and downloads of consecutive steps on
-    three streams (double-buffered), as a user would pipeline them."""
+    three streams (`nbuf` device buffer sets), as a user would pipeline them.
+    The host link bounds it: on the GB300 machine pinned H2D copies reach about
+    209 GB/s and D2H 192 GB/s whatever the number of streams or chunks, and
+    329 GB/s together, so a step's 805 MB takes 2.45 ms at least; three or
+    four buffer sets measure the same as two."""
     n = A.shape[0]
     a_h = torch.from_numpy(A).pin_memory()
     b_h = torch.from_numpy(B).pin_memory()
-    c_h = [torch.empty(n, n).pin_memory() for _ in range(2)]
-    a32 = [torch.empty(n, n, device=dev) for _ in range(2)]
-    b32 = [torch.empty(n, n, device=dev) for _ in range(2)]
-    cc = [torch.empty(n, n, device=dev) for _ in range(2)]
+    c_h = [torch.empty(n, n).pin_memory() for _ in range(nbuf)]
+    a32 = [torch.empty(n, n, device=dev) for _ in range(nbuf)]
+    b32 = [torch.empty(n, n, device=dev) for _ in range(nbuf)]
+    cc = [torch.empty(n, n, device=dev) for _ in range(nbuf)]
     a16 = torch.empty(n, n, dtype=torch.bfloat16, device=dev)
     bt16 = torch.empty(n, n, dtype=torch.bfloat16, device=dev)
     ws = nk.workspace(nk.nk_matmul_workspace_size(a16, bt16.t(), cc[0], "bf16"), dev)
     s_up, s_dn = torch.cuda.Stream(), torch.cuda.Stream()
     s_c = torch.cuda.current_stream()
-    comp_done = [torch.cuda.Event() for _ in range(2)]
-    down_done = [torch.cuda.Event() for _ in range(2)]
-    up_done = [torch.cuda.Event() for _ in range(2)]
-    for j in range(2):
+    comp_done = [torch.cuda.Event() for _ in range(nbuf)]
+    down_done = [torch.cuda.Event() for _ in range(nbuf)]
+    up_done = [torch.cuda.Event() for _ in range(nbuf)]
+    for j in range(nbuf):
         comp_done[j].record(s_c)
         down_done[j].record(s_c)
 
     def run(k):
         for i in range(k):
-            j = i % 2
+            j = i % nbuf
             with torch.cuda.stream(s_up):
                 s_up.wait_event(comp_done[j])
                 a32[j].copy_(a_h, non_blocking=True)
@@ -287,7 +291,7 @@ def e2e_report(torch, nk, dev, A, B, reps):
     nk.nk_sync_status()
     return {"value": 2.0 * n ** 3 / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms,
             "h2d_bytes_per_step": 2 * n * n * 4, "d2h_bytes_per_step": n * n * 4,
-            "how": "host wall clock over pipelined steps (upload / compute / download streams)"}
+            "how": f"host wall clock over pipelined steps (upload / compute / download streams, {nbuf} buffer sets)"}
 
 
 def grouped_report(torch, nk, synth, dev):
