@@ -202,6 +202,34 @@ nk_status nk_conv2d_workspace_size(const nk_tensor* I, const nk_tensor* W,
                                    const int64_t pad[4], int32_t precision,
                                    const nk_schedule* sched, size_t* bytes);
 
+/* ---------------------------------------------------- grouped convolution */
+
+/* One convolution of a grouped launch: linalg.conv_2d_nhwc_hwcf (Sec. 4.1,
+ * in NHWC/HWCF) with its epilogue ReLU?(beta*O + acc + bias[f]).
+ * I: BF16 NHWC [N,H,W,C], unit channel stride, 16-byte aligned base and
+ * rows; W: BF16 packed by nk_conv2d_pack_weights (a [KH,KW,C,F] view with
+ * strides {KW*ldw, ldw, 1, sF}); O: FP32 contiguous NHWC [N,OH,OW,F].
+ * stride / dilation / pad as for nk_conv2d_nhwc_hwcf (stride <= 8).       */
+typedef struct {
+  nk_tensor I, W, O;
+  int64_t stride[2], dilation[2], pad[4];
+  const float* bias; /* FP32 [F] device vector or NULL */
+  int32_t relu;
+  int32_t accumulate;
+} nk_conv_group;
+
+/* Plan of G independent convolutions of uneven shapes computed by one
+ * persistent launch (run with nk_grouped_plan_run, CUDA-graph replayable;
+ * free with nk_grouped_plan_destroy).  Every group's tiles (its own output
+ * tiling, input and weight tensor maps, bias, ReLU) share one grid; groups
+ * are ordered by decreasing K so the longest tiles start first.
+ * sched (NULL = 128 x 128 tiles, deepest ring): tile_m 128, tile_k 64,
+ * cluster 1, split_k 1, tile_n 64 / 128 / 256.  Allocates the plan's
+ * device table.                                                            */
+nk_status nk_conv2d_grouped_plan_create(int32_t G, const nk_conv_group* groups,
+                                        const nk_schedule* sched,
+                                        nk_grouped_plan** plan);
+
 /* Converts FP32 HWCF weights W [KH,KW,C,F] (contiguous) to the BF16 layout
  * the tensor-core convolution reads: element (kh,kw,c,f) at
  * Wp + f*(KH*KW*ldw) + (kh*KW + kw)*ldw + c, with ldw >= C a multiple of 8

@@ -108,7 +108,11 @@ struct GroupDesc {
   float* C;
   int64_t ldc;
   float beta;
+  int kblocks;            // K blocks of 64 elements (a conv: taps x channel blocks)
+  const float* bias;      // per output column, or null
+  int relu;
   int pad;
+  ConvTile cv;            // grouped convolutions: the group's output tiling
 };
 
 // One pipeline stage: mch A tiles of 128 rows (one per accumulator chain)
@@ -130,6 +134,9 @@ struct UnitView {
   float* C;
   int64_t ldc;
   float beta;
+  const float* bias;
+  int relu;
+  const ConvTile* cv;    // conv launches: the tiling of this unit's convolution
 };
 
 __device__ __forceinline__ Unit decode_unit(const TcParams& p, int u, int cl, int rank) {
@@ -164,7 +171,7 @@ __device__ __forceinline__ UnitView view_unit(const TcParams& p, int u, int cl, 
     v.tn = t % g.tiles_n;
     v.split = 0;
     v.kb0 = 0;
-    v.kb1 = (g.K + 63) / 64;
+    v.kb1 = g.kblocks;
     v.M = g.M;
     v.N = g.N;
     v.ma = p.gmaps + 2 * lo;
@@ -172,6 +179,9 @@ __device__ __forceinline__ UnitView view_unit(const TcParams& p, int u, int cl, 
     v.C = g.C;
     v.ldc = g.ldc;
     v.beta = g.beta;
+    v.bias = g.bias;
+    v.relu = g.relu;
+    v.cv = &g.cv;
   } else {
     const Unit t = decode_unit(p, u, cl, rank);
     v.tm = t.tm;
@@ -186,6 +196,9 @@ __device__ __forceinline__ UnitView view_unit(const TcParams& p, int u, int cl, 
     v.C = p.C;
     v.ldc = p.ldc;
     v.beta = p.beta;
+    v.bias = p.bias;
+    v.relu = p.relu;
+    v.cv = &p.cv;
   }
   return v;
 }
@@ -323,15 +336,15 @@ __global__ void __launch_bounds__(WIDE ? 320 : 192, 1) tc_gemm_kernel(const __gr
             const uint32_t lf = ptx::mapa(full_bar(s), 0);
             const int by = t.tn * p.bn + rank * b_rows_smem;
             if constexpr (CONV) {
-              const ConvTile& c = p.cv;
+              const ConvTile& c = *t.cv;
               if (rank == 0) ptx::mbar_arrive_expect_tx(full_bar(s), 2u * (p.a_box_bytes + (uint32_t)b_bytes));
               const int tap = kb / c.cblocks, c0 = (kb % c.cblocks) * c.cblk;
               const int kh = tap / c.KW, kw = tap % c.KW;
               const int tw = t.tm % c.tiles_w, th = (t.tm / c.tiles_w) % c.tiles_h;
               const int tb = t.tm / (c.tiles_w * c.tiles_h);
-              ptx::tma_load_4d_pair(a_smem(s, 0), &p.tmA, lf, c0, tw * c.Q * c.sw + kw * c.dw - c.pl,
+              ptx::tma_load_4d_pair(a_smem(s, 0), t.ma, lf, c0, tw * c.Q * c.sw + kw * c.dw - c.pl,
                                     th * c.R * c.sh + kh * c.dh - c.pt, tb * c.NB);
-              ptx::tma_load_3d_pair(b_smem(s, 0), &p.tmB, lf, c0, tap, by);
+              ptx::tma_load_3d_pair(b_smem(s, 0), t.mb, lf, c0, tap, by);
             } else {
               if (rank == 0) ptx::mbar_arrive_expect_tx(full_bar(s), 2u * (uint32_t)sb);
               const int kx = kb * kblk;
@@ -353,23 +366,25 @@ __global__ void __launch_bounds__(WIDE ? 320 : 192, 1) tc_gemm_kernel(const __gr
           if constexpr (CONV) {
             // K block kb = (filter tap, 64-channel block); the A box is the
             // input window that tap sees, shifted and strided by TMA.
-            const ConvTile& c = p.cv;
-            ptx::mbar_arrive_expect_tx(full_bar(s), MCH * p.a_box_bytes + (uint32_t)b_bytes);
+            const ConvTile& c = *t.cv;
+            // bytes one A box writes (a short conv tile writes fewer than 16 KB)
+            const uint32_t a_box = GROUPED ? (uint32_t)(c.Q * c.R * c.NB * kRowBytes) : p.a_box_bytes;
+            ptx::mbar_arrive_expect_tx(full_bar(s), MCH * a_box + (uint32_t)b_bytes);
             const int tap = kb / c.cblocks, c0 = (kb % c.cblocks) * c.cblk;
             const int kh = tap / c.KW, kw = tap % c.KW;
             for (int ch = 0; ch < MCH; ++ch) {
               const int ct = t.tm * MCH + ch;   // conv tile of this chain
               const int tw = ct % c.tiles_w, th = (ct / c.tiles_w) % c.tiles_h;
               const int tb = ct / (c.tiles_w * c.tiles_h);
-              ptx::tma_load_4d(a_smem(s, 0) + ch * kBM * kRowBytes, &p.tmA, full_bar(s), c0,
+              ptx::tma_load_4d(a_smem(s, 0) + ch * kBM * kRowBytes, t.ma, full_bar(s), c0,
                                tw * c.Q * c.sw + kw * c.dw - c.pl, th * c.R * c.sh + kh * c.dh - c.pt, tb * c.NB);
             }
             const int fy = t.tn * p.bn + rank * b_rows;
             if (CL == 2)
-              ptx::tma_load_3d_mc(b_smem(s, 0) + rank * b_rows * kRowBytes, &p.tmB, full_bar(s), c0, tap,
+              ptx::tma_load_3d_mc(b_smem(s, 0) + rank * b_rows * kRowBytes, t.mb, full_bar(s), c0, tap,
                                   fy, (uint16_t)0x3);
             else
-              ptx::tma_load_3d(b_smem(s, 0), &p.tmB, full_bar(s), c0, tap, fy);
+              ptx::tma_load_3d(b_smem(s, 0), t.mb, full_bar(s), c0, tap, fy);
             continue;
           }
           ptx::mbar_arrive_expect_tx(full_bar(s), (uint32_t)sb);
@@ -476,7 +491,7 @@ __global__ void __launch_bounds__(WIDE ? 320 : 192, 1) tc_gemm_kernel(const __gr
       ptx::tc_fence_after();
       for (int ch = 0; ch < MCH; ++ch) {   // chains of a tall tile (one otherwise)
       const int tmc = t.tm * MCH + ch;
-      const int row = CONV ? conv_row(p.cv, tmc, q * 32 + lane) : tmc * kBM + q * 32 + lane;
+      const int row = CONV ? conv_row(*t.cv, tmc, q * 32 + lane) : tmc * kBM + q * 32 + lane;
       const bool row_ok = CONV ? row >= 0 : row < t.M;
       // a wide tile has two warps per lane quarter, each draining one chain's 256 columns
       const int c_begin = WIDE ? ((warp - 2) / 4) * 256 : 0;
@@ -500,7 +515,7 @@ __global__ void __launch_bounds__(WIDE ? 320 : 192, 1) tc_gemm_kernel(const __gr
           const uint32_t stg = stg0 + (uint32_t)((warp - 2) * kStageBox);
           if (lane == 0) ptx::bulk_wait_read0();   // the box's previous store has read it
           __syncwarp();
-          const float bm = (p.bias && p.bias_on_m && row_ok) ? __ldg(p.bias + row) : 0.f;
+          const float bm = (t.bias && p.bias_on_m && row_ok) ? __ldg(t.bias + row) : 0.f;
 #pragma unroll
           for (int j16 = 0; j16 < 8; ++j16) {
             float o[4];
@@ -508,8 +523,8 @@ __global__ void __launch_bounds__(WIDE ? 320 : 192, 1) tc_gemm_kernel(const __gr
             for (int e = 0; e < 4; ++e) {
               const int j = 4 * j16 + e;
               float x = alpha * v[j];
-              if (p.bias) x += p.bias_on_m ? bm : (col0 + j < t.N ? __ldg(p.bias + col0 + j) : 0.f);
-              if (p.relu) x = (x > 0.f || x != x) ? x : 0.f;
+              if (t.bias) x += p.bias_on_m ? bm : (col0 + j < t.N ? __ldg(t.bias + col0 + j) : 0.f);
+              if (t.relu) x = (x > 0.f || x != x) ? x : 0.f;
               o[e] = x;
             }
             const uint32_t addr = stg + (uint32_t)(lane * 128 + ((j16 ^ (lane & 7)) * 16));
@@ -540,7 +555,7 @@ __global__ void __launch_bounds__(WIDE ? 320 : 192, 1) tc_gemm_kernel(const __gr
           continue;
         }
         float* dst = t.C + (int64_t)row * t.ldc + col0;
-        const float bm = (p.bias && p.bias_on_m) ? __ldg(p.bias + row) : 0.f;
+        const float bm = (t.bias && p.bias_on_m) ? __ldg(t.bias + row) : 0.f;
         const float beta = t.beta;
         if (p.c_vec && col0 + 32 <= t.N) {
 #pragma unroll
@@ -553,8 +568,8 @@ __global__ void __launch_bounds__(WIDE ? 320 : 192, 1) tc_gemm_kernel(const __gr
             for (int e = 0; e < 4; ++e) {
               float x = alpha * v[j + e];
               if (beta != 0.f) x = fmaf(beta, ci[e], x);
-              if (p.bias) x += p.bias_on_m ? bm : __ldg(p.bias + col0 + j + e);
-              if (p.relu) x = (x > 0.f || x != x) ? x : 0.f;
+              if (t.bias) x += p.bias_on_m ? bm : __ldg(t.bias + col0 + j + e);
+              if (t.relu) x = (x > 0.f || x != x) ? x : 0.f;
               o[e] = x;
             }
             *reinterpret_cast<float4*>(dst + j) = make_float4(o[0], o[1], o[2], o[3]);
@@ -565,8 +580,8 @@ __global__ void __launch_bounds__(WIDE ? 320 : 192, 1) tc_gemm_kernel(const __gr
             if (col0 + j >= t.N) continue;
             float x = alpha * v[j];
             if (beta != 0.f) x = fmaf(beta, dst[j], x);
-            if (p.bias) x += p.bias_on_m ? bm : __ldg(p.bias + col0 + j);
-            if (p.relu) x = (x > 0.f || x != x) ? x : 0.f;
+            if (t.bias) x += p.bias_on_m ? bm : __ldg(t.bias + col0 + j);
+            if (t.relu) x = (x > 0.f || x != x) ? x : 0.f;
             dst[j] = x;
           }
         }
@@ -916,7 +931,7 @@ ConvTile choose_conv_tile(const ConvGeom& g, int kind) {
   return t;
 }
 
-nk_status make_conv_maps(TcParams& p, const TcConv& c, const ConvTile& t, int bn_box) {
+nk_status make_conv_maps(CUtensorMap* map_a, CUtensorMap* map_b, const TcConv& c, const ConvTile& t, int bn_box) {
   auto fn = encode_fn();
   if (!fn) return fail(NK_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
   const ConvGeom& g = c.g;
@@ -928,7 +943,7 @@ nk_status make_conv_maps(TcParams& p, const TcConv& c, const ConvTile& t, int bn
     cuuint64_t strides[3] = {(cuuint64_t)c.sI_w * esz, (cuuint64_t)c.sI_h * esz, (cuuint64_t)c.sI_n * esz};
     cuuint32_t box[4] = {(cuuint32_t)t.cblk, (cuuint32_t)(t.Q * g.sw), (cuuint32_t)(t.R * g.sh), (cuuint32_t)t.NB};
     cuuint32_t es[4] = {1, (cuuint32_t)g.sw, (cuuint32_t)g.sh, 1};
-    CUresult r = fn(&p.tmA, dt, 4, const_cast<void*>(c.I), dims, strides, box,
+    CUresult r = fn(map_a, dt, 4, const_cast<void*>(c.I), dims, strides, box,
                     es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(NK_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d) for the conv input", (int)r);
@@ -939,7 +954,7 @@ nk_status make_conv_maps(TcParams& p, const TcConv& c, const ConvTile& t, int bn
     cuuint64_t strides[2] = {(cuuint64_t)c.ldw * esz, (cuuint64_t)c.sW_f * esz};
     cuuint32_t box[3] = {(cuuint32_t)t.cblk, 1, (cuuint32_t)bn_box};
     cuuint32_t es[3] = {1, 1, 1};
-    CUresult r = fn(&p.tmB, dt, 3, const_cast<void*>(c.Wt), dims, strides, box,
+    CUresult r = fn(map_b, dt, 3, const_cast<void*>(c.Wt), dims, strides, box,
                     es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(NK_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d) for the conv weights", (int)r);
@@ -1017,7 +1032,7 @@ nk_status tc_conv(const TcConv& c, const nk_schedule& s, void* ws, size_t ws_byt
   TcParams p;
   memset(&p, 0, sizeof p);
   const int CL = s.cluster;
-  if ((status = make_conv_maps(p, c, t, s.tile_n / CL)) != NK_OK) return status;
+  if ((status = make_conv_maps(&p.tmA, &p.tmB, c, t, s.tile_n / CL)) != NK_OK) return status;
   p.cv = t;
   p.a_box_bytes = (uint32_t)(t.Q * t.R * t.NB * kRowBytes);
   p.M = M; p.N = c.F; p.K = g.kh * g.kw * g.c;
@@ -1096,6 +1111,7 @@ struct nk_grouped_plan {
   void* dev = nullptr;     // device table (owned when built by nk_grouped_plan_create)
   bool owned = false;
   bool pair = false;       // 256-row tiles on CTA pairs (cta_group::2)
+  bool conv = false;       // groups are convolutions (implicit GEMM, per-tap loads)
   int units = 0;
   int grid = 0;
   int smem = 0;
@@ -1189,6 +1205,7 @@ nk_status build_grouped(int G, const nk_gemm_group* groups, int precision, const
     d.C = q.C;
     d.ldc = q.ldc;
     d.beta = q.accumulate ? 1.f : 0.f;
+    d.kblocks = (q.K + 63) / 64;
     starts[i] = (int)total;
     total += (int64_t)((q.M + rows - 1) / rows) * d.tiles_n;
     if (total > INT32_MAX) return fail(NK_ERR_UNSUPPORTED, "too many tiles");
@@ -1216,6 +1233,125 @@ nk_status build_grouped(int G, const nk_gemm_group* groups, int precision, const
   int grid = sms * ctas_per_sm(TC_BF16, s) / CL * CL;
   if (grid > plan.units * CL) grid = plan.units * CL;
   plan.grid = grid < CL ? CL : grid;
+  return NK_OK;
+}
+
+// Grouped convolutions: each group a linalg.conv_2d_nhwc_hwcf on BF16 NHWC
+// input and packed BF16 weights, with its own output tiling (ConvTile), 4-D
+// input and 3-D weight maps, bias and ReLU in the device table.
+nk_status build_grouped_conv(int G, const nk_conv_group* groups, const nk_schedule* user, void* dev_base,
+                             std::vector<uint8_t>& host, nk_grouped_plan& plan) {
+  if (G < 0) return fail(NK_ERR_INVALID_ARG, "negative group count");
+  if (G > 0 && !groups) return fail(NK_ERR_INVALID_ARG, "groups is NULL");
+  const nk_schedule s = grouped_schedule(user);
+  if (s.tile_m != 128 || s.cluster != 1 || s.split_k != 1 || s.tile_n == 512 || s.tile_k != 64 ||
+      !tc_schedule_valid(TC_BF16, s, 1, 1, 1))
+    return fail(NK_ERR_NO_SCHEDULE, "grouped conv schedule needs tile_m 128, tile_k 64, cluster 1, split_k 1");
+  int sms = 0;
+  nk_status st = require_device(&sms);
+  if (st != NK_OK) return st;
+  std::vector<TcConv> convs(G);
+  std::vector<int> kblocks(G);
+  for (int i = 0; i < G; ++i) {
+    const nk_conv_group& q = groups[i];
+    const nk_tensor &I = q.I, &W = q.W, &O = q.O;
+    if (I.rank != 4 || W.rank != 4 || O.rank != 4 || I.dtype != NK_BF16 || W.dtype != NK_BF16 || O.dtype != NK_F32)
+      return fail(NK_ERR_UNSUPPORTED, "conv group %d: BF16 NHWC I, packed BF16 W and FP32 NHWC O", i);
+    for (int d = 0; d < 2; ++d)
+      if (q.stride[d] < 1 || q.dilation[d] < 1) return fail(NK_ERR_INVALID_ARG, "conv group %d: stride, dilation", i);
+    for (int d = 0; d < 4; ++d)
+      if (q.pad[d] < 0) return fail(NK_ERR_INVALID_ARG, "conv group %d: negative padding", i);
+    ConvGeom g{};
+    g.n = (int)I.shape[0]; g.h = (int)I.shape[1]; g.w = (int)I.shape[2]; g.c = (int)I.shape[3];
+    g.kh = (int)W.shape[0]; g.kw = (int)W.shape[1];
+    g.sh = (int)q.stride[0]; g.sw = (int)q.stride[1]; g.dh = (int)q.dilation[0]; g.dw = (int)q.dilation[1];
+    g.pt = (int)q.pad[0]; g.pl = (int)q.pad[2];
+    const int64_t oh = (g.h + q.pad[0] + q.pad[1] - g.dh * (g.kh - 1) - 1) / g.sh + 1;
+    const int64_t ow = (g.w + q.pad[2] + q.pad[3] - g.dw * (g.kw - 1) - 1) / g.sw + 1;
+    if (oh < 1 || ow < 1 || g.n < 1 || g.c < 1 || W.shape[3] < 1)
+      return fail(NK_ERR_INVALID_ARG, "conv group %d: empty problem", i);
+    if (W.shape[2] != g.c) return fail(NK_ERR_INVALID_ARG, "conv group %d: I channels != W channels", i);
+    if (O.shape[0] != g.n || O.shape[1] != oh || O.shape[2] != ow || O.shape[3] != W.shape[3])
+      return fail(NK_ERR_INVALID_ARG, "conv group %d: O must be [%d,%lld,%lld,%lld]", i, g.n, (long long)oh,
+                  (long long)ow, (long long)W.shape[3]);
+    if (g.sh > 8 || g.sw > 8) return fail(NK_ERR_UNSUPPORTED, "conv group %d: stride above 8", i);
+    g.oh = (int)oh; g.ow = (int)ow;
+    g.sin_n = I.stride[0]; g.sin_h = I.stride[1]; g.sin_w = I.stride[2];
+    const int64_t ldw = W.stride[1], sF = W.stride[3];
+    if (I.stride[3] != 1 || W.stride[2] != 1 || ldw < g.c || ldw % 8 || W.stride[0] != W.shape[1] * ldw ||
+        sF % 8 || sF < W.shape[0] * W.shape[1] * ldw)
+      return fail(NK_ERR_UNSUPPORTED, "conv group %d: I needs unit channel stride, W the packed layout", i);
+    if (O.stride[3] != 1 || O.stride[2] != O.shape[3] || O.stride[1] != O.shape[2] * O.stride[2] ||
+        O.stride[0] != O.shape[1] * O.stride[1])
+      return fail(NK_ERR_UNSUPPORTED, "conv group %d: O must be contiguous NHWC", i);
+    if ((g.sin_w * 2) % 16 || (g.sin_h * 2) % 16 || (g.sin_n * 2) % 16 ||
+        (reinterpret_cast<uintptr_t>(I.ptr) & 15) || (reinterpret_cast<uintptr_t>(W.ptr) & 15))
+      return fail(NK_ERR_MISALIGNED, "conv group %d: operands need 16-byte aligned bases and rows", i);
+    if ((int64_t)g.n * g.oh * g.ow > INT32_MAX) return fail(NK_ERR_UNSUPPORTED, "conv group %d: too large", i);
+    TcConv& c = convs[i];
+    c.kind = TC_BF16;
+    c.I = I.ptr; c.sI_n = g.sin_n; c.sI_h = g.sin_h; c.sI_w = g.sin_w;
+    c.Wt = W.ptr; c.ldw = ldw; c.sW_f = sF;
+    c.g = g;
+    c.F = (int)W.shape[3];
+    c.O = static_cast<float*>(O.ptr);
+    kblocks[i] = g.kh * g.kw * ((g.c + 63) / 64);
+  }
+  std::vector<int> order(G);
+  for (int g = 0; g < G; ++g) order[g] = g;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return kblocks[a] > kblocks[b]; });
+  host.assign(grouped_bytes(G), 0);
+  CUtensorMap* maps = reinterpret_cast<CUtensorMap*>(host.data());
+  const size_t off_desc = (size_t)G * 2 * sizeof(CUtensorMap);
+  const size_t off_start = off_desc + ((size_t)G * sizeof(GroupDesc) + 127) / 128 * 128;
+  GroupDesc* descs = reinterpret_cast<GroupDesc*>(host.data() + off_desc);
+  int* starts = reinterpret_cast<int*>(host.data() + off_start);
+  bool cvec = true;
+  int64_t total = 0;
+  for (int i = 0; i < G; ++i) {
+    const int gi = order[i];
+    const TcConv& c = convs[gi];
+    const ConvTile t = choose_conv_tile(c.g, TC_BF16);
+    if ((st = make_conv_maps(&maps[2 * i], &maps[2 * i + 1], c, t, s.tile_n)) != NK_OK) return st;
+    GroupDesc& d = descs[i];
+    d.M = c.g.n * c.g.oh * c.g.ow;
+    d.N = c.F;
+    d.K = c.g.kh * c.g.kw * c.g.c;
+    d.tiles_n = (c.F + s.tile_n - 1) / s.tile_n;
+    d.C = c.O;
+    d.ldc = c.F;
+    d.beta = groups[gi].accumulate ? 1.f : 0.f;
+    d.kblocks = kblocks[gi];
+    d.bias = groups[gi].bias;
+    d.relu = groups[gi].relu;
+    d.cv = t;
+    starts[i] = (int)total;
+    total += (int64_t)t.tiles_w * t.tiles_h * ((c.g.n + t.NB - 1) / t.NB) * d.tiles_n;
+    if (total > INT32_MAX) return fail(NK_ERR_UNSUPPORTED, "too many tiles");
+    cvec = cvec && ((reinterpret_cast<uintptr_t>(c.O) & 15) == 0) && (c.F % 4 == 0);
+  }
+  starts[G] = (int)total;
+  TcParams& p = plan.p;
+  memset(&p, 0, sizeof p);
+  p.bn = s.tile_n;
+  p.stages = s.stages;
+  p.units = (int)total;
+  p.splits = 1;
+  p.alpha = 1.f;
+  p.budget = wait_budget();
+  p.c_vec = cvec ? 1 : 0;
+  p.G = G;
+  uint8_t* db = static_cast<uint8_t*>(dev_base);
+  p.gmaps = reinterpret_cast<const CUtensorMap*>(db);
+  p.groups = reinterpret_cast<const GroupDesc*>(db + off_desc);
+  p.tile_start = reinterpret_cast<const int*>(db + off_start);
+  plan.units = (int)total;
+  plan.pair = false;
+  plan.conv = true;
+  plan.smem = smem_of(TC_BF16, s);
+  int grid = sms * ctas_per_sm(TC_BF16, s);
+  if (grid > plan.units) grid = plan.units;
+  plan.grid = grid < 1 ? 1 : grid;
   return NK_OK;
 }
 
@@ -1257,9 +1393,33 @@ nk_status nk_grouped_plan_create(int32_t G, const nk_gemm_group* groups, int32_t
   return NK_OK;
 }
 
+nk_status nk_conv2d_grouped_plan_create(int32_t G, const nk_conv_group* groups, const nk_schedule* sched,
+                                        nk_grouped_plan** out) {
+  if (!out) return fail(NK_ERR_INVALID_ARG, "plan is NULL");
+  *out = nullptr;
+  auto* plan = new nk_grouped_plan();
+  void* dev = nullptr;
+  const size_t bytes = grouped_bytes(G);
+  cudaError_t e = cudaMalloc(&dev, bytes > 0 ? bytes : 1);
+  if (e != cudaSuccess) { delete plan; return cuda_fail(e, "cudaMalloc(grouped conv plan)"); }
+  std::vector<uint8_t> host;
+  nk_status s = build_grouped_conv(G, groups, sched, dev, host, *plan);
+  if (s == NK_OK && bytes) {
+    e = cudaMemcpy(dev, host.data(), bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) s = cuda_fail(e, "cudaMemcpy(grouped conv plan)");
+  }
+  if (s != NK_OK) { cudaFree(dev); delete plan; return s; }
+  plan->dev = dev;
+  plan->owned = true;
+  *out = plan;
+  return NK_OK;
+}
+
 nk_status nk_grouped_plan_run(const nk_grouped_plan* plan, void* stream) {
   if (!plan) return fail(NK_ERR_INVALID_ARG, "plan is NULL");
   if (plan->units == 0) return NK_OK;
+  if (plan->conv)
+    return launch<TC_BF16, 1, true, true>(plan->p, plan->grid, plan->smem, static_cast<cudaStream_t>(stream));
   if (plan->pair)
     return launch<TC_BF16, 2, true, false, true>(plan->p, plan->grid, plan->smem, static_cast<cudaStream_t>(stream));
   return launch<TC_BF16, 1, true>(plan->p, plan->grid, plan->smem, static_cast<cudaStream_t>(stream));

@@ -56,6 +56,12 @@ class nk_gemm_group(ctypes.Structure):
 
 _P = ctypes.c_void_p
 _I32, _I64, _SZ = ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+class nk_conv_group(ctypes.Structure):
+    _fields_ = [("I", nk_tensor), ("W", nk_tensor), ("O", nk_tensor), ("stride", ctypes.c_int64 * 2),
+                ("dilation", ctypes.c_int64 * 2), ("pad", ctypes.c_int64 * 4), ("bias", ctypes.c_void_p),
+                ("relu", ctypes.c_int32), ("accumulate", ctypes.c_int32)]
+
+
 _PT = ctypes.POINTER(nk_tensor)
 _PE = ctypes.POINTER(nk_epilogue)
 _PS = ctypes.POINTER(nk_schedule)
@@ -65,6 +71,7 @@ SIGNATURES = {
     "nk_matmul": (_I32, [_PT, _PT, _PT, _I32, _PE, _PS, _P, _SZ, _P]),
     "nk_matmul_workspace_size": (_I32, [_PT, _PT, _PT, _I32, _PS, ctypes.POINTER(_SZ)]),
     "nk_grouped_plan_create": (_I32, [_I32, ctypes.POINTER(nk_gemm_group), _I32, _PS, ctypes.POINTER(_P)]),
+    "nk_conv2d_grouped_plan_create": (_I32, [_I32, ctypes.POINTER(nk_conv_group), _PS, ctypes.POINTER(_P)]),
     "nk_grouped_plan_run": (_I32, [_P, _P]),
     "nk_grouped_plan_destroy": (_I32, [_P]),
     "nk_batch_matmul_grouped": (_I32, [_I32, ctypes.POINTER(nk_gemm_group), _I32, _PS, _P, _SZ, _P]),
@@ -317,6 +324,33 @@ def nk_grouped_workspace_size(G: int) -> int:
     n = ctypes.c_size_t(0)
     _check(lib().nk_grouped_workspace_size(G, None, PREC["bf16"], None, ctypes.byref(n)))
     return n.value
+
+
+def make_conv_groups(convs):
+    """nk_conv_group array from dicts with I (BF16 NHWC), W (packed BF16, from
+    nk_conv2d_pack_weights), O (FP32 NHWC) and optional stride, dilation,
+    pad (top, bottom, left, right), bias, relu, accumulate."""
+    G = len(convs)
+    arr = (nk_conv_group * max(G, 1))()
+    for g, d in enumerate(convs):
+        q = arr[g]
+        q.I, q.W, q.O = as_nk_tensor(d["I"]), as_nk_tensor(d["W"]), as_nk_tensor(d["O"])
+        st, dl, pd = d.get("stride", (1, 1)), d.get("dilation", (1, 1)), d.get("pad", (0, 0, 0, 0))
+        for i in range(2):
+            q.stride[i], q.dilation[i] = int(st[i]), int(dl[i])
+        for i in range(4):
+            q.pad[i] = int(pd[i])
+        b = d.get("bias")
+        q.bias = b.data_ptr() if b is not None else None
+        q.relu = int(bool(d.get("relu", False)))
+        q.accumulate = int(bool(d.get("accumulate", False)))
+    return arr, G
+
+
+def nk_conv2d_grouped_plan_create(groups, G, schedule=None):
+    h = ctypes.c_void_p()
+    _check(lib().nk_conv2d_grouped_plan_create(G, groups, _sched(schedule), ctypes.byref(h)))
+    return h
 
 
 def nk_grouped_plan_create(groups, G, precision="bf16", schedule=None):

@@ -282,3 +282,79 @@ def test_gpu_conv_equals_gpu_gemm_on_explicit_im2col(nk, case, prec):
     gemm = host(c).reshape(conv.shape)
     np.testing.assert_array_equal(conv, gemm)
     np.testing.assert_array_equal(conv, O.conv2d_nhwc_hwcf(I, W, st, dl, pad))
+
+
+CONV_GROUPS = [
+    # N, H, W, C, F, KH, KW, stride, dilation, pad, relu, accumulate
+    (2, 14, 14, 64, 64, 3, 3, (1, 1), (1, 1), (1, 1, 1, 1), True, False),
+    (1, 9, 13, 128, 96, 3, 3, (2, 2), (1, 1), (1, 1, 1, 1), False, False),
+    (3, 7, 7, 64, 200, 1, 1, (1, 1), (1, 1), (0, 0, 0, 0), True, True),
+    (1, 20, 18, 32, 40, 5, 3, (1, 2), (2, 1), (2, 2, 1, 1), False, True),
+    (2, 5, 6, 16, 24, 3, 3, (1, 1), (1, 1), (0, 1, 2, 0), True, False),
+    (1, 30, 30, 8, 8, 3, 3, (1, 1), (1, 1), (1, 1, 1, 1), False, False),
+]
+
+
+def _conv_group_operands(nk, seed):
+    convs, refs = [], []
+    for i, (N, H, Wd, C, F, KH, KW, st, dl, pad, relu, acc) in enumerate(CONV_GROUPS):
+        I = synth.small_ints(seed, 10 * i, (N, H, Wd, C))
+        W = synth.small_ints(seed, 10 * i + 1, (KH, KW, C, F))
+        b = synth.small_ints(seed, 10 * i + 2, (F,))
+        OH = O.conv_out_size(H, KH, st[0], dl[0], pad[0], pad[1])
+        OW = O.conv_out_size(Wd, KW, st[1], dl[1], pad[2], pad[3])
+        C0 = synth.small_ints(seed, 10 * i + 3, (N, OH, OW, F)) if acc else np.zeros((N, OH, OW, F), np.float32)
+        convs.append(dict(I=dev(I).to(torch.bfloat16), W=nk.nk_conv2d_pack_weights(dev(W)), O=dev(C0), stride=st,
+                          dilation=dl, pad=pad, bias=dev(b), relu=relu, accumulate=acc))
+        refs.append(O.epilogue(O.conv2d_nhwc_hwcf(I, W, st, dl, pad), c_in=C0, beta=1.0 if acc else 0.0, bias=b,
+                               relu=relu))
+    return convs, refs
+
+
+@pytest.mark.parametrize("sched", [None, (128, 64, 64, 1, 4, 1), (128, 256, 64, 1, 3, 1)])
+def test_grouped_convs_one_launch_bitwise(nk, sched):
+    """Six uneven convolutions (strides, dilations, 1x1 / 3x3 / 5x3 filters,
+    bias, ReLU, accumulate) computed by one persistent launch."""
+    convs, refs = _conv_group_operands(nk, 100)
+    groups, G = nk.make_conv_groups(convs)
+    plan = nk.nk_conv2d_grouped_plan_create(groups, G, schedule=sched)
+    nk.nk_grouped_plan_run(plan)
+    nk.nk_sync_status()
+    nk.nk_grouped_plan_destroy(plan)
+    for g in range(G):
+        np.testing.assert_array_equal(host(convs[g]["O"]), refs[g], err_msg=f"group {g}")
+
+
+def test_grouped_convs_graph_replay(nk):
+    """The grouped conv launch captured in a CUDA graph and replayed gives
+    the eager result (accumulate groups excluded: they add on every run)."""
+    convs, refs = _conv_group_operands(nk, 101)
+    for d in convs:
+        d["accumulate"] = False
+    groups, G = nk.make_conv_groups(convs)
+    plan = nk.nk_conv2d_grouped_plan_create(groups, G)
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        nk.nk_grouped_plan_run(plan, s.cuda_stream)
+        torch.cuda.synchronize()
+        eager = [host(d["O"]).copy() for d in convs]
+        for d in convs:
+            d["O"].zero_()
+        with torch.cuda.graph(g, stream=s):
+            nk.nk_grouped_plan_run(plan, s.cuda_stream)
+    g.replay()
+    torch.cuda.synchronize()
+    nk.nk_sync_status()
+    nk.nk_grouped_plan_destroy(plan)
+    for i in range(G):
+        np.testing.assert_array_equal(host(convs[i]["O"]), eager[i])
+
+
+def test_grouped_convs_reject_bad_groups(nk):
+    convs, _ = _conv_group_operands(nk, 102)
+    bad = dict(convs[0])
+    bad["I"] = bad["I"].float()       # FP32 input: the grouped launch takes BF16
+    groups, G = nk.make_conv_groups([convs[1], bad])
+    with pytest.raises(nk.NkError):
+        nk.nk_conv2d_grouped_plan_create(groups, G)
