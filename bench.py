@@ -460,6 +460,42 @@ def stack_graph(torch, synth, dev, batch, picks, flop):
             "how": "20 nk_conv2d calls on packed BF16 weights (one conv kernel each) in one CUDA graph, device time"}
 
 
+def grouped_conv_report(torch, nk, synth, dev, batch=8):
+    """The 20 ResNet-stack layer shapes at batch 8 as independent convolutions
+    (each with its own input): one persistent launch of all 20 (a grouped
+    conv plan) against 20 nk_conv2d calls with built-in schedules, both
+    replayed from CUDA graphs."""
+    convs, flop = [], 0.0
+    for L in synth.resnet_stack(batch):
+        oh = (L["H"] + 2 * L["pad"] - L["KH"]) // L["stride"] + 1
+        i = torch.empty(L["N"], L["H"], L["W"], L["C"], device=dev).uniform_(0, 1).to(torch.bfloat16)
+        w = nk.nk_conv2d_pack_weights(torch.empty(L["KH"], L["KW"], L["C"], L["F"], device=dev).normal_(0, 0.05))
+        o = torch.empty(L["N"], oh, oh, L["F"], device=dev)
+        convs.append(dict(I=i, W=w, O=o, stride=(L["stride"],) * 2, pad=(L["pad"],) * 4, relu=True,
+                          bias=torch.zeros(L["F"], device=dev)))
+        flop += 2.0 * L["N"] * oh * oh * L["F"] * L["KH"] * L["KW"] * L["C"]
+    groups, G = nk.make_conv_groups(convs)
+    from paper_2307_16080_gb300 import nk_tune as nt
+    tuned, trep = nt.nk_conv2d_grouped_tune(groups, G, reps=3)   # the autotuner picks the tile
+    plan = nk.nk_conv2d_grouped_plan_create(groups, G, schedule=tuned)
+    t_grouped = graph_time(torch, lambda: nk.nk_grouped_plan_run(plan), calls=2, reps=10)
+    nk.nk_grouped_plan_destroy(plan)
+    wss = [nk.workspace(nk.nk_conv2d_workspace_size(d["I"], d["W"], d["O"], d["stride"], (1, 1), d["pad"], "bf16"),
+                        dev) for d in convs]
+
+    def separate():
+        for d, ws in zip(convs, wss):
+            nk.nk_conv2d_nhwc_hwcf(d["I"], d["W"], d["O"], d["stride"], (1, 1), d["pad"], "bf16", bias=d["bias"],
+                                   relu=True, ws=ws)
+    t_sep = graph_time(torch, separate, calls=2, reps=10)
+    nk.nk_sync_status()
+    return {"groups": G, "batch": batch, "flop": flop, "one_launch_ms": t_grouped,
+            "one_launch_tflops": flop / (t_grouped * 1e-3) / 1e12, "separate_launches_ms": t_sep,
+            "separate_tflops": flop / (t_sep * 1e-3) / 1e12, "speedup": t_sep / t_grouped,
+            "schedule": list(tuned), "schedules_timed": trep.timed, "untuned_default_ms": trep.default_ms,
+            "how": "device time of CUDA-graph replays; grouped: per-tap kernel, tile from nk_conv2d_grouped_tune"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -566,6 +602,7 @@ def main():
         rr = resnet_report(torch, synth, dev)
         if rr is not None:
             extra["resnet_stack_bf16"] = rr
+        extra["grouped_conv_resnet_layers"] = grouped_conv_report(torch, nk, synth, dev)
 
     if rank != 0:
         if world > 1:

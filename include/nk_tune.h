@@ -103,6 +103,14 @@ nk_status nk_tune(const nk_problem* p, int32_t mode, int32_t topk, const float* 
 nk_status nk_grouped_tune(int32_t G, const nk_gemm_group* groups, int32_t precision, int32_t reps,
                           nk_schedule* best, nk_tune_report* rep, void* stream);
 
+/* Grouped convolutions (nk_conv2d_grouped_plan_create): times every legal
+ * grouped conv schedule (tile_m 128, tile_k 64, cluster 1, split_k 1;
+ * tile_n 64 / 128 / 256; stages 2..8) on the caller's groups and returns the
+ * fastest; every group's O is overwritten while timing (accumulate flags
+ * are ignored).  Same conventions as nk_grouped_tune.                      */
+nk_status nk_conv2d_grouped_tune(int32_t G, const nk_conv_group* groups, int32_t reps,
+                                 nk_schedule* best, nk_tune_report* rep, void* stream);
+
 /* ------------------------------------------------------- the cost model */
 /* Parameters: one FP32 device buffer of nk_mlp_param_count() values laid out
  * W1 [128][16], b1 [128], W2 [128][128], b2 [128], W3 [128], b3 [1].

@@ -589,6 +589,57 @@ nk_status nk_grouped_tune(int32_t G, const nk_gemm_group* groups, int32_t precis
   return NK_OK;
 }
 
+nk_status nk_conv2d_grouped_tune(int32_t G, const nk_conv_group* groups, int32_t reps, nk_schedule* best,
+                                 nk_tune_report* rep, void* stream) {
+  if (!best) return fail(NK_ERR_INVALID_ARG, "best is NULL");
+  if (G < 1 || !groups) return fail(NK_ERR_INVALID_ARG, "need at least one group");
+  nk_status st = require_device();
+  if (st != NK_OK) return st;
+  std::lock_guard<std::mutex> lk(g_mu);
+  cudaStream_t user = static_cast<cudaStream_t>(stream);
+  cudaError_t e = user ? cudaStreamSynchronize(user) : cudaSuccess;
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+  std::vector<nk_conv_group> gs(groups, groups + G);
+  for (auto& q : gs) q.accumulate = 0;   // repeated runs must not pile up into O
+  auto time_plan = [&](const nk_schedule* s, float* ms) -> nk_status {
+    nk_grouped_plan* plan = nullptr;
+    nk_status r = nk_conv2d_grouped_plan_create(G, gs.data(), s, &plan);
+    if (r != NK_OK) return r;
+    r = time_device([&](cudaStream_t cs) { return nk_grouped_plan_run(plan, cs); }, reps, ms);
+    nk_grouped_plan_destroy(plan);
+    return r;
+  };
+  float dms = 0.f;
+  if ((st = time_plan(nullptr, &dms)) != NK_OK) return st;
+  int cands = 0, timed = 0;
+  float best_ms = 0.f;
+  for (int tn : {64, 128, 256})
+    for (int stages = 2; stages <= 8; ++stages) {
+      const nk_schedule s{128, tn, 64, 1, stages, 1};
+      nk_grouped_plan* probe = nullptr;
+      nk_status r = nk_conv2d_grouped_plan_create(G, gs.data(), &s, &probe);
+      if (r == NK_ERR_NO_SCHEDULE) continue;   // does not fit shared memory
+      if (r != NK_OK) return r;
+      nk_grouped_plan_destroy(probe);
+      ++cands;
+      float ms = 0.f;
+      if ((st = time_plan(&s, &ms)) != NK_OK) return st;
+      ++timed;
+      if (timed == 1 || ms < best_ms) {
+        best_ms = ms;
+        *best = s;
+      }
+    }
+  if (rep) {
+    rep->candidates = cands;
+    rep->timed = timed;
+    rep->best_ms = best_ms;
+    rep->default_ms = dms;
+  }
+  return NK_OK;
+}
+
 nk_status nk_time_schedule(const nk_problem* p, const nk_schedule* s, int32_t reps, float* median_ms,
                            void* stream) {
   nk_status st = check_problem(p);

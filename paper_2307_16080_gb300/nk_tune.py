@@ -37,6 +37,7 @@ SIGNATURES = {
     "nk_tune_release": (_I32, []),
     "nk_tune": (_I32, [_PP, _I32, _I32, _P, _I32, _PS, ctypes.POINTER(nk_tune_report), _P]),
     "nk_grouped_tune": (_I32, [_I32, _P, _I32, _I32, _PS, ctypes.POINTER(nk_tune_report), _P]),
+    "nk_conv2d_grouped_tune": (_I32, [_I32, _P, _I32, _PS, ctypes.POINTER(nk_tune_report), _P]),
     "nk_mlp_param_count": (_SZ, []),
     "nk_mlp_forward": (_I32, [_P, _P, _I64, _P, _P]),
     "nk_mlp_workspace_size": (_SZ, [_I64]),
@@ -125,6 +126,16 @@ def nk_grouped_tune(groups, G, precision="bf16", reps=3, stream=None):
     rep = nk_tune_report()
     _check(lib().nk_grouped_tune(G, ctypes.cast(groups, ctypes.c_void_p), nk.PREC[precision], reps,
                                  ctypes.byref(best), ctypes.byref(rep), _stream(stream)))
+    return best.as_tuple(), rep
+
+
+def nk_conv2d_grouped_tune(groups, G, reps=3, stream=None):
+    """Fastest grouped-conv plan schedule for these groups (from
+    nk.make_conv_groups); overwrites every group's O while timing."""
+    best = nk_schedule()
+    rep = nk_tune_report()
+    _check(lib().nk_conv2d_grouped_tune(G, ctypes.cast(groups, ctypes.c_void_p), reps, ctypes.byref(best),
+                                        ctypes.byref(rep), _stream(stream)))
     return best.as_tuple(), rep
 
 

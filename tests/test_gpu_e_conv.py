@@ -358,3 +358,22 @@ def test_grouped_convs_reject_bad_groups(nk):
     groups, G = nk.make_conv_groups([convs[1], bad])
     with pytest.raises(nk.NkError):
         nk.nk_conv2d_grouped_plan_create(groups, G)
+
+
+def test_grouped_convs_tune_and_exact(nk):
+    """nk_conv2d_grouped_tune returns the fastest legal grouped-conv tile (no
+    slower than the built-in one) and a plan built with it stays exact."""
+    from paper_2307_16080_gb300 import nk_tune as nt
+    convs, refs = _conv_group_operands(nk, 103)
+    groups, G = nk.make_conv_groups(convs)
+    best, rep = nt.nk_conv2d_grouped_tune(groups, G, reps=3)
+    assert rep.timed == rep.candidates >= 10 and best[0] == 128 and best[3] == 1 and best[5] == 1
+    assert 0 < rep.best_ms <= rep.default_ms * 1.05
+    convs, refs = _conv_group_operands(nk, 103)     # fresh O (tuning overwrote them)
+    groups, G = nk.make_conv_groups(convs)
+    plan = nk.nk_conv2d_grouped_plan_create(groups, G, schedule=best)
+    nk.nk_grouped_plan_run(plan)
+    nk.nk_sync_status()
+    nk.nk_grouped_plan_destroy(plan)
+    for g in range(G):
+        np.testing.assert_array_equal(host(convs[g]["O"]), refs[g], err_msg=f"group {g}")
