@@ -348,6 +348,24 @@ def layer_roofline(N, H, W, C, F, KH, KW, stride, pad, ms):
             "peak_source": f"{src} (MEASURED_PEAKS.json)"}
 
 
+def conv_batch32(torch, nk, synth, dev):
+    """The same layer at batch 32 (the ResNet stack's first layers): FP32 on
+    the CUDA cores vs BF16 on packed weights, graph-replayed device time."""
+    I, W, bias = synth.conv_resnet_block(N=32)
+    i32, w32, b32 = (torch.from_numpy(x).to(dev) for x in (I, W, bias))
+    out = torch.empty(32, 56, 56, 64, device=dev)
+    flop = 2.0 * 32 * 56 * 56 * 64 * 9 * 64
+    g32 = graph_time(torch, lambda: nk.nk_conv2d_nhwc_hwcf(i32, w32, out, pad=(1, 1, 1, 1), bias=b32, relu=True),
+                     calls=4, reps=5)
+    i16, wp = i32.to(torch.bfloat16), nk.nk_conv2d_pack_weights(w32)
+    ws = nk.workspace(nk.nk_conv2d_workspace_size(i16, wp, out, pad=(1, 1, 1, 1), precision="bf16"), dev)
+    gp = graph_time(torch, lambda: nk.nk_conv2d_nhwc_hwcf(i16, wp, out, pad=(1, 1, 1, 1), precision="bf16",
+                                                          bias=b32, relu=True, ws=ws))
+    nk.nk_sync_status()
+    return {"f32_ms": g32, "f32_tflops": flop / (g32 * 1e-3) / 1e12, "bf16_packed_ms": gp,
+            "bf16_packed_tflops": flop / (gp * 1e-3) / 1e12, "bf16_packed_over_f32": g32 / gp}
+
+
 def conv_report(torch, nk, synth, dev):
     """FP32 conv config (8x56x56x64, 3x3x64x64, s1 p1, bias + ReLU) on the
     CUDA cores, and the same layer in BF16 on the tensor cores."""
@@ -379,6 +397,7 @@ def conv_report(torch, nk, synth, dev):
             "graph_bf16_packed_over_f32": g32 / gp,
             "roofline_bf16_packed": layer_roofline(8, 56, 56, 64, 64, 3, 3, 1, 1, gp),
             "graph_fp8_ms": g8, "graph_fp8_tflops": flop / (g8 * 1e-3) / 1e12, "graph_fp8_over_f32": g32 / g8,
+            "batch32": conv_batch32(torch, nk, synth, dev),
             "note": "per call: host overhead included; graph: device time of calls replayed from a CUDA graph; "
                     "bf16 includes the per-call FP32 -> BF16 weight cast, bf16_packed takes weights packed once "
                     "by nk_conv2d_pack_weights, fp8 includes the per-call amax and E4M3 quantisation of I and W"}
