@@ -22,6 +22,13 @@ What it computes, and where the paper defines it:
   zero padding (out-of-range input reads as 0).
 * ``batch_matmul`` / ``grouped_matmul``: the matmul with a leading batch
   (group) index, one independent contraction per group.
+* ``ew_program`` / ``matmul_fused`` / ``conv2d_fused``: elementwise programs
+  folded around the contraction -- the bias-add loop that follows the matmul
+  of the lowered ``torch.nn.Linear`` (Listing "listing1", Sec. 2.1.2) and the
+  elementwise product ``C[x,y] = A[x,y] * B[x,y]`` of the GPUModule kernel
+  (Listing "gpumodules", Sec. 3.1) -- as epilogues on the output and
+  prologues on the operands, with the usual activations written from their
+  definitions.
 * Number formats (BF16, FP8 E4M3, the BF16 hi/lo split) written from the
   format definitions, not from any conversion routine.
 * The tile-cost MLP (forward, backward, Adam) that ranks schedules for the
@@ -327,6 +334,120 @@ def conv2d_nchw_fchw_loops(inp, ker) -> np.ndarray:
                             for kj in range(K):
                                 out[n, co, ho, wo] += inp[n, ci, ho + ki, wo + kj] * ker[co, ci, ki, kj]
     return out
+
+
+# ------------------------------------------------------------------ elementwise programs
+def sigmoid(x) -> np.ndarray:
+    """The logistic function 1 / (1 + e^-x), written per sign so that exp never
+    overflows: for x < 0 it is e^x / (1 + e^x)."""
+    x = np.asarray(x, dtype=np.float64)
+    out = np.empty_like(x)
+    pos = x >= 0
+    out[pos] = 1.0 / (1.0 + np.exp(-x[pos]))
+    ex = np.exp(x[~pos])
+    out[~pos] = ex / (1.0 + ex)
+    return out
+
+
+def silu(x) -> np.ndarray:
+    """x * sigmoid(x) (the sigmoid-weighted linear unit, also called swish)."""
+    x = np.asarray(x, dtype=np.float64)
+    return x * sigmoid(x)
+
+
+def gelu_tanh(x) -> np.ndarray:
+    """The tanh approximation of GELU from Hendrycks and Gimpel (2016):
+    0.5 x (1 + tanh(sqrt(2/pi) (x + 0.044715 x^3)))."""
+    x = np.asarray(x, dtype=np.float64)
+    return 0.5 * x * (1.0 + np.tanh(math.sqrt(2.0 / math.pi) * (x + 0.044715 * x ** 3)))
+
+
+EW_STEPS = ("mul", "add", "affine", "relu", "gelu", "gelu_tanh", "silu", "sigmoid", "tanh", "clamp")
+
+
+def ew_program(x, prog) -> np.ndarray:
+    """Run an elementwise program on x, step by step in the given order, in FP64.
+
+    Steps: ("mul", T) -> x * T and ("add", T) -> x + T with T of x's shape (the
+    GPUModule product and the Linear layer's bias-add loop, generalised to a
+    full operand); ("affine", a, b) -> a x + b; ("relu",) -> max(x, 0) with NaN
+    kept; ("gelu",) -> x Phi(x); ("gelu_tanh",); ("silu",); ("sigmoid",);
+    ("tanh",); ("clamp", lo, hi) -> lo below lo, hi above hi, NaN kept.
+    """
+    out = np.array(x, dtype=np.float64)
+    for step in prog or ():
+        name, *args = step
+        if name == "mul":
+            out = out * np.asarray(args[0], dtype=np.float64)
+        elif name == "add":
+            out = out + np.asarray(args[0], dtype=np.float64)
+        elif name == "affine":
+            out = float(args[0]) * out + float(args[1])
+        elif name == "relu":
+            out = np.where(np.isnan(out), out, np.maximum(out, 0.0))
+        elif name == "gelu":
+            out = gelu(out)
+        elif name == "gelu_tanh":
+            out = gelu_tanh(out)
+        elif name == "silu":
+            out = silu(out)
+        elif name == "sigmoid":
+            out = sigmoid(out)
+        elif name == "tanh":
+            out = np.tanh(out)
+        elif name == "clamp":
+            lo, hi = float(args[0]), float(args[1])
+            out = np.where(out < lo, lo, np.where(out > hi, hi, out))
+        else:
+            raise ValueError(f"unknown step {name!r}")
+    return out
+
+
+def prologue(x32, prog) -> np.ndarray:
+    """An operand after its prologue, as the value the precision then rounds:
+    the program in FP64, rounded once to FP32 (the precision in which the
+    kernels hand the transformed operand to the BF16 / E4M3 conversion, so
+    that both sides take the rounding decision on the same FP32 value)."""
+    if not prog:
+        return np.asarray(x32, dtype=np.float32)
+    return ew_program(np.asarray(x32, dtype=np.float32), prog).astype(np.float32)
+
+
+def matmul_fused(A32, B32, precision="f32", pro_a=None, pro_b=None, c_in=None, bias=None,
+                 relu=False, beta=0.0, ew=None) -> np.ndarray:
+    """ew(ReLU?(beta*C_in + op(pro_a(A)) @ op(pro_b(B)) + bias)): the prologues
+    on the FP32 operands, the precision's arithmetic (matmul_precision), the
+    epilogue, then the epilogue program on each output element."""
+    A = prologue(A32, pro_a)
+    B = prologue(B32, pro_b)
+    acc = matmul_precision(A, B, precision)
+    return ew_program(epilogue(acc, c_in, bias, relu, beta=beta), ew)
+
+
+def conv2d_precision(I32, W32, precision="f32", stride=(1, 1), dilation=(1, 1), pad=(0, 0, 0, 0)) -> np.ndarray:
+    """The convolution on the values a precision multiplies: FP32 as given,
+    bf16_rn of I and W, or E4M3 codes with per-tensor scales (result divided
+    by s_i * s_w)."""
+    if precision == "f32":
+        return conv2d_nhwc_hwcf(I32, W32, stride, dilation, pad)
+    if precision == "bf16":
+        return conv2d_nhwc_hwcf(bf16_rn(I32), bf16_rn(W32), stride, dilation, pad)
+    if precision == "fp8":
+        si, sw = fp8_scale(I32), fp8_scale(W32)
+        O = conv2d_nhwc_hwcf(fp8_quantize(I32, si), fp8_quantize(W32, sw), stride, dilation, pad)
+        return O / (float(si) * float(sw))
+    raise ValueError(precision)
+
+
+def conv2d_fused(I32, W32, precision="f32", stride=(1, 1), dilation=(1, 1), pad=(0, 0, 0, 0), pro_i=None,
+                 pro_w=None, o_in=None, bias=None, relu=False, beta=0.0, ew=None) -> np.ndarray:
+    """ew(ReLU?(beta*O_in + conv(pro_i(I), pro_w(W)) + bias)).  The prologue
+    runs on the input tensor itself, so the zero padding the convolution
+    reads outside it stays zero."""
+    I = prologue(I32, pro_i)
+    W = prologue(W32, pro_w)
+    acc = conv2d_precision(I, W, precision, stride, dilation, pad)
+    return ew_program(epilogue(acc, o_in, bias, relu, beta=beta), ew)
 
 
 def rel_frobenius(C, R) -> float:
