@@ -19,7 +19,9 @@
  *
  * followed by the epilogue of the lowered torch.nn.Linear (Sec. 2.1.2 Listing
  * "listing1": zero-fill, contraction, bias add), extended with ReLU and a
- * dequantisation scale:   out = ReLU?(beta*C_in + alpha*acc + bias[n]).
+ * dequantisation scale:   out = ReLU?(beta*C_in + alpha*acc + bias[n]),
+ * then an optional fused elementwise program (nk_ew_program); operands may
+ * pass through such a program before the contraction (prologues).
  *
  * Conventions for every entry point
  *  - The caller owns every buffer and the stream.  The library never frees or
@@ -84,18 +86,94 @@ typedef struct {
   int64_t stride[4];
 } nk_tensor;
 
-/* out = ReLU?(beta*C_in + alpha*acc + bias[n]) with beta = accumulate ? 1 : 0.
+/* ------------------------------------------- fused elementwise programs */
+
+/* A program of up to NK_EW_MAX elementwise operations, applied in order to
+ * each element x of a tensor inside the kernel that produces or reads it.
+ * These are the linalg.generic consumers and producers around a contraction
+ * that a lowering otherwise leaves as separate loop nests -- the bias-add
+ * loop after the matmul of the lowered torch.nn.Linear (Sec. 2.1.2 Listing
+ * "listing1") and the elementwise product C[x,y] = A[x,y] * B[x,y] of the
+ * GPUModule kernel (Sec. 3.1 Listing "gpumodules") -- folded into the
+ * epilogue (or, for operands, into the conversion pass or the loads).
+ * Every step computes in FP32 and rounds to FP32.
+ *
+ *   NK_EW_MUL        x = x * t[i]            (t: tensor operand, see below)
+ *   NK_EW_ADD        x = x + t[i]
+ *   NK_EW_AFFINE     x = fma(a, x, b)        (one rounding)
+ *   NK_EW_RELU       x = max(x, 0)           (NaN stays NaN)
+ *   NK_EW_GELU       x = x * Phi(x) = 0.5 x (1 + erf(x / sqrt 2))
+ *   NK_EW_GELU_TANH  x = 0.5 x (1 + tanh(sqrt(2/pi) (x + 0.044715 x^3)))
+ *   NK_EW_SILU       x = x * sigmoid(x)
+ *   NK_EW_SIGMOID    x = 1 / (1 + exp(-x))
+ *   NK_EW_TANH       x = tanh(x)
+ *   NK_EW_CLAMP      x = x < a ? a : (x > b ? b : x)   (a <= b; NaN stays NaN)
+ *
+ * A tensor operand `t` (MUL, ADD) is FP32 with the shape and the strides of
+ * the tensor the program runs over (the output C / O for an epilogue, the
+ * operand A, B, I or W for a prologue), so element (i0, i1, ..) of `t` pairs
+ * with the same element of that tensor.  It may alias that tensor's output
+ * only for an epilogue (each element is read before its own result is
+ * written).  Checked before launch: 0 <= n <= NK_EW_MAX, known opcodes,
+ * finite a <= b for CLAMP, and for MUL / ADD a non-NULL 4-byte aligned FP32
+ * t of matching rank, shape and strides (NK_ERR_INVALID_ARG otherwise).   */
+#define NK_EW_MAX 4
+typedef enum {
+  NK_EW_MUL = 1,
+  NK_EW_ADD = 2,
+  NK_EW_AFFINE = 3,
+  NK_EW_RELU = 4,
+  NK_EW_GELU = 5,
+  NK_EW_GELU_TANH = 6,
+  NK_EW_SILU = 7,
+  NK_EW_SIGMOID = 8,
+  NK_EW_TANH = 9,
+  NK_EW_CLAMP = 10
+} nk_ew_opcode;
+
+typedef struct {
+  int32_t op;   /* nk_ew_opcode */
+  float a, b;   /* AFFINE: a*x + b; CLAMP: [a, b]; ignored otherwise */
+  nk_tensor t;  /* MUL / ADD operand; ignored otherwise */
+} nk_ew_op;
+
+typedef struct {
+  int32_t n;    /* number of operations, 0..NK_EW_MAX */
+  nk_ew_op ops[NK_EW_MAX];
+} nk_ew_program;
+
+/* out = ew(ReLU?(beta*C_in + alpha*acc + bias[n])) with beta = accumulate ?
+ * 1 : 0.
  * bias: FP32 device vector of length N (GEMM) / F (conv), or NULL.
  * scale_a, scale_b: only read for FP8 inputs that are already quantised
  * (dtype NK_F8E4M3): the quantisation scales s_a, s_b; alpha = 1/(s_a*s_b).
- * For FP32 inputs at NK_PREC_FP8 the library computes the scales itself.  */
+ * For FP32 inputs at NK_PREC_FP8 the library computes the scales itself.
+ * ew: elementwise program run on every output element last, or NULL.
+ * pro_a, pro_b: programs run on every element of the FP32 operand A and B
+ * (conv: I and W) before the contraction, or NULL.  The transformed value is
+ * what the precision rounds (BF16, BF16x3) or quantises (FP8: the amax and
+ * the scale are taken over the transformed values); for the convolution the
+ * zero padding stays zero.  An operand that is given already converted
+ * (BF16 / E4M3 dtype, packed conv weights) takes no prologue
+ * (NK_ERR_UNSUPPORTED).  A zero-initialised struct is the plain epilogue.  */
 typedef struct {
   const float* bias;
   int32_t relu;
   int32_t accumulate;
   float scale_a;
   float scale_b;
+  const nk_ew_program* ew;
+  const nk_ew_program* pro_a;
+  const nk_ew_program* pro_b;
 } nk_epilogue;
+
+/* Y = prog(X) elementwise: the GPUModule kernel of Sec. 3.1 (with prog = one
+ * NK_EW_MUL by B it is C[x,y] = A[x,y] * B[x,y]) as a standalone pass.  X, Y:
+ * FP32 tensors of the same rank (1..4) and shape; Y may be X (in place).
+ * Tensor operands of `prog` have Y's shape and strides.  HBM-bound: one read
+ * of X and of each operand, one write of Y.  Allocates nothing.            */
+nk_status nk_elementwise(const nk_tensor* X, nk_tensor* Y, const nk_ew_program* prog,
+                         void* stream);
 
 /* Tile schedule.  tile_m x tile_n output tile per CTA (cluster 2 pairs two
  * CTAs along M that share B tiles through TMA multicast), tile_k reduction

@@ -48,12 +48,13 @@ struct Direct {
   int relu;
   float beta;
   int in_h, in_w;          // halo tile extent
+  EwProg ew;               // fused elementwise program (offsets from O)
 };
 
 // Shared memory is sized to the actual halo tile (18 x 66 floats for a 3 x 3
 // stride-1 filter), so many CTAs share an SM and keep enough loads in flight
 // to reach HBM bandwidth.
-__global__ void __launch_bounds__(THREADS) direct_conv_kernel(Direct p) {
+__global__ void __launch_bounds__(THREADS) direct_conv_kernel(const __grid_constant__ Direct p) {
   extern __shared__ float smem_f[];
   float* ker = smem_f;                    // [CO_G][64] taps of one input channel
   float* tile = smem_f + CO_G * 64;       // [in_h][in_w] halo tile
@@ -127,6 +128,7 @@ __global__ void __launch_bounds__(THREADS) direct_conv_kernel(Direct p) {
       if (p.beta != 0.f && wo + j < p.OW) o = fmaf(p.beta, dst[j], o);
       o += b;
       if (p.relu) o = (o > 0.f || o != o) ? o : 0.f;
+      if (p.ew.n && wo + j < p.OW) o = ew_run(p.ew, o, (dst - p.O) + j);
       v[j] = o;
     }
     if (wo + 3 < p.OW && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
@@ -170,7 +172,7 @@ __device__ __forceinline__ void load_segment(const float* src, int64_t sIh, int 
 }
 
 template <int KH, int KW, int CO_G, int ROWS>
-__global__ void __launch_bounds__(128) direct_rows_kernel(Direct p) {
+__global__ void __launch_bounds__(128) direct_rows_kernel(const __grid_constant__ Direct p) {
   constexpr int SEG = 4 + KW - 1;
   constexpr int TAPS = KH * KW;
   const int wo = blockIdx.x * 512 + threadIdx.x * 4;   // first of this thread's 4 output columns
@@ -228,6 +230,7 @@ __global__ void __launch_bounds__(128) direct_rows_kernel(Direct p) {
         if (p.beta != 0.f && wo + j < p.OW) o = fmaf(p.beta, dst[j], o);
         o += b;
         if (p.relu) o = (o > 0.f || o != o) ? o : 0.f;
+        if (p.ew.n && wo + j < p.OW) o = ew_run(p.ew, o, (dst - p.O) + j);
         v[j] = o;
       }
       const uintptr_t a = reinterpret_cast<uintptr_t>(dst);
@@ -254,6 +257,7 @@ __device__ __forceinline__ void store4(const Direct& p, float* dst, int wo, floa
     if (p.beta != 0.f && wo + j < p.OW) o = fmaf(p.beta, dst[j], o);
     o += b;
     if (p.relu) o = (o > 0.f || o != o) ? o : 0.f;
+    if (p.ew.n && wo + j < p.OW) o = ew_run(p.ew, o, (dst - p.O) + j);
     v[j] = o;
   }
   const uintptr_t ad = reinterpret_cast<uintptr_t>(dst);
@@ -272,7 +276,7 @@ __device__ __forceinline__ void store4(const Direct& p, float* dst, int wo, floa
 // One input channel: output row o lives in accumulator slot o % KH while
 // input rows o .. o+KH-1 arrive; it is stored after the last of them.
 template <int KH, int KW, int CO_G>
-__global__ void __launch_bounds__(128) direct_stream_kernel(Direct p, int rpt) {
+__global__ void __launch_bounds__(128) direct_stream_kernel(const __grid_constant__ Direct p, int rpt) {
   constexpr int SEG = 4 + KW - 1;
   constexpr int TAPS = KH * KW;
   const int wo = blockIdx.x * 512 + threadIdx.x * 4;
@@ -379,8 +383,7 @@ using namespace nk;
 extern "C" nk_status nk_conv2d_nchw_fchw(const nk_tensor* I, const nk_tensor* K, nk_tensor* O,
                                          const int64_t stride[2], const int64_t dilation[2],
                                          const int64_t pad[4], const nk_epilogue* epi, void* stream) {
-  nk_status s = require_device();
-  if (s != NK_OK) return s;
+  nk_status s = NK_OK;
   if (!I || !K || !O || !stride || !dilation || !pad) return fail(NK_ERR_INVALID_ARG, "null argument");
   if (I->rank != 4 || K->rank != 4 || O->rank != 4) return fail(NK_ERR_INVALID_ARG, "I, K, O must have rank 4");
   if (I->dtype != NK_F32 || K->dtype != NK_F32 || O->dtype != NK_F32)
@@ -416,11 +419,15 @@ extern "C" nk_status nk_conv2d_nchw_fchw(const nk_tensor* I, const nk_tensor* K,
   p.Kr = static_cast<const float*>(K->ptr);
   p.O = static_cast<float*>(O->ptr);
   p.sOn = O->stride[0]; p.sOc = O->stride[1]; p.sOh = O->stride[2];
-  const nk_epilogue e0{nullptr, 0, 0, 1.f, 1.f};
+  const nk_epilogue e0{nullptr, 0, 0, 1.f, 1.f, nullptr, nullptr, nullptr};
   const nk_epilogue& E = epi ? *epi : e0;
   p.bias = E.bias;
   p.relu = E.relu;
   p.beta = E.accumulate ? 1.f : 0.f;
+  if (E.pro_a || E.pro_b)
+    return fail(NK_ERR_UNSUPPORTED, "the direct NCHW convolution takes no operand prologue");
+  if ((s = ew_program(E.ew, O, &p.ew, "ew")) != NK_OK) return s;
+  if ((s = require_device()) != NK_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (p.sh == 1 && p.sw == 1 && p.dh == 1 && p.dw == 1 && p.CI == 1) {
     if (p.KH == 3 && p.KW == 3) return launch_stream<3, 3>(p, st);

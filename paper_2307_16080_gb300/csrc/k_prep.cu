@@ -29,11 +29,22 @@ __device__ __forceinline__ float warp_max(float v) {
   return v;
 }
 
+// Prologue program on four consecutive elements starting at offset `off`.
+template <bool PRO>
+__device__ __forceinline__ void pro4(const EwProg& e, float* v, int64_t off) {
+  if constexpr (PRO) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[j] = ew_run(e, v[j], off + j);
+  }
+}
+
 // amax over a [rows, cols] matrix with row stride ld.  Stage 1: one partial
 // per block; stage 2: one block folds the partials.  NaN inputs make the
-// result NaN (the scale then falls back to 1).
+// result NaN (the scale then falls back to 1).  PRO: the amax of the values
+// after the prologue program `pro`.
+template <bool PRO>
 __global__ void amax_stage1(const float* __restrict__ x, int64_t rows, int64_t cols, int64_t ld,
-                            float* __restrict__ partial) {
+                            float* __restrict__ partial, const __grid_constant__ EwProg pro) {
   float m = 0.f;
   bool nan = false;
   const bool al = (reinterpret_cast<uintptr_t>(x) & 15) == 0;
@@ -42,7 +53,12 @@ __global__ void amax_stage1(const float* __restrict__ x, int64_t rows, int64_t c
     const float4* x4 = reinterpret_cast<const float4*>(x);
     const int64_t n4 = rows * cols / 4;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
-      const float4 v = __ldg(x4 + i);
+      float4 v = __ldg(x4 + i);
+      if constexpr (PRO) {
+        float w[4] = {v.x, v.y, v.z, v.w};
+        pro4<PRO>(pro, w, 4 * i);
+        v = make_float4(w[0], w[1], w[2], w[3]);
+      }
       nan |= (v.x != v.x) | (v.y != v.y) | (v.z != v.z) | (v.w != v.w);
       m = fmaxf(m, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
     }
@@ -53,13 +69,19 @@ __global__ void amax_stage1(const float* __restrict__ x, int64_t rows, int64_t c
       const float* row = x + r * ld;
       if (vec) {
         for (int64_t c = threadIdx.x; c < cols / 4; c += blockDim.x) {
-          const float4 v = __ldg(reinterpret_cast<const float4*>(row) + c);
+          float4 v = __ldg(reinterpret_cast<const float4*>(row) + c);
+          if constexpr (PRO) {
+            float w[4] = {v.x, v.y, v.z, v.w};
+            pro4<PRO>(pro, w, r * ld + 4 * c);
+            v = make_float4(w[0], w[1], w[2], w[3]);
+          }
           nan |= (v.x != v.x) | (v.y != v.y) | (v.z != v.z) | (v.w != v.w);
           m = fmaxf(m, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
         }
       } else {
         for (int64_t c = threadIdx.x; c < cols; c += blockDim.x) {
-          const float v = row[c];
+          float v = row[c];
+          if constexpr (PRO) v = ew_run(pro, v, r * ld + c);
           nan |= (v != v);
           m = fmaxf(m, fabsf(v));
         }
@@ -135,11 +157,12 @@ struct Caster<2> {
 };
 
 // Row-major cast without transpose: four elements per thread per step.
-template <int KIND>
+// PRO: the prologue program `pro` runs on each element before the cast.
+template <int KIND, bool PRO>
 __global__ void cast_rows(const float* __restrict__ in, int64_t rows, int64_t cols, int64_t ld_in,
                           const float* __restrict__ amax, typename Caster<KIND>::T* __restrict__ o0,
                           typename Caster<KIND>::T* __restrict__ o1, int64_t ld_out,
-                          float* scale_out) {
+                          float* scale_out, const __grid_constant__ EwProg pro) {
   using T = typename Caster<KIND>::T;
   const float s = KIND == 1 ? fp8_scale_of(amax) : 1.f;
   if (scale_out && blockIdx.x == 0 && threadIdx.x == 0) *scale_out = s;
@@ -158,6 +181,11 @@ __global__ void cast_rows(const float* __restrict__ in, int64_t rows, int64_t co
 #pragma unroll
       for (int j = 0; j < 4; ++j) v[j] = (c + j < cols) ? in[r * ld_in + c + j] : 0.f;
     }
+    if constexpr (PRO) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (c + j < cols) v[j] = ew_run(pro, v[j], r * ld_in + c + j);
+    }
     T a[4], b[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) Caster<KIND>::cvt(v[j], s, a[j], b[j]);
@@ -174,12 +202,12 @@ __global__ void cast_rows(const float* __restrict__ in, int64_t rows, int64_t co
 // Transposing cast: a 64 x 64 tile through shared memory.  Reads are 128-bit
 // along the input rows; writes pack 8 BF16 (or 16 E4M3) consecutive output
 // elements into one 16-byte store, so both sides move whole sectors.
-template <int KIND>
+template <int KIND, bool PRO>
 __global__ void __launch_bounds__(256) cast_transpose(const float* __restrict__ in, int64_t rows, int64_t cols,
                                                       int64_t ld_in, const float* __restrict__ amax,
                                                       typename Caster<KIND>::T* __restrict__ o0,
                                                       typename Caster<KIND>::T* __restrict__ o1, int64_t ld_out,
-                                                      float* scale_out) {
+                                                      float* scale_out, const __grid_constant__ EwProg pro) {
   using T = typename Caster<KIND>::T;
   constexpr int TS = 64;
   constexpr int VEC = sizeof(T) == 1 ? 16 : 8;      // output elements per 16-byte store
@@ -202,6 +230,11 @@ __global__ void __launch_bounds__(256) cast_transpose(const float* __restrict__ 
 #pragma unroll
         for (int j = 0; j < 4; ++j)
           if (c + j < cols) v[j] = in[r * ld_in + c + j];
+      }
+      if constexpr (PRO) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (c + j < cols) v[j] = ew_run(pro, v[j], r * ld_in + c + j);
       }
     }
 #pragma unroll
@@ -289,27 +322,78 @@ __global__ void norm_stage2(const double* __restrict__ partial, int n, double* _
   }
 }
 
-template <int KIND>
+template <int KIND, bool PRO>
 nk_status launch_cast(const float* in, int64_t rows, int64_t cols, int64_t ld_in,
                       const float* amax, void* out0, void* out1, int64_t ld_out, int transpose,
-                      float* scale_out, cudaStream_t st, int sms) {
+                      float* scale_out, cudaStream_t st, int sms, const EwProg& pro) {
   using T = typename Caster<KIND>::T;
   T* o0 = static_cast<T*>(out0);
   T* o1 = static_cast<T*>(out1);
   if (transpose) {
     dim3 grid((unsigned)((cols + 63) / 64), (unsigned)((rows + 63) / 64));
     if (grid.y > 65535) return fail(NK_ERR_UNSUPPORTED, "too many rows for the transposing cast");
-    cast_transpose<KIND><<<grid, 256, 0, st>>>(in, rows, cols, ld_in, amax, o0, o1, ld_out, scale_out);
+    cast_transpose<KIND, PRO><<<grid, 256, 0, st>>>(in, rows, cols, ld_in, amax, o0, o1, ld_out, scale_out, pro);
   } else {
     const int64_t work = rows * ((cols + 3) / 4);
     int64_t blocks = (work + 255) / 256;
     const int64_t cap = (int64_t)sms * 16;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    cast_rows<KIND><<<(unsigned)blocks, 256, 0, st>>>(in, rows, cols, ld_in, amax, o0, o1, ld_out,
-                                                       scale_out);
+    cast_rows<KIND, PRO><<<(unsigned)blocks, 256, 0, st>>>(in, rows, cols, ld_in, amax, o0, o1, ld_out,
+                                                            scale_out, pro);
   }
   return check_launch("cast kernel");
+}
+
+template <int KIND>
+nk_status launch_cast(const float* in, int64_t rows, int64_t cols, int64_t ld_in, const float* amax,
+                      void* out0, void* out1, int64_t ld_out, int transpose, float* scale_out, cudaStream_t st,
+                      int sms, const EwProg* pro) {
+  if (pro && pro->n)
+    return launch_cast<KIND, true>(in, rows, cols, ld_in, amax, out0, out1, ld_out, transpose, scale_out, st, sms,
+                                   *pro);
+  return launch_cast<KIND, false>(in, rows, cols, ld_in, amax, out0, out1, ld_out, transpose, scale_out, st, sms,
+                                  EwProg{});
+}
+
+// Y = prog(X) over a rank-4 (padded) strided tensor: one element per thread
+// per step, grid-stride.  `dense`: X, Y and the operands are one contiguous
+// run, handled as float4 (the element offset is the flat index).
+__global__ void ew_dense_kernel(const float* x, float* y, int64_t n,
+                                const __grid_constant__ EwProg prog) {
+  const int64_t n4 = n / 4;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+    const float4 v = reinterpret_cast<const float4*>(x)[i];
+    float4 o;
+    o.x = ew_run(prog, v.x, 4 * i);
+    o.y = ew_run(prog, v.y, 4 * i + 1);
+    o.z = ew_run(prog, v.z, 4 * i + 2);
+    o.w = ew_run(prog, v.w, 4 * i + 3);
+    reinterpret_cast<float4*>(y)[i] = o;
+  }
+  for (int64_t i = 4 * n4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    y[i] = ew_run(prog, x[i], i);
+}
+
+struct Strided4 {
+  int64_t shape[4];
+  int64_t sx[4], sy[4];
+};
+
+__global__ void ew_strided_kernel(const float* x, float* y, int64_t n, const __grid_constant__ Strided4 g,
+                                  const __grid_constant__ EwProg prog) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t r = i, ox = 0, oy = 0;
+#pragma unroll
+    for (int d = 3; d >= 0; --d) {
+      const int64_t id = r % g.shape[d];
+      r /= g.shape[d];
+      ox += id * g.sx[d];
+      oy += id * g.sy[d];
+    }
+    y[oy] = ew_run(prog, x[ox], oy);
+  }
 }
 
 }  // namespace
@@ -317,7 +401,7 @@ nk_status launch_cast(const float* in, int64_t rows, int64_t cols, int64_t ld_in
 size_t prep_amax_ws(int64_t) { return kAmaxBlocks * sizeof(float); }
 
 nk_status prep_amax(const float* x, int64_t rows, int64_t cols, int64_t ld, float* amax, void* ws,
-                    size_t ws_bytes, cudaStream_t st) {
+                    size_t ws_bytes, cudaStream_t st, const EwProg* pro) {
   if (!amax) return fail(NK_ERR_INVALID_ARG, "amax: null pointer");
   if (rows * cols == 0) {   // max over nothing: 0 (the scale then falls back to 1)
     cudaError_t e = cudaMemsetAsync(amax, 0, sizeof(float), st);
@@ -326,7 +410,10 @@ nk_status prep_amax(const float* x, int64_t rows, int64_t cols, int64_t ld, floa
   if (!x) return fail(NK_ERR_INVALID_ARG, "amax: null pointer");
   if (!ws || ws_bytes < prep_amax_ws(rows * cols))
     return fail(NK_ERR_WORKSPACE, "amax needs %zu bytes of workspace", prep_amax_ws(rows * cols));
-  amax_stage1<<<kAmaxBlocks, 256, 0, st>>>(x, rows, cols, ld, static_cast<float*>(ws));
+  if (pro && pro->n)
+    amax_stage1<true><<<kAmaxBlocks, 256, 0, st>>>(x, rows, cols, ld, static_cast<float*>(ws), *pro);
+  else
+    amax_stage1<false><<<kAmaxBlocks, 256, 0, st>>>(x, rows, cols, ld, static_cast<float*>(ws), EwProg{});
   nk_status s = check_launch("amax_stage1");
   if (s != NK_OK) return s;
   amax_stage2<<<1, 1024, 0, st>>>(static_cast<float*>(ws), kAmaxBlocks, amax);
@@ -335,17 +422,49 @@ nk_status prep_amax(const float* x, int64_t rows, int64_t cols, int64_t ld, floa
 
 nk_status prep_cast(int kind, const float* in, int64_t rows, int64_t cols, int64_t ld_in,
                     const float* amax, void* out0, void* out1, int64_t ld_out, int transpose,
-                    float* scale_out, cudaStream_t st) {
+                    float* scale_out, cudaStream_t st, const EwProg* pro) {
   int sms = 0;
   nk_status s = require_device(&sms);
   if (s != NK_OK) return s;
   if (rows <= 0 || cols <= 0) return NK_OK;
   switch (kind) {
-    case 0: return launch_cast<0>(in, rows, cols, ld_in, amax, out0, out1, ld_out, transpose, scale_out, st, sms);
-    case 1: return launch_cast<1>(in, rows, cols, ld_in, amax, out0, out1, ld_out, transpose, scale_out, st, sms);
-    case 2: return launch_cast<2>(in, rows, cols, ld_in, amax, out0, out1, ld_out, transpose, scale_out, st, sms);
+    case 0: return launch_cast<0>(in, rows, cols, ld_in, amax, out0, out1, ld_out, transpose, scale_out, st, sms, pro);
+    case 1: return launch_cast<1>(in, rows, cols, ld_in, amax, out0, out1, ld_out, transpose, scale_out, st, sms, pro);
+    case 2: return launch_cast<2>(in, rows, cols, ld_in, amax, out0, out1, ld_out, transpose, scale_out, st, sms, pro);
     default: return fail(NK_ERR_INVALID_ARG, "unknown cast kind %d", kind);
   }
+}
+
+nk_status ew_tensor(const float* x, const int64_t* sx, float* y, const int64_t* sy, const int64_t* shape, int rank,
+                    const EwProg& prog, cudaStream_t st) {
+  int sms = 0;
+  nk_status s = require_device(&sms);
+  if (s != NK_OK) return s;
+  Strided4 g{};
+  int64_t n = 1;
+  for (int d = 0; d < 4; ++d) {
+    const int src = d - (4 - rank);   // leading dimensions pad to extent 1
+    g.shape[d] = src >= 0 ? shape[src] : 1;
+    g.sx[d] = src >= 0 ? sx[src] : 0;
+    g.sy[d] = src >= 0 ? sy[src] : 0;
+    n *= g.shape[d];
+  }
+  if (n == 0) return NK_OK;
+  // dense row-major X and Y with the same strides: one flat run
+  bool dense = true;
+  int64_t run = 1;
+  for (int d = 3; d >= 0; --d) {
+    if (g.shape[d] != 1 && (g.sx[d] != run || g.sy[d] != run)) dense = false;
+    run *= g.shape[d];
+  }
+  const int64_t per = dense ? (n + 3) / 4 : n;
+  int64_t blocks = (per + 255) / 256;
+  if (blocks > (int64_t)sms * 16) blocks = (int64_t)sms * 16;
+  if (blocks < 1) blocks = 1;
+  const bool al = ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 15) == 0;
+  if (dense && al) ew_dense_kernel<<<(unsigned)blocks, 256, 0, st>>>(x, y, n, prog);
+  else ew_strided_kernel<<<(unsigned)blocks, 256, 0, st>>>(x, y, n, g, prog);
+  return check_launch("elementwise kernel");
 }
 
 size_t norm_ws(int64_t, int64_t) { return 2 * kNormBlocks * sizeof(double); }

@@ -33,8 +33,9 @@ struct KArgs {
   float* partial;   // [splits][M][N] or null
 };
 
-// Implicit im2col element A[m,k] of the convolution (0 outside the input).
-__device__ __forceinline__ float conv_a(const SimtGemm& p, int m, int k) {
+// Implicit im2col element A[m,k] of the convolution (0 outside the input);
+// *off = its offset in the input, or -1 for the zero padding.
+__device__ __forceinline__ float conv_a(const SimtGemm& p, int m, int k, int64_t* off) {
   const ConvGeom& g = p.conv;
   int ow = m % g.ow;
   int t = m / g.ow;
@@ -46,12 +47,17 @@ __device__ __forceinline__ float conv_a(const SimtGemm& p, int m, int k) {
   int kh = tap / g.kw;
   int ih = oh * g.sh + kh * g.dh - g.pt;
   int iw = ow * g.sw + kw * g.dw - g.pl;
-  if (ih < 0 || ih >= g.h || iw < 0 || iw >= g.w) return 0.f;
-  return p.A[n * g.sin_n + ih * g.sin_h + iw * g.sin_w + c];
+  if (ih < 0 || ih >= g.h || iw < 0 || iw >= g.w) {
+    *off = -1;
+    return 0.f;
+  }
+  *off = n * g.sin_n + ih * g.sin_h + iw * g.sin_w + c;
+  return p.A[*off];
 }
 
-// Four consecutive k (same tap, since C % 4 == 0) of conv row m.
-__device__ __forceinline__ float4 conv_a4(const SimtGemm& p, int m, int k) {
+// Four consecutive k (same tap, since C % 4 == 0) of conv row m; *off as
+// for conv_a, for the first of the four.
+__device__ __forceinline__ float4 conv_a4(const SimtGemm& p, int m, int k, int64_t* off) {
   const ConvGeom& g = p.conv;
   int ow = m % g.ow;
   int t = m / g.ow;
@@ -63,12 +69,24 @@ __device__ __forceinline__ float4 conv_a4(const SimtGemm& p, int m, int k) {
   int kh = tap / g.kw;
   int ih = oh * g.sh + kh * g.dh - g.pt;
   int iw = ow * g.sw + kw * g.dw - g.pl;
-  if (ih < 0 || ih >= g.h || iw < 0 || iw >= g.w) return make_float4(0.f, 0.f, 0.f, 0.f);
-  return __ldg(reinterpret_cast<const float4*>(p.A + n * g.sin_n + ih * g.sin_h + iw * g.sin_w + c));
+  if (ih < 0 || ih >= g.h || iw < 0 || iw >= g.w) {
+    *off = -1;
+    return make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  *off = n * g.sin_n + ih * g.sin_h + iw * g.sin_w + c;
+  return __ldg(reinterpret_cast<const float4*>(p.A + *off));
+}
+
+// Prologue on four loaded values whose offsets are off, off+d, off+2d, off+3d.
+__device__ __forceinline__ void pro4(const EwProg& e, float4& v, int64_t off, int64_t d) {
+  v.x = ew_run(e, v.x, off);
+  v.y = ew_run(e, v.y, off + d);
+  v.z = ew_run(e, v.z, off + 2 * d);
+  v.w = ew_run(e, v.w, off + 3 * d);
 }
 
 template <int RM, int RN, int AM, int BMD>
-__global__ void __launch_bounds__(THREADS, 2) simt_gemm_kernel(KArgs args) {
+__global__ void __launch_bounds__(THREADS, 2) simt_gemm_kernel(const __grid_constant__ KArgs args) {
   constexpr int BM = 64 * RM;
   constexpr int BN = 64 * RN;
   constexpr int APAD = 4;
@@ -99,10 +117,12 @@ __global__ void __launch_bounds__(THREADS, 2) simt_gemm_kernel(KArgs args) {
         int m = m0 + row, k = k0 + kq;
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
         if (m < p.M && k < kend) {
+          int64_t off = (int64_t)m * p.sam + k;
           if constexpr (AM == A_KVEC)
-            v = __ldg(reinterpret_cast<const float4*>(p.A + (int64_t)m * p.sam + k));
+            v = __ldg(reinterpret_cast<const float4*>(p.A + off));
           else
-            v = conv_a4(p, m, k);
+            v = conv_a4(p, m, k, &off);
+          if (p.pro_a.n && off >= 0) pro4(p.pro_a, v, off, 1);
         }
         ra[4 * j + 0] = v.x; ra[4 * j + 1] = v.y; ra[4 * j + 2] = v.z; ra[4 * j + 3] = v.w;
       }
@@ -113,8 +133,10 @@ __global__ void __launch_bounds__(THREADS, 2) simt_gemm_kernel(KArgs args) {
         int kk = L / (BM / 4), mq = (L % (BM / 4)) * 4;
         int m = m0 + mq, k = k0 + kk;
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (m < p.M && k < kend)
+        if (m < p.M && k < kend) {
           v = __ldg(reinterpret_cast<const float4*>(p.A + (int64_t)k * p.sak + m));
+          if (p.pro_a.n) pro4(p.pro_a, v, (int64_t)k * p.sak + m, 1);
+        }
         ra[4 * j + 0] = v.x; ra[4 * j + 1] = v.y; ra[4 * j + 2] = v.z; ra[4 * j + 3] = v.w;
       }
     } else {
@@ -125,8 +147,10 @@ __global__ void __launch_bounds__(THREADS, 2) simt_gemm_kernel(KArgs args) {
         int m = m0 + row, k = k0 + kk;
         float v = 0.f;
         if (m < p.M && k < kend) {
-          if constexpr (AM == A_CONV_SCALAR) v = conv_a(p, m, k);
-          else v = p.A[(int64_t)m * p.sam + (int64_t)k * p.sak];
+          int64_t off = (int64_t)m * p.sam + (int64_t)k * p.sak;
+          if constexpr (AM == A_CONV_SCALAR) v = conv_a(p, m, k, &off);
+          else v = p.A[off];
+          if (p.pro_a.n && off >= 0) v = ew_run(p.pro_a, v, off);
         }
         ra[j] = v;
       }
@@ -165,8 +189,10 @@ __global__ void __launch_bounds__(THREADS, 2) simt_gemm_kernel(KArgs args) {
         int kk = L / (BN / 4), nq = (L % (BN / 4)) * 4;
         int n = n0 + nq, k = k0 + kk;
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (n < p.N && k < kend)
+        if (n < p.N && k < kend) {
           v = __ldg(reinterpret_cast<const float4*>(p.B + (int64_t)k * p.sbk + n));
+          if (p.pro_b.n) pro4(p.pro_b, v, (int64_t)k * p.sbk + n, 1);
+        }
         rb[4 * j + 0] = v.x; rb[4 * j + 1] = v.y; rb[4 * j + 2] = v.z; rb[4 * j + 3] = v.w;
       }
     } else if constexpr (BMD == B_KVEC) {
@@ -176,8 +202,10 @@ __global__ void __launch_bounds__(THREADS, 2) simt_gemm_kernel(KArgs args) {
         int col = L / 4, kq = (L % 4) * 4;
         int n = n0 + col, k = k0 + kq;
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (n < p.N && k < kend)
+        if (n < p.N && k < kend) {
           v = __ldg(reinterpret_cast<const float4*>(p.B + (int64_t)n * p.sbn + k));
+          if (p.pro_b.n) pro4(p.pro_b, v, (int64_t)n * p.sbn + k, 1);
+        }
         rb[4 * j + 0] = v.x; rb[4 * j + 1] = v.y; rb[4 * j + 2] = v.z; rb[4 * j + 3] = v.w;
       }
     } else {
@@ -186,7 +214,13 @@ __global__ void __launch_bounds__(THREADS, 2) simt_gemm_kernel(KArgs args) {
         int L = tid + j * THREADS;
         int col = L % BN, kk = L / BN;
         int n = n0 + col, k = k0 + kk;
-        rb[j] = (n < p.N && k < kend) ? p.B[(int64_t)k * p.sbk + (int64_t)n * p.sbn] : 0.f;
+        float v = 0.f;
+        if (n < p.N && k < kend) {
+          const int64_t off = (int64_t)k * p.sbk + (int64_t)n * p.sbn;
+          v = p.B[off];
+          if (p.pro_b.n) v = ew_run(p.pro_b, v, off);
+        }
+        rb[j] = v;
       }
     }
   };
@@ -285,6 +319,7 @@ __global__ void __launch_bounds__(THREADS, 2) simt_gemm_kernel(KArgs args) {
           if (p.beta != 0.f) o = fmaf(p.beta, p.C[(int64_t)m * p.scm + (int64_t)n * p.scn], o);
           if (p.bias) o += p.bias[p.bias_on_m ? m : n];
           if (p.relu) o = (o > 0.f || o != o) ? o : 0.f;
+          if (p.ew.n) o = ew_run(p.ew, o, (int64_t)m * p.scm + (int64_t)n * p.scn);
         }
         v[j] = o;
       }
@@ -303,7 +338,7 @@ __global__ void __launch_bounds__(THREADS, 2) simt_gemm_kernel(KArgs args) {
 // Split-K reduce: lanes of a warp form groups of S (a power of two); lane
 // s of a group reads slice s of one output, the group sums with an xor
 // shuffle tree (same order every run), lane 0 applies the epilogue.
-__global__ void splitk_reduce_kernel(SplitReduce r, int S) {
+__global__ void splitk_reduce_kernel(const __grid_constant__ SplitReduce r, int S) {
   const int lane = threadIdx.x & 31;
   const int per_warp = 32 / S;
   const int s = lane % S;
@@ -325,6 +360,7 @@ __global__ void splitk_reduce_kernel(SplitReduce r, int S) {
       if (r.beta != 0.f) o = fmaf(r.beta, *c, o);
       if (r.bias) o += r.bias[r.bias_on_m ? m : n];
       if (r.relu) o = (o > 0.f || o != o) ? o : 0.f;
+      if (r.ew.n) o = ew_run(r.ew, o, (int64_t)m * r.scm + (int64_t)n * r.scn);
       *c = o;
     }
   }
@@ -400,7 +436,7 @@ nk_status simt_gemm(const SimtGemm& p, int tile, int splits, void* ws, size_t ws
   nk_status s = tile == 128 ? launch_a<2, 2>(a, amode, bmode, grid, st)
                             : launch_a<1, 1>(a, amode, bmode, grid, st);
   if (s != NK_OK || splits == 1) return s;
-  SplitReduce r;
+  SplitReduce r{};
   r.partial = a.partial;
   r.splits = splits;
   r.M = p.M;
@@ -415,6 +451,7 @@ nk_status simt_gemm(const SimtGemm& p, int tile, int splits, void* ws, size_t ws
   r.relu = p.relu;
   r.scale_a = nullptr;
   r.scale_b = nullptr;
+  r.ew = p.ew;
   return splitk_reduce(r, st);
 }
 

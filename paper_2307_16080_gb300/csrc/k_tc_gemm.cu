@@ -95,6 +95,7 @@ struct TcParams {
   // epilogue through shared memory and TMA stores (plain GEMM, beta = 0, one K slice)
   CUtensorMap tmC;
   int c_tma;
+  EwProg ew;                    // fused elementwise program (offsets from C), single launches
 };
 
 // Epilogue staging: one 32 x 32 FP32 box (4 KB, 128B-swizzled) per epilogue warp.
@@ -570,6 +571,7 @@ __global__ void __launch_bounds__(WIDE ? 320 : 192, 1) tc_gemm_kernel(const __gr
               if (beta != 0.f) x = fmaf(beta, ci[e], x);
               if (t.bias) x += p.bias_on_m ? bm : __ldg(t.bias + col0 + j + e);
               if (t.relu) x = (x > 0.f || x != x) ? x : 0.f;
+              if (p.ew.n) x = ew_run(p.ew, x, (int64_t)row * t.ldc + col0 + j + e);
               o[e] = x;
             }
             *reinterpret_cast<float4*>(dst + j) = make_float4(o[0], o[1], o[2], o[3]);
@@ -582,6 +584,7 @@ __global__ void __launch_bounds__(WIDE ? 320 : 192, 1) tc_gemm_kernel(const __gr
             if (beta != 0.f) x = fmaf(beta, dst[j], x);
             if (t.bias) x += p.bias_on_m ? bm : __ldg(t.bias + col0 + j);
             if (t.relu) x = (x > 0.f || x != x) ? x : 0.f;
+            if (p.ew.n) x = ew_run(p.ew, x, (int64_t)row * t.ldc + col0 + j);
             dst[j] = x;
           }
         }
@@ -768,6 +771,7 @@ nk_status tc_gemm(const TcGemm& g, const nk_schedule& s, void* ws, size_t ws_byt
     z.bias = g.bias; z.bias_on_m = g.bias_on_m;
     z.M = g.M; z.N = g.N; z.K = 0;
     z.alpha = 1.f; z.beta = g.beta; z.relu = g.relu;
+    z.ew = g.ew;
     return simt_gemm(z, 64, 1, nullptr, 0, st);
   }
   const bool fp8 = g.kind == TC_FP8;
@@ -812,13 +816,15 @@ nk_status tc_gemm(const TcGemm& g, const nk_schedule& s, void* ws, size_t ws_byt
   p.alpha = g.alpha;
   p.scale_a = g.scale_a;
   p.scale_b = g.scale_b;
+  p.ew = g.ew;
   p.budget = wait_budget();
   const bool cvec = ((reinterpret_cast<uintptr_t>(g.C) & 15) == 0) && (g.ldc % 4 == 0) &&
                     (splits == 1 || (g.N % 4 == 0 && (reinterpret_cast<uintptr_t>(ws) & 15) == 0));
   p.c_vec = cvec ? 1 : 0;
   // TMA-store epilogue: plain overwrite of a 16-byte aligned C in one K slice.
   p.c_tma = 0;
-  if (mch == 1 && splits == 1 && g.beta == 0.f && (reinterpret_cast<uintptr_t>(g.C) & 15) == 0 && (g.ldc * 4) % 16 == 0) {
+  if (mch == 1 && splits == 1 && g.beta == 0.f && g.ew.n == 0 && (reinterpret_cast<uintptr_t>(g.C) & 15) == 0 &&
+      (g.ldc * 4) % 16 == 0) {
     auto fn = encode_fn();
     cuuint64_t dims[2] = {(cuuint64_t)g.N, (cuuint64_t)g.M};
     cuuint64_t strides[1] = {(cuuint64_t)(g.ldc * 4)};
@@ -858,7 +864,7 @@ nk_status tc_gemm(const TcGemm& g, const nk_schedule& s, void* ws, size_t ws_byt
     default: status = launch<TC_BF16X3, 2, false, false, true>(p, grid, smem, st); break;
   }
   if (status != NK_OK || splits == 1) return status;
-  SplitReduce r;
+  SplitReduce r{};
   r.partial = p.partial;
   r.splits = splits;
   r.M = g.M;
@@ -873,6 +879,7 @@ nk_status tc_gemm(const TcGemm& g, const nk_schedule& s, void* ws, size_t ws_byt
   r.relu = g.relu;
   r.scale_a = g.scale_a;
   r.scale_b = g.scale_b;
+  r.ew = g.ew;
   return splitk_reduce(r, st);
 }
 
@@ -1062,6 +1069,7 @@ nk_status tc_conv(const TcConv& c, const nk_schedule& s, void* ws, size_t ws_byt
   p.alpha = 1.f;
   p.scale_a = c.scale_i;   // E4M3: alpha = 1 / (s_i * s_w), read on the device
   p.scale_b = c.scale_w;
+  p.ew = c.ew;
   p.budget = wait_budget();
   p.c_vec = ((reinterpret_cast<uintptr_t>(c.O) & 15) == 0 && c.F % 4 == 0 &&
              (splits == 1 || (reinterpret_cast<uintptr_t>(ws) & 15) == 0)) ? 1 : 0;
@@ -1096,6 +1104,7 @@ nk_status tc_conv(const TcConv& c, const nk_schedule& s, void* ws, size_t ws_byt
   r.relu = c.relu;
   r.scale_a = c.scale_i;
   r.scale_b = c.scale_w;
+  r.ew = c.ew;
   return splitk_reduce(r, st);
 }
 

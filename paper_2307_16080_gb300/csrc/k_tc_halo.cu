@@ -92,6 +92,7 @@ struct HaloParams {
   float beta;
   int c_vec;
   int64_t budget;
+  EwProg ew;             // fused elementwise program (offsets from O)
 };
 
 // First GEMM row a tap reads: tap (kh, kw) sees the window kh*dh rows down
@@ -276,7 +277,8 @@ __global__ void __launch_bounds__(kThreads, 1) halo_conv_kernel(const __grid_con
         const int y = r / t.P, x = r - y * t.P;
         const int n = tb * t.NB + b, oh = th * t.R + y, ow = tw * t.Q + x;
         const bool row_ok = b < t.NB && y < t.R && x < t.Q && n < t.N && oh < t.OH && ow < t.OW;
-        float* orow = p.O + ((int64_t)(n * t.OH + oh) * t.OW + ow) * p.F;
+        const int64_t orow_off = ((int64_t)(n * t.OH + oh) * t.OW + ow) * p.F;
+        float* orow = p.O + orow_off;
         for (int c0 = 0; c0 < p.bn; c0 += 32) {
           float v[32];
           ptx::tmem_ld32(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)acc * acc_cols +
@@ -298,6 +300,7 @@ __global__ void __launch_bounds__(kThreads, 1) halo_conv_kernel(const __grid_con
                 if (p.beta != 0.f) xv = fmaf(p.beta, ci[e], xv);
                 if (p.bias) xv += __ldg(p.bias + col0 + j + e);
                 if (p.relu) xv = (xv > 0.f || xv != xv) ? xv : 0.f;
+                if (p.ew.n) xv = ew_run(p.ew, xv, orow_off + col0 + j + e);
                 o[e] = xv;
               }
               *reinterpret_cast<float4*>(dst + j) = make_float4(o[0], o[1], o[2], o[3]);
@@ -310,6 +313,7 @@ __global__ void __launch_bounds__(kThreads, 1) halo_conv_kernel(const __grid_con
               if (p.beta != 0.f) xv = fmaf(p.beta, dst[j], xv);
               if (p.bias) xv += __ldg(p.bias + col0 + j);
               if (p.relu) xv = (xv > 0.f || xv != xv) ? xv : 0.f;
+              if (p.ew.n) xv = ew_run(p.ew, xv, orow_off + col0 + j);
               dst[j] = xv;
             }
           }
@@ -573,6 +577,7 @@ nk_status tc_halo_conv(const TcConv& c, const nk_schedule& s, cudaStream_t st) {
   p.bias = c.bias;
   p.relu = c.relu;
   p.beta = c.beta;
+  p.ew = c.ew;
   p.c_vec = ((reinterpret_cast<uintptr_t>(c.O) & 15) == 0 && c.F % 4 == 0) ? 1 : 0;
   p.budget = wait_budget();
   if (p.units == 0) return NK_OK;

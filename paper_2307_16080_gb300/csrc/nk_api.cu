@@ -15,6 +15,7 @@
 #include <atomic>
 #include <mutex>
 #include <string>
+#include <utility>
 
 #include "nk_internal.cuh"
 
@@ -99,6 +100,68 @@ int dtype_size(int dt) {
     default: return 0;
   }
 }
+
+}  // namespace
+
+nk_status nk::ew_program(const nk_ew_program* prog, const nk_tensor* like, EwProg* out, const char* what) {
+  *out = EwProg{};
+  if (!prog) return NK_OK;
+  if (prog->n < 0 || prog->n > NK_EW_MAX)
+    return fail(NK_ERR_INVALID_ARG, "%s: %d operations (0..%d allowed)", what, prog->n, NK_EW_MAX);
+  int64_t elems = 1;
+  for (int d = 0; d < like->rank; ++d) elems *= like->shape[d];
+  for (int i = 0; i < prog->n; ++i) {
+    const nk_ew_op& o = prog->ops[i];
+    out->op[i] = o.op;
+    out->a[i] = o.a;
+    out->b[i] = o.b;
+    out->t[i] = nullptr;
+    switch (o.op) {
+      case NK_EW_MUL:
+      case NK_EW_ADD: {
+        const nk_tensor& t = o.t;
+        if (t.dtype != NK_F32) return fail(NK_ERR_INVALID_ARG, "%s op %d: the tensor operand must be FP32", what, i);
+        if (t.rank != like->rank)
+          return fail(NK_ERR_INVALID_ARG, "%s op %d: the tensor operand has rank %d, not %d", what, i, t.rank,
+                      like->rank);
+        for (int d = 0; d < like->rank; ++d)
+          if (t.shape[d] != like->shape[d])
+            return fail(NK_ERR_INVALID_ARG, "%s op %d: the tensor operand's dim %d is %lld, not %lld", what, i, d,
+                        (long long)t.shape[d], (long long)like->shape[d]);
+        for (int d = 0; d < like->rank; ++d) {
+          if (like->shape[d] > 1 && t.stride[d] != like->stride[d])
+            return fail(NK_ERR_INVALID_ARG, "%s op %d: the tensor operand's stride %d is %lld, not %lld", what, i,
+                        d, (long long)t.stride[d], (long long)like->stride[d]);
+        }
+        if (elems > 0 && !t.ptr) return fail(NK_ERR_INVALID_ARG, "%s op %d: NULL tensor operand", what, i);
+        if (reinterpret_cast<uintptr_t>(t.ptr) & 3)
+          return fail(NK_ERR_INVALID_ARG, "%s op %d: the tensor operand is not 4-byte aligned", what, i);
+        out->t[i] = static_cast<const float*>(t.ptr);
+        break;
+      }
+      case NK_EW_AFFINE:
+        if (o.a != o.a || o.b != o.b) return fail(NK_ERR_INVALID_ARG, "%s op %d: NaN coefficient", what, i);
+        break;
+      case NK_EW_CLAMP:
+        if (o.a != o.a || o.b != o.b || !(o.a <= o.b))
+          return fail(NK_ERR_INVALID_ARG, "%s op %d: CLAMP needs a <= b (no NaN)", what, i);
+        break;
+      case NK_EW_RELU:
+      case NK_EW_GELU:
+      case NK_EW_GELU_TANH:
+      case NK_EW_SILU:
+      case NK_EW_SIGMOID:
+      case NK_EW_TANH:
+        break;
+      default:
+        return fail(NK_ERR_INVALID_ARG, "%s op %d: unknown opcode %d", what, i, o.op);
+    }
+  }
+  out->n = prog->n;
+  return NK_OK;
+}
+
+namespace {
 
 // A rank-2 view after normalisation.
 struct View {
@@ -304,13 +367,22 @@ nk_status nk_matmul(const nk_tensor* A, const nk_tensor* B, nk_tensor* C, int32_
   MatmulPlan P;
   nk_status s = plan_matmul(A, B, C, precision, sched, P);
   if (s != NK_OK) return s;
+  const nk_epilogue e0{nullptr, 0, 0, 1.f, 1.f, nullptr, nullptr, nullptr};
+  const nk_epilogue& E = epi ? *epi : e0;
+  // Fused programs; operands swap roles with C column-major (C^T = B^T A^T),
+  // and so do their prologues.  Offsets stay memory offsets of each tensor.
+  EwProg ew, pro_a, pro_b;
+  if ((s = ew_program(E.ew, C, &ew, "ew")) != NK_OK) return s;
+  if ((s = ew_program(E.pro_a, A, &pro_a, "pro_a")) != NK_OK) return s;
+  if ((s = ew_program(E.pro_b, B, &pro_b, "pro_b")) != NK_OK) return s;
+  if (P.bias_on_m) std::swap(pro_a, pro_b);
+  if (P.direct && (pro_a.n || pro_b.n))
+    return fail(NK_ERR_UNSUPPORTED, "operands given as BF16 / E4M3 take no prologue (it runs before the cast)");
   if ((s = require_device()) != NK_OK) return s;
   if (P.total > 0 && (!ws || ws_bytes < P.total))
     return fail(NK_ERR_WORKSPACE, "nk_matmul needs %zu bytes of workspace (got %zu)", P.total, ws_bytes);
   if (ws && !aligned16(ws)) return fail(NK_ERR_MISALIGNED, "workspace must be 16-byte aligned");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const nk_epilogue e0{nullptr, 0, 0, 1.f, 1.f};
-  const nk_epilogue& E = epi ? *epi : e0;
   if (P.M == 0 || P.N == 0) return NK_OK;
   char* w = static_cast<char*>(ws);
 
@@ -323,6 +395,7 @@ nk_status nk_matmul(const nk_tensor* A, const nk_tensor* B, nk_tensor* C, int32_
     g.M = P.M; g.N = P.N; g.K = P.K;
     g.alpha = 1.f; g.beta = E.accumulate ? 1.f : 0.f; g.relu = E.relu;
     g.is_conv = 0;
+    g.ew = ew; g.pro_a = pro_a; g.pro_b = pro_b;
     return simt_gemm(g, P.sched.tile_m, P.sched.split_k, ws, ws_bytes, st);
   }
 
@@ -335,6 +408,7 @@ nk_status nk_matmul(const nk_tensor* A, const nk_tensor* B, nk_tensor* C, int32_
   g.bias = E.bias; g.bias_on_m = P.bias_on_m; g.relu = E.relu;
   g.beta = E.accumulate ? 1.f : 0.f;
   g.alpha = 1.f;
+  g.ew = ew;
   if (P.direct) {
     g.A = P.A.p; g.lda = P.A.s0;
     g.B = P.B.p; g.ldb = P.B.s1;
@@ -360,18 +434,18 @@ nk_status nk_matmul(const nk_tensor* A, const nk_tensor* B, nk_tensor* C, int32_
   if (kind == TC_FP8) {
     void* aw = w + P.off_amax;
     const size_t awb = prep_amax_ws(0);
-    if (a_kmajor) s = prep_amax(Af, P.M, P.K, P.A.s0, scal + 0, aw, awb, st);
-    else s = prep_amax(Af, P.K, P.M, P.A.s1, scal + 0, aw, awb, st);
+    if (a_kmajor) s = prep_amax(Af, P.M, P.K, P.A.s0, scal + 0, aw, awb, st, &pro_a);
+    else s = prep_amax(Af, P.K, P.M, P.A.s1, scal + 0, aw, awb, st, &pro_a);
     if (s != NK_OK) return s;
-    if (b_kmajor) s = prep_amax(Bf, P.N, P.K, P.B.s1, scal + 1, aw, awb, st);
-    else s = prep_amax(Bf, P.K, P.N, P.B.s0, scal + 1, aw, awb, st);
+    if (b_kmajor) s = prep_amax(Bf, P.N, P.K, P.B.s1, scal + 1, aw, awb, st, &pro_b);
+    else s = prep_amax(Bf, P.K, P.N, P.B.s0, scal + 1, aw, awb, st, &pro_b);
     if (s != NK_OK) return s;
   }
-  if (a_kmajor) s = prep_cast(ck, Af, P.M, P.K, P.A.s0, scal + 0, a0, a1, P.ldk, 0, scal + 2, st);
-  else s = prep_cast(ck, Af, P.K, P.M, P.A.s1, scal + 0, a0, a1, P.ldk, 1, scal + 2, st);
+  if (a_kmajor) s = prep_cast(ck, Af, P.M, P.K, P.A.s0, scal + 0, a0, a1, P.ldk, 0, scal + 2, st, &pro_a);
+  else s = prep_cast(ck, Af, P.K, P.M, P.A.s1, scal + 0, a0, a1, P.ldk, 1, scal + 2, st, &pro_a);
   if (s != NK_OK) return s;
-  if (b_kmajor) s = prep_cast(ck, Bf, P.N, P.K, P.B.s1, scal + 1, b0, b1, P.ldk, 0, scal + 3, st);
-  else s = prep_cast(ck, Bf, P.K, P.N, P.B.s0, scal + 1, b0, b1, P.ldk, 1, scal + 3, st);
+  if (b_kmajor) s = prep_cast(ck, Bf, P.N, P.K, P.B.s1, scal + 1, b0, b1, P.ldk, 0, scal + 3, st, &pro_b);
+  else s = prep_cast(ck, Bf, P.K, P.N, P.B.s0, scal + 1, b0, b1, P.ldk, 1, scal + 3, st, &pro_b);
   if (s != NK_OK) return s;
   g.A = a0; g.B = b0; g.A2 = a1; g.B2 = b1;
   g.lda = P.ldk; g.ldb = P.ldk;
@@ -493,14 +567,15 @@ static nk_status plan_tc_conv(const nk_tensor* I, const nk_tensor* W, const nk_t
 // rows): one transposing cast when ldw == C, else one per tap.  ck: 0 BF16,
 // 1 E4M3 scaled by 448 / *amax (the scale written to *scale_out).
 static nk_status pack_weights(int ck, const float* Wf, int taps, int C, int F, int64_t ldw, void* out,
-                              const float* amax, float* scale_out, cudaStream_t st) {
+                              const float* amax, float* scale_out, cudaStream_t st, const EwProg* pro = nullptr) {
   char* wt = static_cast<char*>(out);
   const int esz = ck == 1 ? 1 : 2;
   if (ldw == C)
-    return prep_cast(ck, Wf, (int64_t)taps * C, F, F, amax, wt, nullptr, (int64_t)taps * C, 1, scale_out, st);
+    return prep_cast(ck, Wf, (int64_t)taps * C, F, F, amax, wt, nullptr, (int64_t)taps * C, 1, scale_out, st, pro);
   for (int tap = 0; tap < taps; ++tap) {
+    const EwProg sp = pro ? ew_shift(*pro, (int64_t)tap * C * F) : EwProg{};
     nk_status s = prep_cast(ck, Wf + (int64_t)tap * C * F, C, F, F, amax, wt + (size_t)tap * ldw * esz, nullptr,
-                            (int64_t)taps * ldw, 1, scale_out, st);
+                            (int64_t)taps * ldw, 1, scale_out, st, &sp);
     if (s != NK_OK) return s;
   }
   return NK_OK;
@@ -539,10 +614,16 @@ nk_status nk_conv2d_nhwc_hwcf(const nk_tensor* I, const nk_tensor* W, nk_tensor*
   ConvGeom g;
   nk_status s = plan_conv(I, W, O, stride, dilation, pad, g);
   if (s != NK_OK) return s;
-  if ((s = require_device()) != NK_OK) return s;
-  const nk_epilogue e0{nullptr, 0, 0, 1.f, 1.f};
+  const nk_epilogue e0{nullptr, 0, 0, 1.f, 1.f, nullptr, nullptr, nullptr};
   const nk_epilogue& E = epi ? *epi : e0;
   if (!o_dense(O)) return fail(NK_ERR_UNSUPPORTED, "O must be contiguous NHWC");
+  EwProg ew, pro_i, pro_w;
+  if ((s = ew_program(E.ew, O, &ew, "ew")) != NK_OK) return s;
+  if ((s = ew_program(E.pro_a, I, &pro_i, "pro_a (I)")) != NK_OK) return s;
+  if ((s = ew_program(E.pro_b, W, &pro_w, "pro_b (W)")) != NK_OK) return s;
+  if ((pro_i.n && I->dtype != NK_F32) || (pro_w.n && W->dtype != NK_F32))
+    return fail(NK_ERR_UNSUPPORTED, "a prologue needs an FP32 operand (BF16 / packed operands are already cast)");
+  if ((s = require_device()) != NK_OK) return s;
   if (precision == NK_PREC_BF16 || precision == NK_PREC_FP8) {
     ConvPlan P;
     if ((s = plan_tc_conv(I, W, O, g, precision, sched, P)) != NK_OK) return s;
@@ -561,17 +642,17 @@ nk_status nk_conv2d_nhwc_hwcf(const nk_tensor* I, const nk_tensor* W, nk_tensor*
       void* aw = w + P.off_amax;
       const size_t awb = prep_amax_ws(0);
       if ((s = prep_amax(static_cast<const float*>(I->ptr), (int64_t)g.n * g.h * g.w, g.c, g.c, scal + 0, aw, awb,
-                         st)) != NK_OK)
+                         st, &pro_i)) != NK_OK)
         return s;
-      if ((s = prep_amax(static_cast<const float*>(W->ptr), (int64_t)taps * g.c, F, F, scal + 1, aw, awb, st)) !=
-          NK_OK)
+      if ((s = prep_amax(static_cast<const float*>(W->ptr), (int64_t)taps * g.c, F, F, scal + 1, aw, awb, st,
+                         &pro_w)) != NK_OK)
         return s;
       c.scale_i = scal + 2;
       c.scale_w = scal + 3;
     }
     if (P.cast_i) {
       s = prep_cast(ck, static_cast<const float*>(I->ptr), (int64_t)g.n * g.h * g.w, g.c, g.c,
-                    scal ? scal + 0 : nullptr, w + P.off_i, nullptr, P.Cp, 0, scal ? scal + 2 : nullptr, st);
+                    scal ? scal + 0 : nullptr, w + P.off_i, nullptr, P.Cp, 0, scal ? scal + 2 : nullptr, st, &pro_i);
       if (s != NK_OK) return s;
       c.I = w + P.off_i;
       c.sI_w = P.Cp; c.sI_h = (int64_t)g.w * P.Cp; c.sI_n = (int64_t)g.h * g.w * P.Cp;
@@ -582,7 +663,7 @@ nk_status nk_conv2d_nhwc_hwcf(const nk_tensor* I, const nk_tensor* W, nk_tensor*
     if (P.cast_w) {
       char* wt = w + P.off_w;
       if ((s = pack_weights(ck, static_cast<const float*>(W->ptr), g.kh * g.kw, g.c, F, P.Cp, wt,
-                            scal ? scal + 1 : nullptr, scal ? scal + 3 : nullptr, st)) != NK_OK)
+                            scal ? scal + 1 : nullptr, scal ? scal + 3 : nullptr, st, &pro_w)) != NK_OK)
         return s;
       c.Wt = wt;
       c.ldw = P.Cp;
@@ -596,6 +677,7 @@ nk_status nk_conv2d_nhwc_hwcf(const nk_tensor* I, const nk_tensor* W, nk_tensor*
     c.bias = E.bias;
     c.relu = E.relu;
     c.beta = E.accumulate ? 1.f : 0.f;
+    c.ew = ew;
     return tc_conv(c, P.sched, w + P.off_k, P.kern, st);
   }
   if (precision != NK_PREC_F32 || I->dtype != NK_F32 || W->dtype != NK_F32)
@@ -610,6 +692,7 @@ nk_status nk_conv2d_nhwc_hwcf(const nk_tensor* I, const nk_tensor* W, nk_tensor*
   p.M = g.n * g.oh * g.ow; p.N = (int)W->shape[3]; p.K = g.kh * g.kw * g.c;
   p.alpha = 1.f; p.beta = E.accumulate ? 1.f : 0.f; p.relu = E.relu;
   p.is_conv = 1; p.conv = g;
+  p.ew = ew; p.pro_a = pro_i; p.pro_b = pro_w;
   int tile = sched && sched->tile_m > 0 ? sched->tile_m : 64;
   int split = sched && sched->split_k > 0 ? sched->split_k : 1;
   return simt_gemm(p, tile, split, ws, ws_bytes, static_cast<cudaStream_t>(stream));
@@ -629,6 +712,29 @@ nk_status nk_conv2d_pack_weights(const nk_tensor* W, void* Wp, int64_t ldw, void
   if (s != NK_OK) return s;
   return pack_weights(0, static_cast<const float*>(W->ptr), (int)(W->shape[0] * W->shape[1]), (int)W->shape[2],
                       (int)W->shape[3], ldw, Wp, nullptr, nullptr, static_cast<cudaStream_t>(stream));
+}
+
+// ------------------------------------------------------------- elementwise
+nk_status nk_elementwise(const nk_tensor* X, nk_tensor* Y, const nk_ew_program* prog, void* stream) {
+  if (!X || !Y) return fail(NK_ERR_INVALID_ARG, "X and Y must be non-NULL");
+  if (X->rank < 1 || X->rank > 4 || Y->rank != X->rank)
+    return fail(NK_ERR_INVALID_ARG, "X and Y need the same rank, 1..4");
+  if (X->dtype != NK_F32 || Y->dtype != NK_F32) return fail(NK_ERR_UNSUPPORTED, "X and Y must be FP32");
+  int64_t n = 1;
+  for (int d = 0; d < X->rank; ++d) {
+    if (X->shape[d] < 0 || X->shape[d] != Y->shape[d])
+      return fail(NK_ERR_INVALID_ARG, "X and Y shapes differ (dim %d)", d);
+    n *= X->shape[d];
+  }
+  if (n > 0 && (!X->ptr || !Y->ptr)) return fail(NK_ERR_INVALID_ARG, "NULL data pointer");
+  if (((reinterpret_cast<uintptr_t>(X->ptr) | reinterpret_cast<uintptr_t>(Y->ptr)) & 3))
+    return fail(NK_ERR_INVALID_ARG, "X and Y must be 4-byte aligned");
+  EwProg e;
+  nk_status s = ew_program(prog, Y, &e, "prog");
+  if (s != NK_OK) return s;
+  if ((s = require_device()) != NK_OK) return s;
+  return ew_tensor(static_cast<const float*>(X->ptr), X->stride, static_cast<float*>(Y->ptr), Y->stride, Y->shape,
+                   Y->rank, e, static_cast<cudaStream_t>(stream));
 }
 
 // ------------------------------------------------------------- operand prep

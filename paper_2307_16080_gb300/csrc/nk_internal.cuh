@@ -12,6 +12,7 @@
 #include <string>
 
 #include "../../include/nk.h"
+#include "ew.cuh"
 
 namespace nk {
 
@@ -68,6 +69,8 @@ struct SimtGemm {
   int relu;
   int is_conv;           // A is the implicit im2col matrix of `conv`
   ConvGeom conv;
+  EwProg ew;             // epilogue program (offsets from C)
+  EwProg pro_a, pro_b;   // prologues on the loaded A / B (offsets from A, B; conv: from I)
 };
 
 // tile: 128 or 64 (square CTA tile); splits >= 1.  When splits > 1 the
@@ -90,17 +93,28 @@ struct SplitReduce {
   int relu;
   const float* scale_a;  // when set, alpha = 1/(*scale_a * *scale_b) (device scalars)
   const float* scale_b;
+  EwProg ew;             // epilogue program (offsets from C)
 };
 nk_status splitk_reduce(const SplitReduce& r, cudaStream_t st);
 
+// Converts a fused elementwise program (nk.h rules) whose tensor operands must
+// have the rank, shape and strides of `like`; NULL gives the empty program.
+// `what` names the program in error messages.
+nk_status ew_program(const nk_ew_program* prog, const nk_tensor* like, EwProg* out, const char* what);
+
 // ------------------------------------------------------------- prep / norm
+// `pro` (optional): a prologue program run on each element (offsets from x /
+// in) before the amax or the cast sees it.
 nk_status prep_amax(const float* x, int64_t rows, int64_t cols, int64_t ld, float* amax,
-                    void* ws, size_t ws_bytes, cudaStream_t st);
+                    void* ws, size_t ws_bytes, cudaStream_t st, const EwProg* pro = nullptr);
 size_t prep_amax_ws(int64_t n);
 // kind: 0 = bf16, 1 = fp8 (scale from *amax), 2 = bf16 hi/lo pair
 nk_status prep_cast(int kind, const float* in, int64_t rows, int64_t cols, int64_t ld_in,
                     const float* amax, void* out0, void* out1, int64_t ld_out, int transpose,
-                    float* scale_out, cudaStream_t st);
+                    float* scale_out, cudaStream_t st, const EwProg* pro = nullptr);
+// Y = prog(X) over a rank-r strided tensor (nk_elementwise).
+nk_status ew_tensor(const float* x, const int64_t* sx, float* y, const int64_t* sy, const int64_t* shape,
+                    int rank, const EwProg& prog, cudaStream_t st);
 nk_status norm_sumsq(const float* C, int64_t ldc, const double* R, int64_t ldr, int64_t M,
                      int64_t N, double* out, void* ws, size_t ws_bytes, cudaStream_t st);
 size_t norm_ws(int64_t M, int64_t N);
@@ -133,6 +147,7 @@ struct TcGemm {
   float alpha;
   const float* scale_a;   // device scalars (FP8 computed on device) or null
   const float* scale_b;
+  EwProg ew;              // epilogue program (offsets from C)
 };
 
 nk_status tc_gemm(const TcGemm& g, const nk_schedule& s, void* ws, size_t ws_bytes,
@@ -160,6 +175,7 @@ struct TcConv {
   float beta;
   const float* scale_i;
   const float* scale_w;
+  EwProg ew;              // epilogue program (offsets from O)
 };
 // tc_conv dispatches a window schedule (see below) to tc_halo_conv.
 nk_status tc_conv(const TcConv& c, const nk_schedule& s, void* ws, size_t ws_bytes, cudaStream_t st);

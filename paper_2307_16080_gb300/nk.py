@@ -34,9 +34,23 @@ class nk_tensor(ctypes.Structure):
                 ("shape", ctypes.c_int64 * 4), ("stride", ctypes.c_int64 * 4)]
 
 
+NK_EW_MAX = 4
+EW_OPS = {"mul": 1, "add": 2, "affine": 3, "relu": 4, "gelu": 5, "gelu_tanh": 6, "silu": 7, "sigmoid": 8,
+          "tanh": 9, "clamp": 10}
+
+
+class nk_ew_op(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int32), ("a", ctypes.c_float), ("b", ctypes.c_float), ("t", nk_tensor)]
+
+
+class nk_ew_program(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("ops", nk_ew_op * NK_EW_MAX)]
+
+
 class nk_epilogue(ctypes.Structure):
     _fields_ = [("bias", ctypes.c_void_p), ("relu", ctypes.c_int32), ("accumulate", ctypes.c_int32),
-                ("scale_a", ctypes.c_float), ("scale_b", ctypes.c_float)]
+                ("scale_a", ctypes.c_float), ("scale_b", ctypes.c_float), ("ew", ctypes.c_void_p),
+                ("pro_a", ctypes.c_void_p), ("pro_b", ctypes.c_void_p)]
 
 
 class nk_schedule(ctypes.Structure):
@@ -95,6 +109,7 @@ SIGNATURES = {
     "nk_sync_status": (_I32, [_P]),
     "nk_set_wait_budget": (_I32, [_I64]),
     "nk_device_info": (_I32, [ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
+    "nk_elementwise": (_I32, [_PT, _PT, ctypes.POINTER(nk_ew_program), _P]),
 }
 
 _lib = None
@@ -156,13 +171,44 @@ def _sched(schedule):
     return ctypes.byref(nk_schedule(*schedule))
 
 
-def _epi(bias, relu, accumulate, scale_a, scale_b):
+def make_ew_program(spec) -> nk_ew_program | None:
+    """An nk_ew_program from a list of steps, each a tuple: ("mul", T),
+    ("add", T), ("affine", a, b), ("clamp", lo, hi) or (name,) for "relu",
+    "gelu", "gelu_tanh", "silu", "sigmoid", "tanh".  T: an FP32 CUDA tensor
+    with the shape and strides of the tensor the program runs over.  The
+    caller keeps the T tensors alive until the call's kernels have run."""
+    if spec is None:
+        return None
+    prog = nk_ew_program()
+    spec = list(spec)
+    prog.n = len(spec)   # above NK_EW_MAX the library rejects the count
+    for i, step in enumerate(spec[:NK_EW_MAX]):
+        name, *args = step
+        op = prog.ops[i]
+        op.op = EW_OPS.get(name, -1) if isinstance(name, str) else int(name)
+        if name in ("mul", "add"):
+            op.t = as_nk_tensor(args[0])
+        elif name in ("affine", "clamp"):
+            op.a, op.b = float(args[0]), float(args[1])
+    return prog
+
+
+def _epi(bias, relu, accumulate, scale_a, scale_b, ew=None, pro_a=None, pro_b=None):
+    """The epilogue struct plus the program structs it points to (returned so
+    that they outlive the call)."""
     e = nk_epilogue()
     e.bias = bias.data_ptr() if bias is not None else None
     e.relu = int(bool(relu))
     e.accumulate = int(bool(accumulate))
     e.scale_a = float(scale_a)
     e.scale_b = float(scale_b)
+    keep = []
+    for field, spec in (("ew", ew), ("pro_a", pro_a), ("pro_b", pro_b)):
+        prog = make_ew_program(spec)
+        if prog is not None:
+            keep.append(prog)
+            setattr(e, field, ctypes.addressof(prog))
+    e._keep = keep
     return e
 
 
@@ -181,12 +227,13 @@ def workspace(nbytes: int, device=None) -> torch.Tensor | None:
 
 
 def nk_matmul(A, B, C, precision="f32", bias=None, relu=False, accumulate=False, scale_a=1.0,
-              scale_b=1.0, schedule=None, ws=None, stream=None):
-    """C = ReLU?(accumulate*C + alpha*(A @ B) + bias) through nk_matmul."""
+              scale_b=1.0, schedule=None, ws=None, stream=None, ew=None, pro_a=None, pro_b=None):
+    """C = ew(ReLU?(accumulate*C + alpha*(pro_a(A) @ pro_b(B)) + bias)) through
+    nk_matmul; ew / pro_a / pro_b are program step lists (make_ew_program)."""
     ta, tb, tc = as_nk_tensor(A), as_nk_tensor(B), as_nk_tensor(C)
     if ws is None:
         ws = workspace(nk_matmul_workspace_size(A, B, C, precision, schedule), C.device)
-    e = _epi(bias, relu, accumulate, scale_a, scale_b)
+    e = _epi(bias, relu, accumulate, scale_a, scale_b, ew, pro_a, pro_b)
     _check(lib().nk_matmul(ctypes.byref(ta), ctypes.byref(tb), ctypes.byref(tc), PREC[precision],
                            ctypes.byref(e), _sched(schedule), ws.data_ptr() if ws is not None else None,
                            ws.numel() if ws is not None else 0, _stream(stream)))
@@ -211,12 +258,15 @@ def nk_conv2d_workspace_size(I, W, O, stride=(1, 1), dilation=(1, 1), pad=(0, 0,
 
 
 def nk_conv2d_nhwc_hwcf(I, W, O, stride=(1, 1), dilation=(1, 1), pad=(0, 0, 0, 0), precision="f32",
-                        bias=None, relu=False, accumulate=False, schedule=None, ws=None, stream=None):
+                        bias=None, relu=False, accumulate=False, schedule=None, ws=None, stream=None,
+                        ew=None, pro_i=None, pro_w=None):
+    """O = ew(ReLU?(accumulate*O + conv(pro_i(I), pro_w(W)) + bias)); the
+    programs are step lists (make_ew_program), the zero padding stays 0."""
     ti, tw, to = as_nk_tensor(I), as_nk_tensor(W), as_nk_tensor(O)
     st, dl, pd = _conv_args(stride, dilation, pad)
     if ws is None:
         ws = workspace(nk_conv2d_workspace_size(I, W, O, stride, dilation, pad, precision, schedule), O.device)
-    e = _epi(bias, relu, accumulate, 1.0, 1.0)
+    e = _epi(bias, relu, accumulate, 1.0, 1.0, ew, pro_i, pro_w)
     _check(lib().nk_conv2d_nhwc_hwcf(ctypes.byref(ti), ctypes.byref(tw), ctypes.byref(to), st, dl, pd,
                                      PREC[precision], ctypes.byref(e), _sched(schedule),
                                      ws.data_ptr() if ws is not None else None,
@@ -237,14 +287,23 @@ def nk_conv2d_pack_weights(W, ldw=None, stream=None) -> torch.Tensor:
 
 
 def nk_conv2d_nchw_fchw(I, K, O, stride=(1, 1), dilation=(1, 1), pad=(0, 0, 0, 0), bias=None, relu=False,
-                        accumulate=False, stream=None):
+                        accumulate=False, stream=None, ew=None):
     """Direct NCHW / FCHW convolution (Listing "2dnchwconv" layout)."""
     ti, tk, to = as_nk_tensor(I), as_nk_tensor(K), as_nk_tensor(O)
     st, dl, pd = _conv_args(stride, dilation, pad)
-    e = _epi(bias, relu, accumulate, 1.0, 1.0)
+    e = _epi(bias, relu, accumulate, 1.0, 1.0, ew)
     _check(lib().nk_conv2d_nchw_fchw(ctypes.byref(ti), ctypes.byref(tk), ctypes.byref(to), st, dl, pd,
                                      ctypes.byref(e), _stream(stream)))
     return O
+
+
+def nk_elementwise(X, Y, prog, stream=None):
+    """Y = prog(X) elementwise (the GPUModule kernel of Sec. 3.1 as one pass)."""
+    tx, ty = as_nk_tensor(X), as_nk_tensor(Y)
+    p = make_ew_program(prog)
+    _check(lib().nk_elementwise(ctypes.byref(tx), ctypes.byref(ty), ctypes.byref(p) if p is not None else None,
+                                _stream(stream)))
+    return Y
 
 
 def nk_amax(x: torch.Tensor, out: torch.Tensor, ws=None, stream=None):
