@@ -467,6 +467,9 @@ def stack_graph(torch, synth, dev, batch, picks, flop):
         for (i, w, o, st, pad, bias, sched, ws) in calls:
             nk.nk_conv2d_nhwc_hwcf(i, w, o, st, (1, 1), pad, "bf16", bias=bias, relu=True, schedule=sched, ws=ws)
     ms = graph_time(torch, forward, calls=2, reps=10)
+    nk.nk_set_pdl(False)   # the same graph captured with plain stream ordering between kernels
+    ms_serial = graph_time(torch, forward, calls=2, reps=10)
+    nk.nk_set_pdl(True)
     nk.nk_sync_status()
     kernels = sum(2 if sched[5] > 1 else 1 for sched in picks)   # split-K adds its reduce
     # the stack's roofline time: each layer at min(tensor peak, HBM x its arithmetic intensity)
@@ -475,8 +478,10 @@ def stack_graph(torch, synth, dev, batch, picks, flop):
         r = layer_roofline(L["N"], L["H"], L["W"], L["C"], L["F"], L["KH"], L["KW"], L["stride"], L["pad"], 1.0)
         roof_ms += r["flop"] / (r["roofline_tflops"] * 1e12) * 1e3
     return {"ms": ms, "tflops": flop / (ms * 1e-3) / 1e12, "kernels_per_forward": kernels,
+            "ms_without_pdl": ms_serial, "pdl_speedup": ms_serial / ms,
             "roofline_ms": roof_ms, "frac_of_roofline": roof_ms / ms,
-            "how": "20 nk_conv2d calls on packed BF16 weights (one conv kernel each) in one CUDA graph, device time"}
+            "how": "20 nk_conv2d calls on packed BF16 weights (one conv kernel each) in one CUDA graph, device time; "
+                   "ms with programmatic dependent launch (default), ms_without_pdl with nk_set_pdl(0)"}
 
 
 def grouped_conv_report(torch, nk, synth, dev, batch=8):

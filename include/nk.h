@@ -404,6 +404,19 @@ nk_status nk_sync_status(void* stream);
  * 0 restores the default.  Lets a test drive the timeout path on purpose. */
 nk_status nk_set_wait_budget(int64_t iterations);
 
+/* Programmatic dependent launch (on by default).  When on, every kernel of
+ * this library is launched so that it may start while the kernel before it
+ * on the same stream is finishing: it prepares its shared memory, mbarriers
+ * and tensor memory, then waits, on the device, until all earlier work on
+ * the stream has completed and is visible before it reads or writes any
+ * global memory.  Results are identical either way; only the gap between
+ * back-to-back kernels (a stream, or a CUDA graph captured from one)
+ * changes.  The setting is process-wide and is read at each launch, so a
+ * graph keeps the setting it was captured with.  The paper has no
+ * counterpart: it is a launch-latency measure of this GPU.                  */
+nk_status nk_set_pdl(int32_t enabled);
+int32_t nk_get_pdl(void);
+
 /* Number of SMs and the compute capability of the current device.          */
 nk_status nk_device_info(int32_t* sm_count, int32_t* cc_major, int32_t* cc_minor);
 

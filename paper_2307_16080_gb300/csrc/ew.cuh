@@ -64,6 +64,17 @@ static __device__ __noinline__ float ew_run(const EwProg& e, float x, int64_t of
   }
   return x;
 }
+
+// Runs program `e` in place over the n consecutive floats at buf, the values
+// of the elements whose offsets start at off0.  The tensor-core epilogues
+// stage a 32-column segment in a local buffer, call this once, then store:
+// the program reads its operands (which may alias the output) before the
+// store, and the unrolled plain epilogue keeps no call in its body (a call
+// there costs the plain path registers and speed even when no program is
+// given).
+static __device__ __noinline__ void ew_apply(const EwProg& e, float* buf, int n, int64_t off0) {
+  for (int j = 0; j < n; ++j) buf[j] = ew_run(e, buf[j], off0 + j);
+}
 #endif
 
 }  // namespace nk

@@ -55,6 +55,8 @@ struct Direct {
 // stride-1 filter), so many CTAs share an SM and keep enough loads in flight
 // to reach HBM bandwidth.
 __global__ void __launch_bounds__(THREADS) direct_conv_kernel(const __grid_constant__ Direct p) {
+  nk::pdl_wait();      // earlier kernels on the stream have finished
+  nk::pdl_trigger();
   extern __shared__ float smem_f[];
   float* ker = smem_f;                    // [CO_G][64] taps of one input channel
   float* tile = smem_f + CO_G * 64;       // [in_h][in_w] halo tile
@@ -173,6 +175,8 @@ __device__ __forceinline__ void load_segment(const float* src, int64_t sIh, int 
 
 template <int KH, int KW, int CO_G, int ROWS>
 __global__ void __launch_bounds__(128) direct_rows_kernel(const __grid_constant__ Direct p) {
+  nk::pdl_wait();      // earlier kernels on the stream have finished
+  nk::pdl_trigger();
   constexpr int SEG = 4 + KW - 1;
   constexpr int TAPS = KH * KW;
   const int wo = blockIdx.x * 512 + threadIdx.x * 4;   // first of this thread's 4 output columns
@@ -230,7 +234,6 @@ __global__ void __launch_bounds__(128) direct_rows_kernel(const __grid_constant_
         if (p.beta != 0.f && wo + j < p.OW) o = fmaf(p.beta, dst[j], o);
         o += b;
         if (p.relu) o = (o > 0.f || o != o) ? o : 0.f;
-        if (p.ew.n && wo + j < p.OW) o = ew_run(p.ew, o, (dst - p.O) + j);
         v[j] = o;
       }
       const uintptr_t a = reinterpret_cast<uintptr_t>(dst);
@@ -257,7 +260,6 @@ __device__ __forceinline__ void store4(const Direct& p, float* dst, int wo, floa
     if (p.beta != 0.f && wo + j < p.OW) o = fmaf(p.beta, dst[j], o);
     o += b;
     if (p.relu) o = (o > 0.f || o != o) ? o : 0.f;
-    if (p.ew.n && wo + j < p.OW) o = ew_run(p.ew, o, (dst - p.O) + j);
     v[j] = o;
   }
   const uintptr_t ad = reinterpret_cast<uintptr_t>(dst);
@@ -277,6 +279,8 @@ __device__ __forceinline__ void store4(const Direct& p, float* dst, int wo, floa
 // input rows o .. o+KH-1 arrive; it is stored after the last of them.
 template <int KH, int KW, int CO_G>
 __global__ void __launch_bounds__(128) direct_stream_kernel(const __grid_constant__ Direct p, int rpt) {
+  nk::pdl_wait();      // earlier kernels on the stream have finished
+  nk::pdl_trigger();
   constexpr int SEG = 4 + KW - 1;
   constexpr int TAPS = KH * KW;
   const int wo = blockIdx.x * 512 + threadIdx.x * 4;
@@ -350,7 +354,7 @@ nk_status launch_rows(const Direct& p, cudaStream_t st) {
   if ((int64_t)p.N * groups > 65535) return fail(NK_ERR_UNSUPPORTED, "batch x channel groups too large");
   dim3 grid((unsigned)((p.OW + 511) / 512), (unsigned)((p.OH + ROWS - 1) / ROWS), (unsigned)(p.N * groups));
   if (grid.y > 65535) return fail(NK_ERR_UNSUPPORTED, "output too tall");
-  direct_rows_kernel<KH, KW, CO_R, ROWS><<<grid, 128, 0, st>>>(p);
+  (void)nk::launch_k(direct_rows_kernel<KH, KW, CO_R, ROWS>, dim3(grid), dim3(128), 0, st, 1, p);
   return check_launch("direct_rows_kernel");
 }
 
@@ -371,7 +375,7 @@ nk_status launch_stream(const Direct& p, cudaStream_t st) {
   rpt = rpt < 4 ? 4 : rpt > 64 ? 64 : rpt;
   dim3 grid((unsigned)((p.OW + 511) / 512), (unsigned)((p.OH + rpt - 1) / rpt), (unsigned)(p.N * groups));
   if (grid.y > 65535) return fail(NK_ERR_UNSUPPORTED, "output too tall");
-  direct_stream_kernel<KH, KW, CO_R><<<grid, 128, 0, st>>>(p, (int)rpt);
+  (void)nk::launch_k(direct_stream_kernel<KH, KW, CO_R>, dim3(grid), dim3(128), 0, st, 1, p, (int)rpt);
   return check_launch("direct_stream_kernel");
 }
 
@@ -429,12 +433,16 @@ extern "C" nk_status nk_conv2d_nchw_fchw(const nk_tensor* I, const nk_tensor* K,
   if ((s = ew_program(E.ew, O, &p.ew, "ew")) != NK_OK) return s;
   if ((s = require_device()) != NK_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (p.sh == 1 && p.sw == 1 && p.dh == 1 && p.dw == 1 && p.CI == 1) {
+  // The register-streaming kernels carry no epilogue program (a call in
+  // their loops would slow the plain path); a program goes to the general
+  // kernel below.
+  const bool plain = p.ew.n == 0;
+  if (plain && p.sh == 1 && p.sw == 1 && p.dh == 1 && p.dw == 1 && p.CI == 1) {
     if (p.KH == 3 && p.KW == 3) return launch_stream<3, 3>(p, st);
     if (p.KH == 5 && p.KW == 5) return launch_stream<5, 5>(p, st);
     if (p.KH == 1 && p.KW == 1) return launch_stream<1, 1>(p, st);
   }
-  if (p.sh == 1 && p.sw == 1 && p.dh == 1 && p.dw == 1) {
+  if (plain && p.sh == 1 && p.sw == 1 && p.dh == 1 && p.dw == 1) {
     if (p.KH == 3 && p.KW == 3) return launch_rows<3, 3>(p, st);
     if (p.KH == 5 && p.KW == 5) return launch_rows<5, 5>(p, st);
     if (p.KH == 1 && p.KW == 1) return launch_rows<1, 1>(p, st);
@@ -444,6 +452,6 @@ extern "C" nk_status nk_conv2d_nchw_fchw(const nk_tensor* I, const nk_tensor* K,
   dim3 grid((unsigned)((p.OW + TW - 1) / TW), (unsigned)((p.OH + TH - 1) / TH), (unsigned)(p.N * groups));
   if (grid.y > 65535) return fail(NK_ERR_UNSUPPORTED, "output too tall");
   const size_t smem = (size_t)(CO_G * 64 + p.in_h * p.in_w) * sizeof(float);
-  direct_conv_kernel<<<grid, THREADS, smem, st>>>(p);
+  (void)nk::launch_k(direct_conv_kernel, dim3(grid), dim3(THREADS), smem, st, 1, p);
   return check_launch("direct_conv_kernel");
 }

@@ -91,6 +91,8 @@ __device__ void forward_rows(const float* __restrict__ P, const float* __restric
 __global__ void __launch_bounds__(THREADS) mlp_forward_kernel(const float* __restrict__ P,
                                                               const float* __restrict__ X, int64_t B,
                                                               float* __restrict__ y) {
+  nk::pdl_wait();      // earlier kernels on the stream have finished
+  nk::pdl_trigger();
   extern __shared__ __align__(16) uint8_t raw[];
   Smem& s = *reinterpret_cast<Smem*>(raw);
   const int64_t r0 = (int64_t)blockIdx.x * ROWS;
@@ -105,6 +107,8 @@ __global__ void __launch_bounds__(THREADS) mlp_grad_kernel(const float* __restri
                                                            const float* __restrict__ X,
                                                            const float* __restrict__ T, int64_t B,
                                                            float* __restrict__ part) {
+  nk::pdl_wait();      // earlier kernels on the stream have finished
+  nk::pdl_trigger();
   extern __shared__ __align__(16) uint8_t raw[];
   Smem& s = *reinterpret_cast<Smem*>(raw);
   const int64_t r0 = (int64_t)blockIdx.x * ROWS;
@@ -173,6 +177,8 @@ __global__ void __launch_bounds__(THREADS) mlp_grad_kernel(const float* __restri
 // grad[p] = sum_b part[b][p] in block order; loss = sum_b part[b][NPARAM] / B.
 __global__ void mlp_reduce_kernel(const float* __restrict__ part, int nblocks, int64_t B,
                                   float* __restrict__ grad, float* __restrict__ loss) {
+  nk::pdl_wait();      // earlier kernels on the stream have finished
+  nk::pdl_trigger();
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p > NPARAM) return;
   float a = 0.f;
@@ -184,6 +190,8 @@ __global__ void mlp_reduce_kernel(const float* __restrict__ part, int nblocks, i
 __global__ void mlp_adam_kernel(float* __restrict__ P, const float* __restrict__ g, float* __restrict__ m,
                                 float* __restrict__ v, int n, float lr, float b1, float b2, float eps,
                                 float bc1, float bc2) {
+  nk::pdl_wait();      // earlier kernels on the stream have finished
+  nk::pdl_trigger();
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
   const float gp = g[p];
@@ -223,7 +231,7 @@ nk_status nk_mlp_forward(const float* params, const float* X, int64_t B, float* 
   if (!params || !X || !y) return fail(NK_ERR_INVALID_ARG, "null pointer");
   if ((s = set_smem(reinterpret_cast<const void*>(mlp_forward_kernel))) != NK_OK) return s;
   const int64_t nb = (B + ROWS - 1) / ROWS;
-  mlp_forward_kernel<<<(unsigned)nb, THREADS, sizeof(Smem), static_cast<cudaStream_t>(stream)>>>(params, X, B, y);
+  (void)nk::launch_k(mlp_forward_kernel, dim3((unsigned)nb), dim3(THREADS), sizeof(Smem), static_cast<cudaStream_t>(stream), 1, params, X, B, y);
   return check_launch("mlp_forward_kernel");
 }
 
@@ -239,9 +247,9 @@ nk_status nk_mlp_grad(const float* params, const float* X, const float* t, int64
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int64_t nb = (B + ROWS - 1) / ROWS;
   float* part = static_cast<float*>(ws);
-  mlp_grad_kernel<<<(unsigned)nb, THREADS, sizeof(Smem), st>>>(params, X, t, B, part);
+  (void)nk::launch_k(mlp_grad_kernel, dim3((unsigned)nb), dim3(THREADS), sizeof(Smem), st, 1, params, X, t, B, part);
   if ((s = check_launch("mlp_grad_kernel")) != NK_OK) return s;
-  mlp_reduce_kernel<<<(NPARAM + 1 + 255) / 256, 256, 0, st>>>(part, (int)nb, B, grad, loss);
+  (void)nk::launch_k(mlp_reduce_kernel, dim3((NPARAM + 1 + 255) / 256), dim3(256), 0, st, 1, part, (int)nb, B, grad, loss);
   return check_launch("mlp_reduce_kernel");
 }
 
@@ -253,7 +261,7 @@ nk_status nk_mlp_adam(float* params, const float* grad, float* m, float* v, int3
   if (!params || !grad || !m || !v) return fail(NK_ERR_INVALID_ARG, "null pointer");
   const float bc1 = 1.f - powf(beta1, (float)step);
   const float bc2 = 1.f - powf(beta2, (float)step);
-  mlp_adam_kernel<<<(NPARAM + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(
+  (void)nk::launch_k(mlp_adam_kernel, dim3((NPARAM + 255) / 256), dim3(256), 0, static_cast<cudaStream_t>(stream), 1, 
       params, grad, m, v, NPARAM, lr, beta1, beta2, eps, bc1, bc2);
   return check_launch("mlp_adam_kernel");
 }

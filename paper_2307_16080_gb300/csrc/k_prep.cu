@@ -45,6 +45,8 @@ __device__ __forceinline__ void pro4(const EwProg& e, float* v, int64_t off) {
 template <bool PRO>
 __global__ void amax_stage1(const float* __restrict__ x, int64_t rows, int64_t cols, int64_t ld,
                             float* __restrict__ partial, const __grid_constant__ EwProg pro) {
+  nk::pdl_wait();      // earlier kernels on the stream have finished
+  nk::pdl_trigger();
   float m = 0.f;
   bool nan = false;
   const bool al = (reinterpret_cast<uintptr_t>(x) & 15) == 0;
@@ -104,6 +106,8 @@ __global__ void amax_stage1(const float* __restrict__ x, int64_t rows, int64_t c
 }
 
 __global__ void amax_stage2(const float* __restrict__ partial, int n, float* __restrict__ out) {
+  nk::pdl_wait();      // earlier kernels on the stream have finished
+  nk::pdl_trigger();
   float m = 0.f;
   bool nan = false;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -163,6 +167,8 @@ __global__ void cast_rows(const float* __restrict__ in, int64_t rows, int64_t co
                           const float* __restrict__ amax, typename Caster<KIND>::T* __restrict__ o0,
                           typename Caster<KIND>::T* __restrict__ o1, int64_t ld_out,
                           float* scale_out, const __grid_constant__ EwProg pro) {
+  nk::pdl_wait();      // earlier kernels on the stream have finished
+  nk::pdl_trigger();
   using T = typename Caster<KIND>::T;
   const float s = KIND == 1 ? fp8_scale_of(amax) : 1.f;
   if (scale_out && blockIdx.x == 0 && threadIdx.x == 0) *scale_out = s;
@@ -208,6 +214,8 @@ __global__ void __launch_bounds__(256) cast_transpose(const float* __restrict__ 
                                                       typename Caster<KIND>::T* __restrict__ o0,
                                                       typename Caster<KIND>::T* __restrict__ o1, int64_t ld_out,
                                                       float* scale_out, const __grid_constant__ EwProg pro) {
+  nk::pdl_wait();      // earlier kernels on the stream have finished
+  nk::pdl_trigger();
   using T = typename Caster<KIND>::T;
   constexpr int TS = 64;
   constexpr int VEC = sizeof(T) == 1 ? 16 : 8;      // output elements per 16-byte store
@@ -279,6 +287,8 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 // b*blockDim + i + k*gridDim*blockDim; warp tree, then a tree over warps.
 __global__ void norm_stage1(const float* __restrict__ C, int64_t ldc, const double* __restrict__ R,
                             int64_t ldr, int64_t M, int64_t N, double* __restrict__ partial) {
+  nk::pdl_wait();      // earlier kernels on the stream have finished
+  nk::pdl_trigger();
   double e = 0.0, r2 = 0.0;
   const int64_t total = M * N;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
@@ -305,6 +315,8 @@ __global__ void norm_stage1(const float* __restrict__ C, int64_t ldc, const doub
 }
 
 __global__ void norm_stage2(const double* __restrict__ partial, int n, double* __restrict__ out) {
+  nk::pdl_wait();      // earlier kernels on the stream have finished
+  nk::pdl_trigger();
   double e = 0.0, r2 = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) { e += partial[2 * i]; r2 += partial[2 * i + 1]; }
   __shared__ double se[32], sr[32];
@@ -332,14 +344,14 @@ nk_status launch_cast(const float* in, int64_t rows, int64_t cols, int64_t ld_in
   if (transpose) {
     dim3 grid((unsigned)((cols + 63) / 64), (unsigned)((rows + 63) / 64));
     if (grid.y > 65535) return fail(NK_ERR_UNSUPPORTED, "too many rows for the transposing cast");
-    cast_transpose<KIND, PRO><<<grid, 256, 0, st>>>(in, rows, cols, ld_in, amax, o0, o1, ld_out, scale_out, pro);
+    (void)nk::launch_k(cast_transpose<KIND, PRO>, dim3(grid), dim3(256), 0, st, 1, in, rows, cols, ld_in, amax, o0, o1, ld_out, scale_out, pro);
   } else {
     const int64_t work = rows * ((cols + 3) / 4);
     int64_t blocks = (work + 255) / 256;
     const int64_t cap = (int64_t)sms * 16;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    cast_rows<KIND, PRO><<<(unsigned)blocks, 256, 0, st>>>(in, rows, cols, ld_in, amax, o0, o1, ld_out,
+    (void)nk::launch_k(cast_rows<KIND, PRO>, dim3((unsigned)blocks), dim3(256), 0, st, 1, in, rows, cols, ld_in, amax, o0, o1, ld_out,
                                                             scale_out, pro);
   }
   return check_launch("cast kernel");
@@ -361,6 +373,8 @@ nk_status launch_cast(const float* in, int64_t rows, int64_t cols, int64_t ld_in
 // run, handled as float4 (the element offset is the flat index).
 __global__ void ew_dense_kernel(const float* x, float* y, int64_t n,
                                 const __grid_constant__ EwProg prog) {
+  nk::pdl_wait();      // earlier kernels on the stream have finished
+  nk::pdl_trigger();
   const int64_t n4 = n / 4;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
@@ -383,6 +397,8 @@ struct Strided4 {
 
 __global__ void ew_strided_kernel(const float* x, float* y, int64_t n, const __grid_constant__ Strided4 g,
                                   const __grid_constant__ EwProg prog) {
+  nk::pdl_wait();      // earlier kernels on the stream have finished
+  nk::pdl_trigger();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     int64_t r = i, ox = 0, oy = 0;
 #pragma unroll
@@ -411,12 +427,12 @@ nk_status prep_amax(const float* x, int64_t rows, int64_t cols, int64_t ld, floa
   if (!ws || ws_bytes < prep_amax_ws(rows * cols))
     return fail(NK_ERR_WORKSPACE, "amax needs %zu bytes of workspace", prep_amax_ws(rows * cols));
   if (pro && pro->n)
-    amax_stage1<true><<<kAmaxBlocks, 256, 0, st>>>(x, rows, cols, ld, static_cast<float*>(ws), *pro);
+    (void)nk::launch_k(amax_stage1<true>, dim3(kAmaxBlocks), dim3(256), 0, st, 1, x, rows, cols, ld, static_cast<float*>(ws), *pro);
   else
-    amax_stage1<false><<<kAmaxBlocks, 256, 0, st>>>(x, rows, cols, ld, static_cast<float*>(ws), EwProg{});
+    (void)nk::launch_k(amax_stage1<false>, dim3(kAmaxBlocks), dim3(256), 0, st, 1, x, rows, cols, ld, static_cast<float*>(ws), EwProg{});
   nk_status s = check_launch("amax_stage1");
   if (s != NK_OK) return s;
-  amax_stage2<<<1, 1024, 0, st>>>(static_cast<float*>(ws), kAmaxBlocks, amax);
+  (void)nk::launch_k(amax_stage2, dim3(1), dim3(1024), 0, st, 1, static_cast<float*>(ws), kAmaxBlocks, amax);
   return check_launch("amax_stage2");
 }
 
@@ -462,8 +478,8 @@ nk_status ew_tensor(const float* x, const int64_t* sx, float* y, const int64_t* 
   if (blocks > (int64_t)sms * 16) blocks = (int64_t)sms * 16;
   if (blocks < 1) blocks = 1;
   const bool al = ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 15) == 0;
-  if (dense && al) ew_dense_kernel<<<(unsigned)blocks, 256, 0, st>>>(x, y, n, prog);
-  else ew_strided_kernel<<<(unsigned)blocks, 256, 0, st>>>(x, y, n, g, prog);
+  if (dense && al) (void)nk::launch_k(ew_dense_kernel, dim3((unsigned)blocks), dim3(256), 0, st, 1, x, y, n, prog);
+  else (void)nk::launch_k(ew_strided_kernel, dim3((unsigned)blocks), dim3(256), 0, st, 1, x, y, n, g, prog);
   return check_launch("elementwise kernel");
 }
 
@@ -474,10 +490,10 @@ nk_status norm_sumsq(const float* C, int64_t ldc, const double* R, int64_t ldr, 
   if (!ws || ws_bytes < norm_ws(M, N))
     return fail(NK_ERR_WORKSPACE, "norm needs %zu bytes of workspace", norm_ws(M, N));
   double* part = static_cast<double*>(ws);
-  norm_stage1<<<kNormBlocks, 256, 0, st>>>(C, ldc, R, ldr, M, N, part);
+  (void)nk::launch_k(norm_stage1, dim3(kNormBlocks), dim3(256), 0, st, 1, C, ldc, R, ldr, M, N, part);
   nk_status s = check_launch("norm_stage1");
   if (s != NK_OK) return s;
-  norm_stage2<<<1, 1024, 0, st>>>(part, kNormBlocks, out);
+  (void)nk::launch_k(norm_stage2, dim3(1), dim3(1024), 0, st, 1, part, kNormBlocks, out);
   return check_launch("norm_stage2");
 }
 

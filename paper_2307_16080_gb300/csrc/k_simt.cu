@@ -85,8 +85,12 @@ __device__ __forceinline__ void pro4(const EwProg& e, float4& v, int64_t off, in
   v.w = ew_run(e, v.w, off + 3 * d);
 }
 
-template <int RM, int RN, int AM, int BMD>
+// FUSED: the variant that runs prologue / epilogue programs (instantiated
+// with the scalar load modes only); the plain variants carry no call.
+template <int RM, int RN, int AM, int BMD, bool FUSED>
 __global__ void __launch_bounds__(THREADS, 2) simt_gemm_kernel(const __grid_constant__ KArgs args) {
+  nk::pdl_wait();      // earlier kernels on the stream have finished
+  nk::pdl_trigger();
   constexpr int BM = 64 * RM;
   constexpr int BN = 64 * RN;
   constexpr int APAD = 4;
@@ -122,7 +126,7 @@ __global__ void __launch_bounds__(THREADS, 2) simt_gemm_kernel(const __grid_cons
             v = __ldg(reinterpret_cast<const float4*>(p.A + off));
           else
             v = conv_a4(p, m, k, &off);
-          if (p.pro_a.n && off >= 0) pro4(p.pro_a, v, off, 1);
+          if (FUSED && p.pro_a.n && off >= 0) pro4(p.pro_a, v, off, 1);
         }
         ra[4 * j + 0] = v.x; ra[4 * j + 1] = v.y; ra[4 * j + 2] = v.z; ra[4 * j + 3] = v.w;
       }
@@ -135,7 +139,7 @@ __global__ void __launch_bounds__(THREADS, 2) simt_gemm_kernel(const __grid_cons
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
         if (m < p.M && k < kend) {
           v = __ldg(reinterpret_cast<const float4*>(p.A + (int64_t)k * p.sak + m));
-          if (p.pro_a.n) pro4(p.pro_a, v, (int64_t)k * p.sak + m, 1);
+          if (FUSED && p.pro_a.n) pro4(p.pro_a, v, (int64_t)k * p.sak + m, 1);
         }
         ra[4 * j + 0] = v.x; ra[4 * j + 1] = v.y; ra[4 * j + 2] = v.z; ra[4 * j + 3] = v.w;
       }
@@ -150,7 +154,7 @@ __global__ void __launch_bounds__(THREADS, 2) simt_gemm_kernel(const __grid_cons
           int64_t off = (int64_t)m * p.sam + (int64_t)k * p.sak;
           if constexpr (AM == A_CONV_SCALAR) v = conv_a(p, m, k, &off);
           else v = p.A[off];
-          if (p.pro_a.n && off >= 0) v = ew_run(p.pro_a, v, off);
+          if (FUSED && p.pro_a.n && off >= 0) v = ew_run(p.pro_a, v, off);
         }
         ra[j] = v;
       }
@@ -191,7 +195,7 @@ __global__ void __launch_bounds__(THREADS, 2) simt_gemm_kernel(const __grid_cons
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
         if (n < p.N && k < kend) {
           v = __ldg(reinterpret_cast<const float4*>(p.B + (int64_t)k * p.sbk + n));
-          if (p.pro_b.n) pro4(p.pro_b, v, (int64_t)k * p.sbk + n, 1);
+          if (FUSED && p.pro_b.n) pro4(p.pro_b, v, (int64_t)k * p.sbk + n, 1);
         }
         rb[4 * j + 0] = v.x; rb[4 * j + 1] = v.y; rb[4 * j + 2] = v.z; rb[4 * j + 3] = v.w;
       }
@@ -204,7 +208,7 @@ __global__ void __launch_bounds__(THREADS, 2) simt_gemm_kernel(const __grid_cons
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
         if (n < p.N && k < kend) {
           v = __ldg(reinterpret_cast<const float4*>(p.B + (int64_t)n * p.sbn + k));
-          if (p.pro_b.n) pro4(p.pro_b, v, (int64_t)n * p.sbn + k, 1);
+          if (FUSED && p.pro_b.n) pro4(p.pro_b, v, (int64_t)n * p.sbn + k, 1);
         }
         rb[4 * j + 0] = v.x; rb[4 * j + 1] = v.y; rb[4 * j + 2] = v.z; rb[4 * j + 3] = v.w;
       }
@@ -218,7 +222,7 @@ __global__ void __launch_bounds__(THREADS, 2) simt_gemm_kernel(const __grid_cons
         if (n < p.N && k < kend) {
           const int64_t off = (int64_t)k * p.sbk + (int64_t)n * p.sbn;
           v = p.B[off];
-          if (p.pro_b.n) v = ew_run(p.pro_b, v, off);
+          if (FUSED && p.pro_b.n) v = ew_run(p.pro_b, v, off);
         }
         rb[j] = v;
       }
@@ -319,7 +323,7 @@ __global__ void __launch_bounds__(THREADS, 2) simt_gemm_kernel(const __grid_cons
           if (p.beta != 0.f) o = fmaf(p.beta, p.C[(int64_t)m * p.scm + (int64_t)n * p.scn], o);
           if (p.bias) o += p.bias[p.bias_on_m ? m : n];
           if (p.relu) o = (o > 0.f || o != o) ? o : 0.f;
-          if (p.ew.n) o = ew_run(p.ew, o, (int64_t)m * p.scm + (int64_t)n * p.scn);
+          if (FUSED && p.ew.n) o = ew_run(p.ew, o, (int64_t)m * p.scm + (int64_t)n * p.scn);
         }
         v[j] = o;
       }
@@ -338,7 +342,10 @@ __global__ void __launch_bounds__(THREADS, 2) simt_gemm_kernel(const __grid_cons
 // Split-K reduce: lanes of a warp form groups of S (a power of two); lane
 // s of a group reads slice s of one output, the group sums with an xor
 // shuffle tree (same order every run), lane 0 applies the epilogue.
+template <bool EW>
 __global__ void splitk_reduce_kernel(const __grid_constant__ SplitReduce r, int S) {
+  nk::pdl_wait();      // earlier kernels on the stream have finished
+  nk::pdl_trigger();
   const int lane = threadIdx.x & 31;
   const int per_warp = 32 / S;
   const int s = lane % S;
@@ -360,7 +367,7 @@ __global__ void splitk_reduce_kernel(const __grid_constant__ SplitReduce r, int 
       if (r.beta != 0.f) o = fmaf(r.beta, *c, o);
       if (r.bias) o += r.bias[r.bias_on_m ? m : n];
       if (r.relu) o = (o > 0.f || o != o) ? o : 0.f;
-      if (r.ew.n) o = ew_run(r.ew, o, (int64_t)m * r.scm + (int64_t)n * r.scn);
+      if (EW && r.ew.n) o = ew_run(r.ew, o, (int64_t)m * r.scm + (int64_t)n * r.scn);
       *c = o;
     }
   }
@@ -369,10 +376,20 @@ __global__ void splitk_reduce_kernel(const __grid_constant__ SplitReduce r, int 
 template <int RM, int RN, int AM>
 nk_status launch_b(const KArgs& a, int bmode, dim3 grid, cudaStream_t st) {
   switch (bmode) {
-    case B_NVEC: simt_gemm_kernel<RM, RN, AM, B_NVEC><<<grid, THREADS, 0, st>>>(a); break;
-    case B_KVEC: simt_gemm_kernel<RM, RN, AM, B_KVEC><<<grid, THREADS, 0, st>>>(a); break;
-    default: simt_gemm_kernel<RM, RN, AM, B_SCALAR><<<grid, THREADS, 0, st>>>(a); break;
+    case B_NVEC: (void)nk::launch_k(simt_gemm_kernel<RM, RN, AM, B_NVEC, false>, dim3(grid), dim3(THREADS), 0, st, 1, a); break;
+    case B_KVEC: (void)nk::launch_k(simt_gemm_kernel<RM, RN, AM, B_KVEC, false>, dim3(grid), dim3(THREADS), 0, st, 1, a); break;
+    default: (void)nk::launch_k(simt_gemm_kernel<RM, RN, AM, B_SCALAR, false>, dim3(grid), dim3(THREADS), 0, st, 1, a); break;
   }
+  return check_launch("simt_gemm_kernel");
+}
+
+// Programs present: scalar loads of any layout, FUSED kernel.
+template <int RM, int RN>
+nk_status launch_fused(const KArgs& a, dim3 grid, cudaStream_t st) {
+  if (a.p.is_conv)
+    (void)nk::launch_k(simt_gemm_kernel<RM, RN, A_CONV_SCALAR, B_SCALAR, true>, dim3(grid), dim3(THREADS), 0, st, 1, a);
+  else
+    (void)nk::launch_k(simt_gemm_kernel<RM, RN, A_SCALAR, B_SCALAR, true>, dim3(grid), dim3(THREADS), 0, st, 1, a);
   return check_launch("simt_gemm_kernel");
 }
 
@@ -433,8 +450,11 @@ nk_status simt_gemm(const SimtGemm& p, int tile, int splits, void* ws, size_t ws
   else bmode = B_SCALAR;
   dim3 grid((p.N + tile - 1) / tile, (p.M + tile - 1) / tile, splits);
   if (grid.y > 65535) return fail(NK_ERR_UNSUPPORTED, "M too large for the SIMT grid");
-  nk_status s = tile == 128 ? launch_a<2, 2>(a, amode, bmode, grid, st)
-                            : launch_a<1, 1>(a, amode, bmode, grid, st);
+  nk_status s;
+  if (p.pro_a.n || p.pro_b.n || p.ew.n)
+    s = tile == 128 ? launch_fused<2, 2>(a, grid, st) : launch_fused<1, 1>(a, grid, st);
+  else
+    s = tile == 128 ? launch_a<2, 2>(a, amode, bmode, grid, st) : launch_a<1, 1>(a, amode, bmode, grid, st);
   if (s != NK_OK || splits == 1) return s;
   SplitReduce r{};
   r.partial = a.partial;
@@ -467,7 +487,8 @@ nk_status splitk_reduce(const SplitReduce& r, cudaStream_t st) {
   int64_t blocks = (warps_needed + 7) / 8;
   blocks = blocks < (int64_t)sms * 8 ? blocks : (int64_t)sms * 8;
   if (blocks < 1) blocks = 1;
-  splitk_reduce_kernel<<<(unsigned)blocks, 256, 0, st>>>(r, S);
+  if (r.ew.n) (void)nk::launch_k(splitk_reduce_kernel<true>, dim3((unsigned)blocks), dim3(256), 0, st, 1, r, S);
+  else (void)nk::launch_k(splitk_reduce_kernel<false>, dim3((unsigned)blocks), dim3(256), 0, st, 1, r, S);
   return check_launch("splitk_reduce_kernel");
 }
 

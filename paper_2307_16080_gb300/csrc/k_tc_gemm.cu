@@ -310,6 +310,10 @@ __global__ void __launch_bounds__(WIDE ? 320 : 192, 1) tc_gemm_kernel(const __gr
   ptx::tc_fence_after();
   if (CL == 2) ptx::cluster_sync();
   const uint32_t tmem_base = *tmem_slot;
+  // Set-up above touched no global data; everything below runs after the
+  // earlier kernels on the stream have finished.
+  nk::pdl_wait();
+  nk::pdl_trigger();
 
   const int a_bytes = MCH * kBM * kRowBytes;
   const int b_bytes = b_rows_smem * kRowBytes;
@@ -558,7 +562,26 @@ __global__ void __launch_bounds__(WIDE ? 320 : 192, 1) tc_gemm_kernel(const __gr
         float* dst = t.C + (int64_t)row * t.ldc + col0;
         const float bm = (t.bias && p.bias_on_m) ? __ldg(t.bias + row) : 0.f;
         const float beta = t.beta;
-        if (p.c_vec && col0 + 32 <= t.N) {
+        if (p.ew.n) {
+          // A program runs out of line.  The segment goes through a local
+          // buffer: the program reads its operands (which may alias C) before
+          // the store, and v[] is not live across the call, so the plain
+          // paths below keep their registers.
+          const int ncol = t.N - col0 < 32 ? t.N - col0 : 32;
+          float buf[32];
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            float x = alpha * v[j];
+            if (j < ncol) {
+              if (beta != 0.f) x = fmaf(beta, dst[j], x);
+              if (t.bias) x += p.bias_on_m ? bm : __ldg(t.bias + col0 + j);
+              if (t.relu) x = (x > 0.f || x != x) ? x : 0.f;
+            }
+            buf[j] = x;
+          }
+          ew_apply(p.ew, buf, ncol, (int64_t)row * t.ldc + col0);
+          for (int j = 0; j < ncol; ++j) dst[j] = buf[j];
+        } else if (p.c_vec && col0 + 32 <= t.N) {
 #pragma unroll
           for (int j = 0; j < 32; j += 4) {
             float o[4];
@@ -571,7 +594,6 @@ __global__ void __launch_bounds__(WIDE ? 320 : 192, 1) tc_gemm_kernel(const __gr
               if (beta != 0.f) x = fmaf(beta, ci[e], x);
               if (t.bias) x += p.bias_on_m ? bm : __ldg(t.bias + col0 + j + e);
               if (t.relu) x = (x > 0.f || x != x) ? x : 0.f;
-              if (p.ew.n) x = ew_run(p.ew, x, (int64_t)row * t.ldc + col0 + j + e);
               o[e] = x;
             }
             *reinterpret_cast<float4*>(dst + j) = make_float4(o[0], o[1], o[2], o[3]);
@@ -584,7 +606,6 @@ __global__ void __launch_bounds__(WIDE ? 320 : 192, 1) tc_gemm_kernel(const __gr
             if (beta != 0.f) x = fmaf(beta, dst[j], x);
             if (t.bias) x += p.bias_on_m ? bm : __ldg(t.bias + col0 + j);
             if (t.relu) x = (x > 0.f || x != x) ? x : 0.f;
-            if (p.ew.n) x = ew_run(p.ew, x, (int64_t)row * t.ldc + col0 + j);
             dst[j] = x;
           }
         }
@@ -675,20 +696,7 @@ nk_status launch(const TcParams& p, int grid, int smem, cudaStream_t st) {
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(tc_gemm_kernel)");
     if (dev >= 0 && dev < 64) set_bytes[dev] = smem;
   }
-  cudaError_t e;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(WIDE ? 320 : kThreads);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = CL;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = CL > 1 ? 1 : 0;
-  e = cudaLaunchKernelEx(&cfg, kern, p);
+  const cudaError_t e = nk::launch_k(kern, dim3(grid), dim3(WIDE ? 320 : kThreads), smem, st, CL, p);
   if (e != cudaSuccess) return cuda_fail(e, "launch tc_gemm_kernel");
   return check_launch("tc_gemm_kernel");
 }

@@ -169,6 +169,10 @@ __global__ void __launch_bounds__(kThreads, 1) halo_conv_kernel(const __grid_con
   __syncthreads();
   ptx::tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
+  // Set-up above touched no global data; everything below runs after the
+  // earlier kernels on the stream have finished.
+  nk::pdl_wait();
+  nk::pdl_trigger();
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
@@ -287,7 +291,25 @@ __global__ void __launch_bounds__(kThreads, 1) halo_conv_kernel(const __grid_con
           const int col0 = tn * p.bn + c0;
           if (!row_ok || col0 >= p.F) continue;
           float* dst = orow + col0;
-          if (p.c_vec && col0 + 32 <= p.F) {
+          if (p.ew.n) {
+            // A program runs out of line: the segment goes through a local
+            // buffer so the program reads its operands (which may alias O)
+            // before the store and v[] is not live across the call.
+            const int ncol = p.F - col0 < 32 ? p.F - col0 : 32;
+            float buf[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              float xv = v[j];
+              if (j < ncol) {
+                if (p.beta != 0.f) xv = fmaf(p.beta, dst[j], xv);
+                if (p.bias) xv += __ldg(p.bias + col0 + j);
+                if (p.relu) xv = (xv > 0.f || xv != xv) ? xv : 0.f;
+              }
+              buf[j] = xv;
+            }
+            ew_apply(p.ew, buf, ncol, orow_off + col0);
+            for (int j = 0; j < ncol; ++j) dst[j] = buf[j];
+          } else if (p.c_vec && col0 + 32 <= p.F) {
 #pragma unroll
             for (int j = 0; j < 32; j += 4) {
               float o[4];
@@ -300,7 +322,6 @@ __global__ void __launch_bounds__(kThreads, 1) halo_conv_kernel(const __grid_con
                 if (p.beta != 0.f) xv = fmaf(p.beta, ci[e], xv);
                 if (p.bias) xv += __ldg(p.bias + col0 + j + e);
                 if (p.relu) xv = (xv > 0.f || xv != xv) ? xv : 0.f;
-                if (p.ew.n) xv = ew_run(p.ew, xv, orow_off + col0 + j + e);
                 o[e] = xv;
               }
               *reinterpret_cast<float4*>(dst + j) = make_float4(o[0], o[1], o[2], o[3]);
@@ -313,7 +334,6 @@ __global__ void __launch_bounds__(kThreads, 1) halo_conv_kernel(const __grid_con
               if (p.beta != 0.f) xv = fmaf(p.beta, dst[j], xv);
               if (p.bias) xv += __ldg(p.bias + col0 + j);
               if (p.relu) xv = (xv > 0.f || xv != xv) ? xv : 0.f;
-              if (p.ew.n) xv = ew_run(p.ew, xv, orow_off + col0 + j);
               dst[j] = xv;
             }
           }
@@ -485,7 +505,7 @@ nk_status launch(const HaloParams& p, int grid, int smem, cudaStream_t st) {
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(halo_conv_kernel)");
     if (dev >= 0 && dev < 64) set_bytes[dev] = smem;
   }
-  kern<<<grid, kThreads, smem, st>>>(p);
+  (void)nk::launch_k(kern, dim3(grid), dim3(kThreads), smem, st, 1, p);
   return check_launch("halo_conv_kernel");
 }
 

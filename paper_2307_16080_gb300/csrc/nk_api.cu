@@ -75,6 +75,9 @@ int64_t wait_budget() {
   return b > 0 ? b : kDefaultWaitBudget;
 }
 
+static std::atomic<int> g_pdl{1};
+bool pdl_enabled() { return g_pdl.load(std::memory_order_relaxed) != 0; }
+
 nk_status collect_device_errors(uint32_t* flags) {
   *flags = tc_read_and_clear_errors() | halo_read_and_clear_errors();
   return NK_OK;
@@ -340,6 +343,13 @@ nk_status nk_set_wait_budget(int64_t iterations) {
   g_wait_budget.store(iterations);
   return NK_OK;
 }
+
+nk_status nk_set_pdl(int32_t enabled) {
+  nk::g_pdl.store(enabled ? 1 : 0);
+  return NK_OK;
+}
+
+int32_t nk_get_pdl(void) { return nk::pdl_enabled() ? 1 : 0; }
 
 nk_status nk_sync_status(void* stream) {
   cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));

@@ -10,6 +10,7 @@
 
 #include <functional>
 #include <string>
+#include <utility>
 
 #include "../../include/nk.h"
 #include "ew.cuh"
@@ -32,6 +33,54 @@ enum : uint32_t { kErrTimeout = 1u, kErrLaunch = 2u };   // kErrLaunch: too litt
 
 // Spin budget shared by the waiting kernels (set through nk_set_wait_budget).
 int64_t wait_budget();
+
+// ------------------------------------------ programmatic dependent launch
+// A kernel started by launch_k() may begin while the kernel before it on the
+// stream is still running.  It does its set-up that touches no global data
+// (mbarrier init, TMEM allocation, prefetch of parameter-space tensor maps),
+// then pdl_wait(), which returns once every earlier kernel on the stream has
+// completed and its writes are visible, and only then reads or writes global
+// memory.  It calls pdl_trigger() after pdl_wait(), so the kernel after it
+// may start its own set-up.  Because a grid triggers only after its own wait,
+// at most two grids overlap; the earlier one is fully resident (a dependent
+// launches only once every CTA of the earlier grid has triggered or exited)
+// and needs nothing from the later one, so a later CTA blocked in pdl_wait()
+// or in a TMEM allocation cannot hold it up.  Launched without the attribute
+// (nk_set_pdl(0)) both instructions do nothing.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+bool pdl_enabled();   // nk_set_pdl; on by default
+
+// cudaLaunchKernelEx with the programmatic-serialization attribute (when
+// enabled) and an optional cluster of `cluster` CTAs along x.  The kernel
+// must follow the pdl_wait() rule above.
+template <typename... Kargs, typename... Args>
+inline cudaError_t launch_k(void (*kern)(Kargs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                            int cluster, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[2];
+  unsigned n = 0;
+  if (pdl_enabled()) {
+    attr[n].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[n].val.programmaticStreamSerializationAllowed = 1;
+    ++n;
+  }
+  if (cluster > 1) {
+    attr[n].id = cudaLaunchAttributeClusterDimension;
+    attr[n].val.clusterDim.x = (unsigned)cluster;
+    attr[n].val.clusterDim.y = 1;
+    attr[n].val.clusterDim.z = 1;
+    ++n;
+  }
+  cfg.attrs = n ? attr : nullptr;
+  cfg.numAttrs = n;
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
 
 // Reads and clears the failure words of every translation unit.
 nk_status collect_device_errors(uint32_t* flags);

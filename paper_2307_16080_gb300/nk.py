@@ -108,6 +108,8 @@ SIGNATURES = {
     "nk_last_error": (ctypes.c_char_p, []),
     "nk_sync_status": (_I32, [_P]),
     "nk_set_wait_budget": (_I32, [_I64]),
+    "nk_set_pdl": (_I32, [_I32]),
+    "nk_get_pdl": (_I32, []),
     "nk_device_info": (_I32, [ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
     "nk_elementwise": (_I32, [_PT, _PT, ctypes.POINTER(nk_ew_program), _P]),
 }
@@ -356,6 +358,15 @@ def nk_sync_status(stream=None):
 
 def nk_set_wait_budget(iterations: int):
     _check(lib().nk_set_wait_budget(int(iterations)))
+
+
+def nk_set_pdl(enabled: bool):
+    """Programmatic dependent launch of the library's kernels (on by default)."""
+    _check(lib().nk_set_pdl(1 if enabled else 0))
+
+
+def nk_get_pdl() -> bool:
+    return bool(lib().nk_get_pdl())
 
 
 def nk_device_info():
