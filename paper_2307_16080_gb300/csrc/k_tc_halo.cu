@@ -25,6 +25,16 @@
 // ([F][taps][C], K-major) stream through their own ring, or stay resident
 // for the whole launch when one N tile holds all filters and they fit.
 //
+// Stacked kernel rows (schedule tile_k = 64*KH): the KW taps of one kernel
+// row go side by side along N.  Each weight tile holds KW boxes of 64
+// filters, so one MMA of N = 64*KW reads the window once at kernel row kh's
+// offset kh*dh*P and yields every tap of that row.  Accumulator column
+// kw*64 + f of GEMM row m is then tap kw's partial sum for output row
+// m - kw*dw.  The epilogue adds them with warp shuffles: lane l takes lane
+// l + kw*dw.  Window rows have a pitch P of 8, 16 or 32, so they sit inside
+// one warp and a valid output never reads across a warp.  That makes KH MMAs
+// per 16 channels instead of KH*KW narrow ones.
+//
 //   warp 0      TMA producer: window slots (one per 64-channel block) and
 //               weight tiles (one per tap and channel block).
 //   warp 1      TMEM allocation; one thread issues tcgen05.mma, M = 128,
@@ -75,6 +85,7 @@ struct HaloTile {
   int tiles_w, tiles_h, tiles_b;
   int N, OH, OW, KH, KW, dh, dw, pt, pl;
   int cblocks;           // 64-channel blocks
+  int stk;               // taps side by side along N: KW when kernel rows are stacked, else 1
 };
 
 struct HaloParams {
@@ -102,18 +113,27 @@ __device__ __forceinline__ int tap_offset(const HaloTile& t, int tap) {
   return kh * t.dh * t.P + kw * t.dw;
 }
 
-template <int MCH>
+// STK (kernel-row stacking, one chain): the KW taps of a kernel row sit side
+// by side along N, so one MMA of N = 64 * KW per kernel row and 16 channels
+// does the work of KW narrow ones.  Accumulator column kw * 64 + f of row m
+// holds the tap-kw partial sum of output row m - kw * dw; the epilogue adds
+// them with warp shuffles.  The window row pitch P divides 32, so a shifted
+// row never leaves its warp.  One accumulator buffer (TMEM for two CTAs).
+template <int MCH, bool STK>
 __global__ void __launch_bounds__(kThreads, 1) halo_conv_kernel(const __grid_constant__ HaloParams p) {
+  static_assert(!STK || MCH == 1, "stacked kernel rows use one chain");
+  constexpr int NACC = STK ? 1 : 2;   // accumulator buffers
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = ptx::smem_u32(smem_raw);
   const uint32_t base = (raw + 1023) & ~1023u;
   uint8_t* base_ptr = smem_raw + (base - raw);
   const HaloTile& t = p.t;
   const int WS = p.wslots, BS = p.bslots;
-  const int taps = t.KH * t.KW;
+  const int nst = STK ? t.KW : 1;                                // taps side by side along N
+  const int kgroups = STK ? t.KH : t.KH * t.KW;                  // K blocks per 64-channel block
   const uint32_t wbase = base;                                   // window slots
   const uint32_t bbase = wbase + (uint32_t)WS * p.slot_bytes;    // weight slots
-  const uint32_t b_tile = (uint32_t)p.bn * kRow;
+  const uint32_t b_tile = (uint32_t)(p.bn * nst) * kRow;
   const uint32_t bar0 = bbase + (uint32_t)BS * b_tile;
   auto wfull = [&](int s) { return bar0 + 8u * s; };
   auto wempty = [&](int s) { return bar0 + 8u * (WS + s); };
@@ -137,8 +157,9 @@ __global__ void __launch_bounds__(kThreads, 1) halo_conv_kernel(const __grid_con
   }
   const int warp = threadIdx.x / 32;
   const int lane = threadIdx.x % 32;
-  const uint32_t acc_cols = (uint32_t)(MCH * p.bn);
-  const uint32_t tmem_cols = 2u * acc_cols;   // 128, 256 or 512: a power of two >= 32
+  const uint32_t acc_cols = (uint32_t)(MCH * p.bn * nst);
+  // 128, 256 or 512 columns: a power of two >= 32 (stacked: 64 * KW rounded up)
+  const uint32_t tmem_cols = STK ? (acc_cols <= 128u ? 128u : 256u) : 2u * acc_cols;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < WS; ++s) {
@@ -194,12 +215,15 @@ __global__ void __launch_bounds__(kThreads, 1) halo_conv_kernel(const __grid_con
             ++wc;
           }
           if (!load_w) continue;
-          for (int tap = 0; tap < taps; ++tap) {
+          for (int kg = 0; kg < kgroups; ++kg) {
             const int s = bc % BS;
             const uint32_t ph = (uint32_t)(bc / BS) & 1u;
             if (!ptx::mbar_wait(bempty(s), ph ^ 1u, p.budget, abort_flag, &g_halo_err)) { ok = false; break; }
             ptx::mbar_arrive_expect_tx(bfull(s), b_tile);
-            ptx::tma_load_3d(bbase + (uint32_t)s * b_tile, &p.tmW, bfull(s), cb * 64, tap, tn * p.bn);
+            // one box of bn filters per tap; stacked: the KW taps of kernel row kg
+            for (int j = 0; j < nst; ++j)
+              ptx::tma_load_3d(bbase + (uint32_t)s * b_tile + (uint32_t)(j * p.bn) * kRow, &p.tmW, bfull(s), cb * 64,
+                               kg * nst + j, tn * p.bn);
             ++bc;
           }
         }
@@ -213,12 +237,12 @@ __global__ void __launch_bounds__(kThreads, 1) halo_conv_kernel(const __grid_con
   } else if (warp == 1) {
     // -------------------------------------------------------------- MMA
     if (lane == 0) {
-      const uint32_t idesc = ptx::make_idesc(1, 128, p.bn);
+      const uint32_t idesc = ptx::make_idesc(1, 128, p.bn * nst);
       int wc = 0, bc = 0, tc = 0;
       bool ok = true;
       for (int u = blockIdx.x; u < p.units && ok; u += gridDim.x, ++tc) {
-        const int acc = tc & 1;
-        const uint32_t aph = (uint32_t)(tc >> 1) & 1u;
+        const int acc = tc % NACC;
+        const uint32_t aph = (uint32_t)(tc / NACC) & 1u;
         if (!ptx::mbar_wait(tempty(acc), aph ^ 1u, p.budget, abort_flag, &g_halo_err)) break;
         ptx::tc_fence_after();
         const uint32_t d = tmem_base + (uint32_t)acc * acc_cols;
@@ -230,14 +254,16 @@ __global__ void __launch_bounds__(kThreads, 1) halo_conv_kernel(const __grid_con
           }
           ptx::tc_fence_after();
           const uint32_t win = wbase + (uint32_t)ws * p.slot_bytes;
-          for (int tap = 0; tap < taps; ++tap) {
+          for (int kg = 0; kg < kgroups; ++kg) {
             // resident weights: slot = K block, phase 0 completed once and stays so
-            const int kb = cb * taps + tap;
+            const int kb = cb * kgroups + kg;
             const int bs = p.resident ? kb : bc % BS;
             const uint32_t bph = p.resident ? 0u : (uint32_t)(bc / BS) & 1u;
             if (!ptx::mbar_wait(bfull(bs), bph, p.budget, abort_flag, &g_halo_err)) { ok = false; break; }
             ptx::tc_fence_after();
-            const uint32_t a0 = win + (uint32_t)tap_offset(t, tap) * kRow;
+            // stacked: kernel row kg starts kg * dh window rows down (the kw
+            // shifts are applied in the epilogue); else tap kg's offset
+            const uint32_t a0 = win + (uint32_t)(STK ? kg * t.dh * t.P : tap_offset(t, kg)) * kRow;
             const uint32_t b0 = bbase + (uint32_t)bs * b_tile;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
@@ -271,8 +297,8 @@ __global__ void __launch_bounds__(kThreads, 1) halo_conv_kernel(const __grid_con
     for (int u = blockIdx.x; u < p.units; u += gridDim.x, ++tc) {
       const int tn = u / p.tiles_m, tm = u - tn * p.tiles_m;
       const int tw = tm % t.tiles_w, th = (tm / t.tiles_w) % t.tiles_h, tb = tm / (t.tiles_w * t.tiles_h);
-      const int acc = tc & 1;
-      if (!ptx::mbar_wait(tfull(acc), (uint32_t)(tc >> 1) & 1u, p.budget, abort_flag, &g_halo_err)) break;
+      const int acc = tc % NACC;
+      if (!ptx::mbar_wait(tfull(acc), (uint32_t)(tc / NACC) & 1u, p.budget, abort_flag, &g_halo_err)) break;
       ptx::tc_fence_after();
       for (int ch = 0; ch < MCH; ++ch) {
         // GEMM row m = window pixel (b, y, x); valid when it is an output pixel
@@ -285,9 +311,18 @@ __global__ void __launch_bounds__(kThreads, 1) halo_conv_kernel(const __grid_con
         float* orow = p.O + orow_off;
         for (int c0 = 0; c0 < p.bn; c0 += 32) {
           float v[32];
-          ptx::tmem_ld32(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)acc * acc_cols +
-                             (uint32_t)(ch * p.bn + c0),
-                         v);
+          const uint32_t lane_base = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)acc * acc_cols;
+          ptx::tmem_ld32(lane_base + (uint32_t)(ch * p.bn + c0), v);
+          if (STK) {
+            // output row m = tap-0 row m + tap-kw row m + kw * dw, same warp
+            for (int j = 1; j < nst; ++j) {
+              float w[32];
+              ptx::tmem_ld32(lane_base + (uint32_t)(j * p.bn + c0), w);
+              const int sh = j * t.dw;
+#pragma unroll
+              for (int e = 0; e < 32; ++e) v[e] += __shfl_down_sync(0xffffffffu, w[e], sh);
+            }
+          }
           const int col0 = tn * p.bn + c0;
           if (!row_ok || col0 >= p.F) continue;
           float* dst = orow + col0;
@@ -369,30 +404,55 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 int taps_of(const ConvGeom& g) { return g.kh * g.kw; }
 int chains_of(const nk_schedule& s) { return s.tile_m / 128; }
 
-// Largest tap offset in GEMM rows.
-int max_offset(const ConvGeom& g, int P) { return (g.kh - 1) * g.dh * P + (g.kw - 1) * g.dw; }
+// Kernel-row stacking: tile_k = 64 * KH (one K block per kernel row and
+// 64-channel block) selects the window kernel with the KW taps of a kernel
+// row side by side along N (N = 64 * KW <= 256, so 2 <= KW <= 4).  For BF16,
+// per-tap schedules have tile_k 64 and plain window schedules 64 * KH * KW,
+// so the encodings do not collide.
+bool stacked_schedule(const ConvGeom& g, const nk_schedule& s) {
+  return g.kh >= 2 && g.kw >= 2 && g.kw <= 4 && s.tile_k == 64 * g.kh;
+}
+
+// Largest row offset the A operand reads, in GEMM rows (stacked: the kw
+// shifts move to the epilogue).
+int max_offset(const ConvGeom& g, int P, bool stk) {
+  return (g.kh - 1) * g.dh * P + (stk ? 0 : (g.kw - 1) * g.dw);
+}
+
+// TMEM columns one CTA allocates: two accumulator buffers of mch * bn, or
+// (stacked) one buffer of 64 * KW rounded up to a power of two.
+int halo_tmem_cols(int mch, int bn, int stk) {
+  return stk > 1 ? (bn * stk <= 128 ? 128 : 256) : 2 * mch * bn;
+}
 
 // Window tile for `mch` chains: the fewest tiles whose valid output rows
 // all fall inside the first mch*128 GEMM rows; ties go to the smaller window.
 // Returns false when no tile fits (box extents <= 256, slot within `max_slot_rows`).
-bool choose_halo_tile(const ConvGeom& g, int mch, int max_slot_rows, HaloTile* out) {
+// Stacked (stk > 1): the window row pitch P is 8, 16 or 32, so window rows
+// are aligned to warps, and every row a valid output reads through the kw
+// shifts (its whole window row) lies inside the first 128 GEMM rows.
+bool choose_halo_tile(const ConvGeom& g, int mch, int max_slot_rows, bool stk, HaloTile* out) {
   const int maxrows = mch * 128;
   const int halo_w = (g.kw - 1) * g.dw, halo_h = (g.kh - 1) * g.dh;
   bool found = false;
   int64_t best_tiles = INT64_MAX;
   int best_slot = INT_MAX;
   HaloTile best{};
-  for (int Q = 1; Q <= g.ow && Q + halo_w <= 256; ++Q) {
+  for (int Q = 1; (stk || Q <= g.ow) && Q + halo_w <= 256; ++Q) {
     const int P = Q + halo_w;
     if (Q > maxrows) break;
+    if (stk && P != 8 && P != 16 && P != 32) {
+      if (P > 32) break;
+      continue;
+    }
     for (int R = 1; R <= g.oh && R + halo_h <= 256; ++R) {
       const int WR = R + halo_h;
-      const int last = (R - 1) * P + Q;   // rows one image's valid outputs span
+      const int last = stk ? R * P : (R - 1) * P + Q;   // rows one image's outputs (and their reads) span
       if (last > maxrows) break;
       int NB = 1 + (maxrows - last) / (WR * P);
       NB = std::min(std::min(NB, g.n), 256);
       const int rows = NB * WR * P;
-      const int slot = (std::max(rows, maxrows + max_offset(g, P)) + 7) / 8 * 8;
+      const int slot = (std::max(rows, maxrows + max_offset(g, P, stk)) + 7) / 8 * 8;
       if (slot > max_slot_rows) continue;
       const int64_t tiles = (int64_t)((g.n + NB - 1) / NB) * ((g.oh + R - 1) / R) * ((g.ow + Q - 1) / Q);
       if (tiles < best_tiles || (tiles == best_tiles && slot < best_slot)) {
@@ -411,6 +471,7 @@ bool choose_halo_tile(const ConvGeom& g, int mch, int max_slot_rows, HaloTile* o
   best.N = g.n; best.OH = g.oh; best.OW = g.ow;
   best.KH = g.kh; best.KW = g.kw; best.dh = g.dh; best.dw = g.dw; best.pt = g.pt; best.pl = g.pl;
   best.cblocks = (g.c + 63) / 64;
+  best.stk = stk ? g.kw : 1;
   *out = best;
   return true;
 }
@@ -420,27 +481,29 @@ bool choose_halo_tile(const ConvGeom& g, int mch, int max_slot_rows, HaloTile* o
 struct TileKey {
   ConvGeom g;
   int mch;
+  int stk;
 };
 std::mutex g_tile_mu;
 std::vector<std::pair<TileKey, std::pair<bool, HaloTile>>> g_tile_cache;
 
-bool cached_halo_tile(const ConvGeom& g, int mch, HaloTile* out) {
+bool cached_halo_tile(const ConvGeom& g, int mch, bool stk, HaloTile* out) {
   // The window slot may use at most what is left beside two weight tiles of
   // 256 rows and the barriers; the real budget is checked per schedule.
   const int max_slot_rows = (kMaxSmem - 1024 - kBarBytes) / kRow;
   std::lock_guard<std::mutex> lk(g_tile_mu);
   for (auto& e : g_tile_cache)
-    if (e.first.mch == mch && std::memcmp(&e.first.g, &g, sizeof g) == 0) {
+    if (e.first.mch == mch && e.first.stk == (int)stk && std::memcmp(&e.first.g, &g, sizeof g) == 0) {
       *out = e.second.second;
       return e.second.first;
     }
   HaloTile t{};
-  const bool ok = choose_halo_tile(g, mch, max_slot_rows, &t);
+  const bool ok = choose_halo_tile(g, mch, max_slot_rows, stk, &t);
   if (g_tile_cache.size() > 4096) g_tile_cache.clear();
   TileKey k;
   std::memset(&k, 0, sizeof k);
   k.g = g;
   k.mch = mch;
+  k.stk = (int)stk;
   g_tile_cache.push_back({k, {ok, t}});
   *out = t;
   return ok;
@@ -454,10 +517,9 @@ struct HaloLayout {
 };
 
 // CTAs of this layout that fit on one SM: shared memory (each CTA also
-// costs 1 KB of reserved space) and two accumulator buffers of MCH * BN
-// TMEM columns each.
-int halo_ctas(int smem, int chains, int bn) {
-  const bool tmem2 = 4 * chains * bn <= 512;
+// costs 1 KB of reserved space) and the TMEM columns each CTA allocates.
+int halo_ctas(int smem, int tmem_cols) {
+  const bool tmem2 = 2 * tmem_cols <= 512;
   return (tmem2 && 2 * (smem + 1024) <= kMaxSmem + 1024) ? 2 : 1;
 }
 
@@ -468,24 +530,25 @@ int halo_ctas(int smem, int chains, int bn) {
 // SM wins; on a tie, resident weights.
 bool halo_layout(const ConvGeom& g, int F, const nk_schedule& s, HaloLayout* L) {
   const int mch = chains_of(s);
-  const int chains = mch;
-  if (!cached_halo_tile(g, mch, &L->t)) return false;
+  const bool stk = stacked_schedule(g, s);
+  if (!cached_halo_tile(g, mch, stk, &L->t)) return false;
+  const int tcols = halo_tmem_cols(mch, s.tile_n, L->t.stk);
   L->slot_bytes = (uint32_t)((L->t.slot_rows * kRow + 1023) / 1024 * 1024);
   L->wslots = s.stages;
   const int fixed = 1024 + s.stages * (int)L->slot_bytes + kBarBytes;
-  const int b_tile = s.tile_n * kRow;
-  const int nkb = taps_of(g) * L->t.cblocks;
+  const int b_tile = s.tile_n * L->t.stk * kRow;   // stacked: KW boxes of tile_n filters
+  const int nkb = (stk ? g.kh : taps_of(g)) * L->t.cblocks;
   const int room = (kMaxSmem - fixed) / b_tile;
   if (room < 2) return false;
   // streamed ring: deepest ring that keeps the CTA count of a 2-slot ring
   int ring = std::min(std::min(room, nkb < 2 ? 2 : nkb), 8);
-  const int want = halo_ctas(fixed + 2 * b_tile, chains, s.tile_n);
-  while (ring > 2 && halo_ctas(fixed + ring * b_tile, chains, s.tile_n) < want) --ring;
+  const int want = halo_ctas(fixed + 2 * b_tile, tcols);
+  while (ring > 2 && halo_ctas(fixed + ring * b_tile, tcols) < want) --ring;
   L->resident = 0;
   L->bslots = ring;
   const bool one_n = (F + s.tile_n - 1) / s.tile_n == 1;
   if (one_n && room >= nkb && 8 * (2 * s.stages + 2 * nkb + 5) + 8 <= kBarBytes &&
-      halo_ctas(fixed + nkb * b_tile, chains, s.tile_n) >= halo_ctas(fixed + ring * b_tile, chains, s.tile_n)) {
+      halo_ctas(fixed + nkb * b_tile, tcols) >= halo_ctas(fixed + ring * b_tile, tcols)) {
     L->resident = 1;
     L->bslots = nkb;
   }
@@ -494,9 +557,9 @@ bool halo_layout(const ConvGeom& g, int F, const nk_schedule& s, HaloLayout* L) 
   return L->smem <= kMaxSmem;
 }
 
-template <int MCH>
+template <int MCH, bool STK = false>
 nk_status launch(const HaloParams& p, int grid, int smem, cudaStream_t st) {
-  auto kern = halo_conv_kernel<MCH>;
+  auto kern = halo_conv_kernel<MCH, STK>;
   static int set_bytes[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
@@ -512,7 +575,7 @@ nk_status launch(const HaloParams& p, int grid, int smem, cudaStream_t st) {
 }  // namespace
 
 bool halo_schedule(const ConvGeom& g, const nk_schedule& s) {
-  return taps_of(g) > 1 && s.tile_k == 64 * taps_of(g);
+  return (taps_of(g) > 1 && s.tile_k == 64 * taps_of(g)) || stacked_schedule(g, s);
 }
 
 bool halo_schedule_valid(const ConvGeom& g, int F, const nk_schedule& s) {
@@ -521,21 +584,39 @@ bool halo_schedule_valid(const ConvGeom& g, int F, const nk_schedule& s) {
   if (s.tile_m != 128 && s.tile_m != 256 && s.tile_m != 512) return false;
   if (s.tile_n != 64 && s.tile_n != 128 && s.tile_n != 256) return false;
   if (chains_of(s) * s.tile_n > 256) return false;   // two accumulator buffers in 512 TMEM columns
+  if (stacked_schedule(g, s) && (s.tile_m != 128 || s.tile_n != 64)) return false;   // N = 64 * KW
   if (s.cluster != 1 || s.split_k != 1) return false;
   if (s.stages < 1 || s.stages > 4) return false;
   HaloLayout L;
   return halo_layout(g, F, s, &L);
 }
 
-// Measured on GB300 (ResNet layers, batch 1..32): the window path wins when
-// one 64-channel block covers C; deeper layers (C >= 128) stream so many
-// weight tiles per window that the per-tap path is faster.  One chain and one
-// window slot keep two CTAs (two independent MMA chains) per SM.
+// Measured on GB300 (3x3 ResNet layers, batch 1..32, device time):
+// stacked kernel rows beat the plain window and the per-tap kernels on
+// every stride-1 layer from 56x56x64 to 7x7x512 (e.g. 8x28x28x128: 8.2 us
+// against 14.6 (window) and 20.8 (per-tap); 8x56x56x64: 8.2 against 9.2),
+// with one window slot when one 64-channel block covers C and two
+// otherwise.  A deep layer (C > 64) whose tiles would cover fewer than an
+// eighth of the SMs (batch 1 at 28x28 and below) stays on the per-tap
+// kernel, which splits K to fill the GPU.  Without stacking (KW = 1 or > 4)
+// the plain window kernel wins when one 64-channel block covers C; deeper
+// layers stream so many weight tiles per window that the per-tap path is
+// faster.  One chain and one window slot keep two CTAs (two independent MMA
+// chains) per SM.
 nk_schedule tc_halo_default_schedule(const ConvGeom& g, int F, int sms, bool* ok) {
-  (void)sms;
   nk_schedule best{};
   *ok = false;
-  if (taps_of(g) <= 1 || g.sh != 1 || g.sw != 1 || g.c > 64) return best;
+  if (taps_of(g) <= 1 || g.sh != 1 || g.sw != 1) return best;
+  for (int st : {g.c <= 64 ? 1 : 2, g.c <= 64 ? 2 : 1}) {
+    nk_schedule s{128, 64, 64 * g.kh, 1, st, 1};
+    HaloLayout L;
+    if (!stacked_schedule(g, s) || !halo_schedule_valid(g, F, s) || !halo_layout(g, F, s, &L)) continue;
+    const int64_t units = (int64_t)L.t.tiles_w * L.t.tiles_h * L.t.tiles_b * ((F + 63) / 64);
+    if (g.c > 64 && units * 8 < sms) break;
+    *ok = true;
+    return s;
+  }
+  if (g.c > 64) return best;
   const int tn = F <= 64 ? 64 : F <= 128 ? 128 : 256;
   for (int st = 1; st <= 2; ++st) {
     nk_schedule s{128, tn, 64 * taps_of(g), 1, st, 1};
@@ -601,7 +682,8 @@ nk_status tc_halo_conv(const TcConv& c, const nk_schedule& s, cudaStream_t st) {
   p.c_vec = ((reinterpret_cast<uintptr_t>(c.O) & 15) == 0 && c.F % 4 == 0) ? 1 : 0;
   p.budget = wait_budget();
   if (p.units == 0) return NK_OK;
-  const int grid = std::min(p.units, sms * halo_ctas(L.smem, chains_of(s), s.tile_n));
+  const int grid = std::min(p.units, sms * halo_ctas(L.smem, halo_tmem_cols(chains_of(s), s.tile_n, t.stk)));
+  if (t.stk > 1) return launch<1, true>(p, grid, L.smem, st);
   switch (chains_of(s)) {
     case 1: return launch<1>(p, grid, L.smem, st);
     case 2: return launch<2>(p, grid, L.smem, st);

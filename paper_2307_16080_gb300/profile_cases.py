@@ -117,6 +117,10 @@ def case_conv(reps):
     _conv_layer(reps, None, "bf16 conv 32x56x56x64 3x3 (built-in schedule)")
 
 
+def case_conv_window(reps):
+    _conv_layer(reps, (128, 64, 576, 1, 1, 1), "bf16 conv 32x56x56x64 3x3 (window kernel, taps in K)")
+
+
 def case_conv_tap(reps):
     _conv_layer(reps, (128, 64, 64, 1, 3, 1), "bf16 conv 32x56x56x64 3x3 (per-tap kernel)")
 
@@ -146,7 +150,8 @@ def case_splitk(reps):
         lambda: nk.nk_matmul(a, b, c, precision="f32", schedule=sched, ws=ws), reps), flop=2.0 * M * N * K)
 
 
-CASES = {"cast": case_cast, "amax": case_amax, "direct": case_direct, "conv": case_conv, "conv_tap": case_conv_tap,
+CASES = {"cast": case_cast, "amax": case_amax, "direct": case_direct, "conv": case_conv, "conv_window": case_conv_window,
+         "conv_tap": case_conv_tap,
          "grouped": case_grouped, "splitk": case_splitk}
 
 
