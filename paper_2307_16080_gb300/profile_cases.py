@@ -125,6 +125,27 @@ def case_conv_tap(reps):
     _conv_layer(reps, (128, 64, 64, 1, 3, 1), "bf16 conv 32x56x56x64 3x3 (per-tap kernel)")
 
 
+def case_stack8(reps):
+    """The 20-layer ResNet-style stack at batch 8: packed BF16 weights, BF16
+    activations, built-in schedules, one nk_conv2d call per layer."""
+    calls, flop = [], 0.0
+    for L in synth.resnet_stack(8):
+        oh = (L["H"] + 2 * L["pad"] - L["KH"]) // L["stride"] + 1
+        x = torch.randn(L["N"], L["H"], L["W"], L["C"], device="cuda").abs().to(torch.bfloat16)
+        w = nk.nk_conv2d_pack_weights(torch.randn(L["KH"], L["KW"], L["C"], L["F"], device="cuda") * 0.05)
+        b = torch.randn(L["F"], device="cuda") * 0.1
+        o = torch.empty(L["N"], oh, oh, L["F"], device="cuda")
+        st, pd = (L["stride"],) * 2, (L["pad"],) * 4
+        ws = nk.workspace(nk.nk_conv2d_workspace_size(x, w, o, st, (1, 1), pd, "bf16"))
+        calls.append((x, w, o, st, pd, b, ws))
+        flop += 2.0 * L["N"] * oh * oh * L["F"] * L["KH"] * L["KW"] * L["C"]
+
+    def forward():
+        for (x, w, o, st, pd, b, ws) in calls:
+            nk.nk_conv2d_nhwc_hwcf(x, w, o, st, (1, 1), pd, "bf16", bias=b, relu=True, ws=ws)
+    _emit("resnet stack batch 8, 20 convs (built-in schedules)", _time(forward, reps), flop=flop)
+
+
 def case_grouped(reps):
     shapes = [tuple(int(v) for v in s) for s in synth.grouped_problems(512)]
     a = [torch.empty(M, K, device="cuda").uniform_(-1, 1).to(torch.bfloat16) for (M, N, K) in shapes]
@@ -150,7 +171,7 @@ def case_splitk(reps):
         lambda: nk.nk_matmul(a, b, c, precision="f32", schedule=sched, ws=ws), reps), flop=2.0 * M * N * K)
 
 
-CASES = {"cast": case_cast, "amax": case_amax, "direct": case_direct, "conv": case_conv, "conv_window": case_conv_window,
+CASES = {"cast": case_cast, "amax": case_amax, "direct": case_direct, "conv": case_conv, "conv_window": case_conv_window, "stack8": case_stack8,
          "conv_tap": case_conv_tap,
          "grouped": case_grouped, "splitk": case_splitk}
 
