@@ -211,7 +211,7 @@ def load_corpus(path):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("cmd", choices=["collect", "train", "eval", "all"])
+    ap.add_argument("cmd", choices=["collect", "train", "eval", "all", "defaults"])
     ap.add_argument("--out", default=MODEL_DIR)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--epochs", type=int, default=400)
@@ -226,6 +226,16 @@ def main():
         save_corpus(tr_path, collect(training_problems(), a.reps, log))
         save_corpus(ho_path, collect(heldout_problems(), a.reps, log))
         log(f"collected in {time.time() - t0:.0f} s")
+    if a.cmd == "defaults":
+        # After a change of the built-in default rule: re-derive each stored
+        # problem's default schedule (host logic, no GPU) so that the default
+        # regret of `eval` scores the current rule on the stored timings.
+        for path in (tr_path, ho_path):
+            c = load_corpus(path)
+            c["defaults"] = np.asarray([nt.nk_default_schedule(nt.nk_problem(*[int(v) for v in pr]))
+                                        for pr in c["problems"]], np.int32)
+            save_corpus(path, c)
+            log(f"defaults re-derived for {len(c['problems'])} problems in {path}")
     if a.cmd in ("train", "all"):
         c = load_corpus(tr_path)
         P, ym, ys, hist = train(c["X"], c["y"], a.epochs, log=log)

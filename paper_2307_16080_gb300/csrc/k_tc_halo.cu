@@ -596,13 +596,13 @@ bool halo_schedule_valid(const ConvGeom& g, int F, const nk_schedule& s) {
 // every stride-1 layer from 56x56x64 to 7x7x512 (e.g. 8x28x28x128: 8.2 us
 // against 14.6 (window) and 20.8 (per-tap); 8x56x56x64: 8.2 against 9.2),
 // with one window slot when one 64-channel block covers C and two
-// otherwise.  A deep layer (C > 64) whose tiles would cover fewer than an
-// eighth of the SMs (batch 1 at 28x28 and below) stays on the per-tap
-// kernel, which splits K to fill the GPU.  Without stacking (KW = 1 or > 4)
-// the plain window kernel wins when one 64-channel block covers C; deeper
-// layers stream so many weight tiles per window that the per-tap path is
-// faster.  One chain and one window slot keep two CTAs (two independent MMA
-// chains) per SM.
+// otherwise.  Small grids of deep layers are the exception: with C > 128
+// and tiles covering under an eighth of the SMs (batch 1 at 14x14x256 and
+// 7x7x512), the per-tap kernel with split-K is as fast or faster, so the
+// default leaves them to it.  Where kernel rows cannot be stacked (KW = 1
+// or > 4, e.g. 5x5), the tuner's corpus has the per-tap kernel ahead of the
+// plain window (which stays in the schedule space).  One chain and one
+// window slot keep two CTAs (two independent MMA chains) per SM.
 nk_schedule tc_halo_default_schedule(const ConvGeom& g, int F, int sms, bool* ok) {
   nk_schedule best{};
   *ok = false;
@@ -612,18 +612,9 @@ nk_schedule tc_halo_default_schedule(const ConvGeom& g, int F, int sms, bool* ok
     HaloLayout L;
     if (!stacked_schedule(g, s) || !halo_schedule_valid(g, F, s) || !halo_layout(g, F, s, &L)) continue;
     const int64_t units = (int64_t)L.t.tiles_w * L.t.tiles_h * L.t.tiles_b * ((F + 63) / 64);
-    if (g.c > 64 && units * 8 < sms) break;
+    if (g.c > 128 && units * 8 < sms) break;
     *ok = true;
     return s;
-  }
-  if (g.c > 64) return best;
-  const int tn = F <= 64 ? 64 : F <= 128 ? 128 : 256;
-  for (int st = 1; st <= 2; ++st) {
-    nk_schedule s{128, tn, 64 * taps_of(g), 1, st, 1};
-    if (halo_schedule_valid(g, F, s)) {
-      *ok = true;
-      return s;
-    }
   }
   return best;
 }
