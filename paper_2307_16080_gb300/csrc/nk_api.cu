@@ -270,7 +270,7 @@ nk_status plan_matmul(const nk_tensor* A, const nk_tensor* B, const nk_tensor* C
     int v = 0;
     if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0) sms = v;
   }
-  nk_schedule d = tc_default_schedule(kind, P.M, P.N, P.K, sms);
+  nk_schedule d = matmul_default_schedule(kind, P.M, P.N, P.K, sms);
   nk_schedule& S = P.sched;
   if (S.tile_m == 0) S.tile_m = d.tile_m;
   if (S.tile_n == 0) S.tile_n = d.tile_n;

@@ -245,6 +245,9 @@ uint32_t halo_read_and_clear_errors();
 size_t tc_gemm_ws(const TcGemm& g, const nk_schedule& s);
 // Fills unset fields of `s` with the built-in choice for this problem.
 nk_schedule tc_default_schedule(int kind, int M, int N, int K, int sms);
+// The built-in matmul schedule: tc_default_schedule refitted to the tuner's
+// corpus for BF16 and E4M3 (tune.cu).
+nk_schedule matmul_default_schedule(int kind, int M, int N, int K, int sms);
 bool tc_schedule_valid(int kind, const nk_schedule& s, int M, int N, int K);
 
 }  // namespace nk

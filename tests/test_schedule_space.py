@@ -33,3 +33,62 @@ def test_stacked_schedules_for_deep_layers():
     """C = 512: weights stream through a ring; still a legal schedule."""
     p = nt.conv_problem(8, 7, 7, 512, 512, 3, 3, 1, 1)
     assert _stacked(p)
+
+
+@pytest.mark.parametrize("batch", [1, 8, 32])
+def test_default_schedules_for_the_resnet_stack(batch):
+    """Built-in choice per layer: stacked kernel rows for the stride-1 3x3
+    layers (except batch-1 layers with C > 128, whose few tiles go to the
+    per-tap kernel with split-K), 128 x 64 per-tap tiles everywhere else."""
+    from paper_2307_16080_gb300 import synth
+    for L in synth.resnet_stack(batch):
+        p = nt.conv_problem(L["N"], L["H"], L["W"], L["C"], L["F"], L["KH"], L["KW"], L["stride"], L["pad"])
+        s = nt.nk_default_schedule(p)
+        assert s in nt.nk_enumerate_schedules(p), (L, s)
+        stackable = L["stride"] == 1 and L["KH"] == 3
+        if stackable and not (batch == 1 and L["C"] > 128):
+            assert s[:3] == (128, 64, 192) and s[5] == 1, (L, s)
+        else:
+            assert s[:3] == (128, 64, 64), (L, s)
+
+
+def _default_regret(path):
+    """Regret of the live built-in default rule on a stored corpus of GPU
+    timings (every legal schedule of each problem was timed): mean per
+    (op, precision), and per batch over the conv problems."""
+    import numpy as np
+    from paper_2307_16080_gb300 import costmodel
+    c = costmodel.load_corpus(path)
+    per, stack = {}, {}
+    for i, pr in enumerate(c["problems"]):
+        rows = np.nonzero(c["pid"] == i)[0]
+        ms = {tuple(int(v) for v in c["sched"][j]): float(np.exp(c["y"][j])) for j in rows}
+        d = tuple(nt.nk_default_schedule(nt.nk_problem(*[int(v) for v in pr])))
+        assert d in ms, d
+        best = min(ms.values())
+        per.setdefault((int(pr[0]), int(pr[1])), []).append(ms[d] / best - 1)
+        if int(pr[0]) == nt.NK_OP_CONV2D:
+            b = stack.setdefault(int(pr[5]), [0.0, 0.0])   # problem field n: the batch
+            b[0] += best
+            b[1] += ms[d]
+    return {k: float(np.mean(v)) for k, v in per.items()}, {k: v[1] / v[0] - 1 for k, v in stack.items()}
+
+
+def test_default_regret_on_stored_corpora():
+    """The default rules were fitted to these corpora; this pins their
+    quality, so a change that loses more fails here first."""
+    import os
+    from paper_2307_16080_gb300 import costmodel
+    tr = os.path.join(costmodel.MODEL_DIR, "corpus_train.npz")
+    ho = os.path.join(costmodel.MODEL_DIR, "corpus_heldout.npz")
+    if not (os.path.exists(tr) and os.path.exists(ho)):
+        pytest.skip("no stored corpora")
+    mean_tr, _ = _default_regret(tr)
+    mean_ho, stack = _default_regret(ho)
+    conv, mm = nt.NK_OP_CONV2D, nt.NK_OP_MATMUL
+    bf16, bf16x3, fp8 = (nt.nk.PREC[k] for k in ("bf16", "bf16x3", "fp8"))
+    assert mean_tr[(conv, bf16)] <= 0.08, mean_tr
+    assert mean_tr[(mm, bf16)] <= 0.12 and mean_tr[(mm, fp8)] <= 0.08, mean_tr
+    assert mean_tr[(mm, bf16x3)] <= 0.20, mean_tr
+    assert mean_ho[(conv, bf16)] <= 0.03, mean_ho
+    assert all(r <= 0.05 for r in stack.values()), stack
