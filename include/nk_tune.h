@@ -63,6 +63,21 @@ nk_status nk_default_schedule(const nk_problem* p, nk_schedule* out);
  * nk_matmul_workspace_size / nk_conv2d_workspace_size return.             */
 nk_status nk_workspace_size(const nk_problem* p, const nk_schedule* sched, size_t* bytes);
 
+/* Diagnostics, host only (no GPU): the tile a window schedule (tile_k =
+ * 64*KH*KW, or 64*KH with stacked kernel rows) launches for a stride-1 NHWC
+ * convolution of N x H x W x C -> F with a KH x KW filter, dilations dh, dw
+ * and pad {top, bottom, left, right}.  out[10] (host) receives: the window
+ * row pitch P (pixels), the output columns Q, rows R and images NB of a
+ * tile, the window rows per image WR, the pixels one window box loads, the
+ * rows reserved per window slot, the taps side by side along N (KW when
+ * stacked, else 1), the number of tiles, and the accumulator chains.  Lets
+ * a test check, without a GPU, that every row a valid output reads stays in
+ * its tile, its warp, the window box and the slot.  NK_ERR_NO_SCHEDULE when
+ * `s` is not a legal window schedule there.  The paper has no counterpart. */
+nk_status nk_conv_window_tile(int32_t n, int32_t h, int32_t w, int32_t c, int32_t f, int32_t kh, int32_t kw,
+                              int32_t dh, int32_t dw, const int32_t pad[4], const nk_schedule* s,
+                              int32_t out[10]);
+
 /* Model features of `count` schedules for one problem, host array
  * [count][NK_TUNE_FEATURES]: log2 M, N, K; is_conv; taps; stride; precision
  * one-hot (BF16, FP8, BF16x3); log2 tile_m, tile_n, tile_k; cluster; stages;

@@ -591,6 +591,17 @@ bool halo_schedule_valid(const ConvGeom& g, int F, const nk_schedule& s) {
   return halo_layout(g, F, s, &L);
 }
 
+// Host-side geometry of a window schedule (see nk_conv_window_tile).
+bool halo_tile_info(const ConvGeom& g, int F, const nk_schedule& s, int32_t out[10]) {
+  HaloLayout L;
+  if (!halo_schedule_valid(g, F, s) || !halo_layout(g, F, s, &L)) return false;
+  const HaloTile& t = L.t;
+  const int32_t v[10] = {t.P, t.Q, t.R, t.NB, t.WR, t.rows, t.slot_rows, t.stk,
+                         t.tiles_w * t.tiles_h * t.tiles_b, chains_of(s)};
+  for (int i = 0; i < 10; ++i) out[i] = v[i];
+  return true;
+}
+
 // Measured on GB300 (3x3 ResNet layers, batch 1..32, device time):
 // stacked kernel rows beat the plain window and the per-tap kernels on
 // every stride-1 layer from 56x56x64 to 7x7x512 (e.g. 8x28x28x128: 8.2 us

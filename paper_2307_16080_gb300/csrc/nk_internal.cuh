@@ -241,6 +241,9 @@ bool halo_schedule(const ConvGeom& g, const nk_schedule& s);
 bool halo_schedule_valid(const ConvGeom& g, int F, const nk_schedule& s);
 nk_status tc_halo_conv(const TcConv& c, const nk_schedule& s, cudaStream_t st);
 nk_schedule tc_halo_default_schedule(const ConvGeom& g, int F, int sms, bool* ok);
+// Window tile of a window schedule: P, Q, R, NB, WR, rows, slot_rows, stk,
+// tiles, chains (false when the schedule is not a legal window schedule).
+bool halo_tile_info(const ConvGeom& g, int F, const nk_schedule& s, int32_t out[10]);
 uint32_t halo_read_and_clear_errors();
 size_t tc_gemm_ws(const TcGemm& g, const nk_schedule& s);
 // Fills unset fields of `s` with the built-in choice for this problem.

@@ -524,6 +524,27 @@ nk_status nk_default_schedule(const nk_problem* p, nk_schedule* out) {
   return NK_OK;
 }
 
+nk_status nk_conv_window_tile(int32_t n, int32_t h, int32_t w, int32_t c, int32_t f, int32_t kh, int32_t kw,
+                              int32_t dh, int32_t dw, const int32_t pad[4], const nk_schedule* s, int32_t out[10]) {
+  if (!pad || !s || !out) return fail(NK_ERR_INVALID_ARG, "pad, schedule and out must be non-NULL");
+  if (n < 1 || h < 1 || w < 1 || c < 1 || f < 1 || kh < 1 || kw < 1 || dh < 1 || dw < 1 || pad[0] < 0 ||
+      pad[1] < 0 || pad[2] < 0 || pad[3] < 0)
+    return fail(NK_ERR_INVALID_ARG, "extents, dilations must be positive and pads non-negative");
+  ConvGeom g{};
+  g.n = n; g.h = h; g.w = w; g.c = c;
+  g.kh = kh; g.kw = kw;
+  g.sh = g.sw = 1;
+  g.dh = dh; g.dw = dw;
+  g.pt = pad[0]; g.pl = pad[2];
+  g.oh = h + pad[0] + pad[1] - (kh - 1) * dh;
+  g.ow = w + pad[2] + pad[3] - (kw - 1) * dw;
+  if (g.oh < 1 || g.ow < 1) return fail(NK_ERR_INVALID_ARG, "empty output");
+  const int cp = (c + 7) / 8 * 8;
+  g.sin_w = cp; g.sin_h = (int64_t)w * cp; g.sin_n = (int64_t)h * w * cp;
+  if (!halo_tile_info(g, f, *s, out)) return fail(NK_ERR_NO_SCHEDULE, "not a legal window schedule for this convolution");
+  return NK_OK;
+}
+
 nk_status nk_schedule_features(const nk_problem* p, const nk_schedule* s, int32_t count, float* f) {
   nk_status st = check_problem(p);
   if (st != NK_OK) return st;

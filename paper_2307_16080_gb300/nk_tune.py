@@ -31,6 +31,7 @@ _PS = ctypes.POINTER(nk_schedule)
 SIGNATURES = {
     "nk_enumerate_schedules": (_I32, [_PP, _PS, _I32, ctypes.POINTER(_I32)]),
     "nk_default_schedule": (_I32, [_PP, _PS]),
+    "nk_conv_window_tile": (_I32, [_I32] * 9 + [ctypes.POINTER(_I32), _PS, ctypes.POINTER(_I32)]),
     "nk_workspace_size": (_I32, [_PP, _PS, ctypes.POINTER(_SZ)]),
     "nk_schedule_features": (_I32, [_PP, _PS, _I32, ctypes.POINTER(ctypes.c_float)]),
     "nk_time_schedule": (_I32, [_PP, _PS, _I32, ctypes.POINTER(ctypes.c_float), _P]),
@@ -81,6 +82,18 @@ def nk_default_schedule(p: nk_problem):
     s = nk_schedule()
     _check(lib().nk_default_schedule(ctypes.byref(p), ctypes.byref(s)))
     return s.as_tuple()
+
+
+WINDOW_TILE_FIELDS = ("P", "Q", "R", "NB", "WR", "rows", "slot_rows", "stk", "tiles", "chains")
+
+
+def nk_conv_window_tile(n, h, w, c, f, kh, kw, dilation=(1, 1), pad=(0, 0, 0, 0), schedule=None) -> dict:
+    """Host-side geometry of the tile a window schedule launches (no GPU)."""
+    pd = (_I32 * 4)(*pad)
+    out = (_I32 * 10)()
+    _check(lib().nk_conv_window_tile(n, h, w, c, f, kh, kw, dilation[0], dilation[1], pd,
+                                     ctypes.byref(nk_schedule(*schedule)), out))
+    return dict(zip(WINDOW_TILE_FIELDS, list(out)))
 
 
 def nk_workspace_size(p: nk_problem, schedule=None) -> int:
