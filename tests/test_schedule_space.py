@@ -92,3 +92,31 @@ def test_default_regret_on_stored_corpora():
     assert mean_tr[(mm, bf16x3)] <= 0.20, mean_tr
     assert mean_ho[(conv, bf16)] <= 0.03, mean_ho
     assert all(r <= 0.05 for r in stack.values()), stack
+
+
+def test_defaults_are_legal_schedules_everywhere():
+    """Every built-in default lies in the problem's legal schedule space:
+    matmuls from one row to 8192 (ragged and tiny included) in every
+    tensor-core precision, and seeded random convolutions."""
+    from paper_2307_16080_gb300 import synth
+    sizes = [1, 16, 100, 128, 300, 1000, 2048, 8192]
+    for M, N, K in zip(sizes * 3, sizes[::-1] * 3, [16, 64, 700, 4096, 8192, 1, 33, 256] * 3):
+        for prec in ("bf16", "fp8", "bf16x3"):
+            p = nt.matmul_problem(M, N, K, prec)
+            assert nt.nk_default_schedule(p) in nt.nk_enumerate_schedules(p), (M, N, K, prec)
+    u = synth.uniform01(95, 0, 6 * 40)
+    for g in range(40):
+        r = u[6 * g: 6 * g + 6]
+        k = (1, 3, 5)[int(r[0] * 3)]
+        s = 1 + int(r[1] * 2)
+        h = k + int(r[2] * 60)
+        n, c, f = 1 + int(r[3] * 32), 8 * (1 + int(r[4] * 64)), 8 * (1 + int(r[5] * 64))
+        for prec in ("bf16", "fp8"):
+            p = nt.conv_problem(n, h, h, c, f, k, k, s, k // 2, prec)
+            assert nt.nk_default_schedule(p) in nt.nk_enumerate_schedules(p), (n, h, c, f, k, s, prec)
+
+
+def test_headline_gemms_keep_the_wide_pair_tile():
+    for prec, tk in (("bf16", 64), ("fp8", 128)):
+        for n in (4096, 8192):
+            assert nt.nk_default_schedule(nt.matmul_problem(n, n, n, prec)) == (256, 512, tk, 2, 4, 1)
