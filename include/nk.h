@@ -404,9 +404,10 @@ nk_status nk_sync_status(void* stream);
  * 0 restores the default.  Lets a test drive the timeout path on purpose. */
 nk_status nk_set_wait_budget(int64_t iterations);
 
-/* Programmatic dependent launch (on by default).  When on, every kernel of
- * this library is launched so that it may start while the kernel before it
- * on the same stream is finishing: it prepares its shared memory, mbarriers
+/* Programmatic dependent launch (on by default).  When on, every compute
+ * kernel of this library (not the tuner's own timing kernels) is launched
+ * so that it may start while the kernel before it on the same stream is
+ * finishing: it prepares its shared memory, mbarriers
  * and tensor memory, then waits, on the device, until all earlier work on
  * the stream has completed and is visible before it reads or writes any
  * global memory.  Results are identical either way; only the gap between
