@@ -175,9 +175,12 @@ typedef struct {
 nk_status nk_elementwise(const nk_tensor* X, nk_tensor* Y, const nk_ew_program* prog,
                          void* stream);
 
-/* Tile schedule.  tile_m x tile_n output tile per CTA (cluster 2 pairs two
- * CTAs along M that share B tiles through TMA multicast), tile_k reduction
- * depth per pipeline stage, stages = shared-memory ring depth, split_k =
+/* Tile schedule.  tile_m x tile_n output tile per CTA; cluster 2 (only with
+ * tile_m 256) makes two CTAs on two SMs a pair that computes one 256-row
+ * tile with 2-SM MMAs, each CTA loading its own 128 rows of A and half of B
+ * (no TMA load is multicast); tile_m 256 / 512 with cluster 1 is one CTA
+ * holding 2 / 4 stacked 128-row tiles.  tile_k reduction depth per pipeline
+ * stage, stages = shared-memory ring depth, split_k =
  * number of K slices reduced by a separate fixed-order pass.  Any field 0
  * means "choose".  For the shared-window convolution (tile_k = 64*KH*KW,
  * see nk_conv2d_nhwc_hwcf) stages counts window slots and split_k is 1.    */

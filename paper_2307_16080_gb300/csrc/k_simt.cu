@@ -507,8 +507,9 @@ namespace {
 constexpr size_t kStaticScratchFloats = size_t(4) << 20;   // 16 MiB of FP32 partials
 __device__ __align__(256) float g_splitk_scratch[kStaticScratchFloats];
 
+constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mu;
-float* g_scratch_addr[64];   // device address of g_splitk_scratch, per device
+float* g_scratch_addr[kMaxDevices];   // device address of g_splitk_scratch, per device ordinal
 
 }  // namespace
 }  // namespace nk
@@ -518,7 +519,8 @@ extern "C" nk_status nk_matmul_f32_splitk_noalloc(const float* A, int64_t lda, c
                                                   int32_t N, int32_t K, int32_t split_k,
                                                   void* stream) {
   using namespace nk;
-  nk_status s = require_device();
+  int sms = 0;
+  nk_status s = require_device(&sms);
   if (s != NK_OK) return s;
   if (M < 0 || N < 0 || K < 0) return fail(NK_ERR_INVALID_ARG, "negative extent");
   if (split_k < 1 || split_k > 32) return fail(NK_ERR_INVALID_ARG, "split_k must be in [1, 32]");
@@ -532,6 +534,9 @@ extern "C" nk_status nk_matmul_f32_splitk_noalloc(const float* A, int64_t lda, c
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices)
+    return fail(NK_ERR_UNSUPPORTED, "device ordinal %d: the static scratch table holds %d devices", dev,
+                kMaxDevices);
   float* scratch = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_scratch_mu);
@@ -551,7 +556,9 @@ extern "C" nk_status nk_matmul_f32_splitk_noalloc(const float* A, int64_t lda, c
   p.C = C; p.scm = ldc; p.scn = 1;
   p.M = M; p.N = N; p.K = K;
   p.alpha = 1.f; p.beta = 0.f;
-  const int tile = (int64_t)((M + 127) / 128) * ((N + 127) / 128) < 152 ? 64 : 128;
+  // The tile nk_matmul's FP32 rule picks: 64 x 64 while 128 x 128 tiles
+  // would not give every SM one.
+  const int tile = (int64_t)((M + 127) / 128) * ((N + 127) / 128) < sms ? 64 : 128;
   // Every slice overwrites its whole [M,N] partial tile, so the scratch needs
   // no clearing between calls.
   return simt_gemm(p, tile, split_k, scratch, kStaticScratchFloats * sizeof(float),

@@ -8,8 +8,9 @@
 //
 //   warp 0      TMA producer: A and B tiles (128-byte rows, 128B swizzle) into
 //               a STAGES-deep shared-memory ring, one mbarrier pair per slot.
-//               With cluster 2 the two CTAs of a pair share B: each loads
-//               half of the B tile and multicasts it to both.
+//               Every CTA loads its own tiles: a cluster of two is a CTA pair
+//               (below), in which each CTA loads its half of B; no TMA load
+//               is multicast.
 //   warp 1      allocates TMEM; one thread issues tcgen05.mma (M=128, N=BN,
 //               K=16 BF16 / K=32 E4M3 per instruction) into a double-buffered
 //               FP32 accumulator in TMEM, and tcgen05.commit frees each slot.
@@ -232,7 +233,7 @@ __device__ __forceinline__ int conv_row(const ConvTile& c, int tm, int r) {
 // keep several independent MMA chains in flight.
 template <int KIND, int CL, bool GROUPED, bool CONV = false, bool PAIR = false, bool WIDE = false, int MCH = 1>
 __global__ void __launch_bounds__(WIDE ? 320 : 192, 1) tc_gemm_kernel(const __grid_constant__ TcParams p) {
-  static_assert(!PAIR || CL == 2, "a CTA pair is a cluster of two");
+  static_assert(PAIR == (CL == 2), "a cluster of two is a CTA pair, and a CTA pair is a cluster of two");
   static_assert(!WIDE || (PAIR && KIND != TC_BF16X3 && !GROUPED), "wide tiles are pair tiles");
   static_assert(MCH == 1 || (!PAIR && !GROUPED && KIND != TC_BF16X3 && CL == 1), "tall tiles: one CTA");
   extern __shared__ uint8_t smem_raw[];
@@ -278,7 +279,7 @@ __global__ void __launch_bounds__(WIDE ? 320 : 192, 1) tc_gemm_kernel(const __gr
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       ptx::mbar_init(full_bar(s), 1);
-      ptx::mbar_init(empty_bar(s), PAIR ? 1 : CL);
+      ptx::mbar_init(empty_bar(s), 1);
     }
     for (int b = 0; b < 2; ++b) {
       ptx::mbar_init(tfull_bar(b), 1);
@@ -326,7 +327,6 @@ __global__ void __launch_bounds__(WIDE ? 320 : 192, 1) tc_gemm_kernel(const __gr
     if (lane == 0) {
       int it = 0;
       const int kblk = KIND == TC_FP8 ? 128 : 64;   // elements per 128-byte row
-      const int b_rows = p.bn / CL;
       bool ok = true;
       for (int u = cluster_id; u < p.units && ok; u += n_clusters) {
         const UnitView t = view_unit<GROUPED>(p, u, CL, rank);
@@ -384,29 +384,20 @@ __global__ void __launch_bounds__(WIDE ? 320 : 192, 1) tc_gemm_kernel(const __gr
               ptx::tma_load_4d(a_smem(s, 0) + ch * kBM * kRowBytes, t.ma, full_bar(s), c0,
                                tw * c.Q * c.sw + kw * c.dw - c.pl, th * c.R * c.sh + kh * c.dh - c.pt, tb * c.NB);
             }
-            const int fy = t.tn * p.bn + rank * b_rows;
-            if (CL == 2)
-              ptx::tma_load_3d_mc(b_smem(s, 0) + rank * b_rows * kRowBytes, t.mb, full_bar(s), c0, tap,
-                                  fy, (uint16_t)0x3);
-            else
-              ptx::tma_load_3d(b_smem(s, 0), t.mb, full_bar(s), c0, tap, fy);
+            ptx::tma_load_3d(b_smem(s, 0), t.mb, full_bar(s), c0, tap, t.tn * p.bn);
             continue;
           }
           ptx::mbar_arrive_expect_tx(full_bar(s), (uint32_t)sb);
           const int kx = kb * kblk;
           const int ay = t.tm * MCH * kBM;
-          const int by = t.tn * p.bn + rank * b_rows;
+          const int by = t.tn * p.bn;
           const int nparts = KIND == TC_BF16X3 ? 2 : 1;
           for (int part = 0; part < nparts; ++part) {
             const CUtensorMap* ma = part ? &p.tmA2 : t.ma;
             const CUtensorMap* mb = part ? &p.tmB2 : t.mb;
             for (int ch = 0; ch < MCH; ++ch)
               ptx::tma_load_2d(a_smem(s, part) + ch * kBM * kRowBytes, ma, full_bar(s), kx, ay + ch * kBM);
-            if (CL == 2)
-              ptx::tma_load_2d_mc(b_smem(s, part) + rank * b_rows * kRowBytes, mb, full_bar(s), kx, by,
-                                  (uint16_t)0x3);
-            else
-              ptx::tma_load_2d(b_smem(s, part), mb, full_bar(s), kx, by);
+            ptx::tma_load_2d(b_smem(s, part), mb, full_bar(s), kx, by);
           }
         }
       }
@@ -470,7 +461,6 @@ __global__ void __launch_bounds__(WIDE ? 320 : 192, 1) tc_gemm_kernel(const __gr
             }
           }
           if (PAIR) ptx::tc_commit_pair_mc(empty_bar(s), (uint16_t)0x3);
-          else if (CL == 2) ptx::tc_commit_mc(empty_bar(s), (uint16_t)0x3);
           else ptx::tc_commit(empty_bar(s));
         }
         if (!ok) break;
@@ -719,9 +709,10 @@ int ctas_per_sm(int kind, const nk_schedule& s) {
 bool tc_schedule_valid(int kind, const nk_schedule& s, int M, int N, int K) {
   (void)M; (void)N; (void)K;
   // tile_m 256 with cluster 2 = a CTA pair issuing 2-SM MMAs; tile_m 256 / 512
-  // with cluster 1 = a tall tile of 2 / 4 accumulator chains sharing B.
+  // with cluster 1 = a tall tile of 2 / 4 accumulator chains sharing B.  A
+  // cluster of two is always a CTA pair: no schedule multicasts a TMA load.
   if (s.tile_m != 128 && s.tile_m != 256 && s.tile_m != 512) return false;
-  if (s.tile_m == 512 && s.cluster != 1) return false;
+  if (s.cluster == 2 && s.tile_m != 256) return false;
   if (chains_of(s) > 1 && (kind == TC_BF16X3 || chains_of(s) * s.tile_n > 256)) return false;
   if (s.tile_n != 64 && s.tile_n != 128 && s.tile_n != 256 && s.tile_n != 512) return false;
   if (s.tile_n == 512 && (s.tile_m != 256 || kind == TC_BF16X3)) return false;   // wide pair tiles only
@@ -860,15 +851,12 @@ nk_status tc_gemm(const TcGemm& g, const nk_schedule& s, void* ws, size_t ws_byt
     if (g.kind == TC_FP8) status = launch<TC_FP8, 1, false, false, false, false, 4>(p, grid, smem, st);
     else status = launch<TC_BF16, 1, false, false, false, false, 4>(p, grid, smem, st);
   } else
-  switch (g.kind * 3 + (pair ? 2 : CL - 1)) {
-    case TC_BF16 * 3 + 0: status = launch<TC_BF16, 1>(p, grid, smem, st); break;
-    case TC_BF16 * 3 + 1: status = launch<TC_BF16, 2>(p, grid, smem, st); break;
-    case TC_BF16 * 3 + 2: status = launch<TC_BF16, 2, false, false, true>(p, grid, smem, st); break;
-    case TC_FP8 * 3 + 0: status = launch<TC_FP8, 1>(p, grid, smem, st); break;
-    case TC_FP8 * 3 + 1: status = launch<TC_FP8, 2>(p, grid, smem, st); break;
-    case TC_FP8 * 3 + 2: status = launch<TC_FP8, 2, false, false, true>(p, grid, smem, st); break;
-    case TC_BF16X3 * 3 + 0: status = launch<TC_BF16X3, 1>(p, grid, smem, st); break;
-    case TC_BF16X3 * 3 + 1: status = launch<TC_BF16X3, 2>(p, grid, smem, st); break;
+  switch (g.kind * 2 + (pair ? 1 : 0)) {
+    case TC_BF16 * 2 + 0: status = launch<TC_BF16, 1>(p, grid, smem, st); break;
+    case TC_BF16 * 2 + 1: status = launch<TC_BF16, 2, false, false, true>(p, grid, smem, st); break;
+    case TC_FP8 * 2 + 0: status = launch<TC_FP8, 1>(p, grid, smem, st); break;
+    case TC_FP8 * 2 + 1: status = launch<TC_FP8, 2, false, false, true>(p, grid, smem, st); break;
+    case TC_BF16X3 * 2 + 0: status = launch<TC_BF16X3, 1>(p, grid, smem, st); break;
     default: status = launch<TC_BF16X3, 2, false, false, true>(p, grid, smem, st); break;
   }
   if (status != NK_OK || splits == 1) return status;
@@ -983,8 +971,8 @@ bool tc_conv_schedule_valid(const ConvGeom& g, int F, const nk_schedule& s, int 
   if (kind == TC_BF16 && halo_schedule(g, s)) return halo_schedule_valid(g, F, s);
   if (kind != TC_BF16 && kind != TC_FP8) return false;
   if (g.sw > 8 || g.sh > 8 || s.tile_n == 512) return false;
-  // E4M3 convolutions: one CTA or a multicast cluster, tall tiles (no CTA pairs)
-  if (kind == TC_FP8 && s.tile_m == 256 && s.cluster == 2) return false;
+  // E4M3 convolutions: one CTA per tile, tall tiles included (no CTA pairs)
+  if (kind == TC_FP8 && s.cluster == 2) return false;
   return tc_schedule_valid(kind, s, g.n * g.oh * g.ow, F, g.kh * g.kw * g.c);
 }
 
@@ -1092,12 +1080,10 @@ nk_status tc_conv(const TcConv& c, const nk_schedule& s, void* ws, size_t ws_byt
   if (kind == TC_FP8) {
     if (mch == 2) status = launch<TC_FP8, 1, false, true, false, false, 2>(p, grid, smem, st);
     else if (mch == 4) status = launch<TC_FP8, 1, false, true, false, false, 4>(p, grid, smem, st);
-    else if (CL == 2) status = launch<TC_FP8, 2, false, true>(p, grid, smem, st);
     else status = launch<TC_FP8, 1, false, true>(p, grid, smem, st);
   } else if (mch == 2) status = launch<TC_BF16, 1, false, true, false, false, 2>(p, grid, smem, st);
   else if (mch == 4) status = launch<TC_BF16, 1, false, true, false, false, 4>(p, grid, smem, st);
-  else if (s.tile_m == 256) status = launch<TC_BF16, 2, false, true, true>(p, grid, smem, st);
-  else if (CL == 2) status = launch<TC_BF16, 2, false, true>(p, grid, smem, st);
+  else if (CL == 2) status = launch<TC_BF16, 2, false, true, true>(p, grid, smem, st);
   else status = launch<TC_BF16, 1, false, true>(p, grid, smem, st);
   if (status != NK_OK || splits == 1) return status;
   SplitReduce r{};

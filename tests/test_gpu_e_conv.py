@@ -60,7 +60,7 @@ def test_bf16_conv_small_ints_bitwise(nk, case):
     np.testing.assert_array_equal(_conv(nk, I, W, st, dl, pad), O.conv2d_nhwc_hwcf(I, W, st, dl, pad))
 
 
-@pytest.mark.parametrize("sched", [(128, 64, 64, 1, 4, 1), (128, 128, 64, 2, 3, 1), (128, 64, 64, 2, 5, 3),
+@pytest.mark.parametrize("sched", [(128, 64, 64, 1, 4, 1), (128, 128, 64, 1, 3, 1), (128, 64, 64, 1, 5, 3),
                                    (128, 256, 64, 1, 4, 2), (256, 128, 64, 2, 4, 1), (256, 64, 64, 2, 6, 3),
                                    (256, 128, 64, 1, 4, 1), (512, 64, 64, 1, 3, 1), (512, 64, 64, 1, 2, 3),
                                    (256, 128, 64, 1, 2, 3), (256, 128, 64, 1, 3, 2)])
@@ -209,7 +209,7 @@ FP8_CASES = [
 
 
 @pytest.mark.parametrize("case", FP8_CASES)
-@pytest.mark.parametrize("sched", [None, (128, 64, 128, 1, 3, 1), (128, 128, 128, 2, 3, 1), (256, 64, 128, 1, 3, 1),
+@pytest.mark.parametrize("sched", [None, (128, 64, 128, 1, 3, 1), (128, 128, 128, 1, 4, 1), (256, 64, 128, 1, 3, 1),
                                    (512, 64, 128, 1, 2, 1), (128, 128, 128, 1, 3, 3)])
 def test_fp8_conv_exact_codes_bitwise(nk, case, sched):
     """E4M3 convolution with per-tensor amax scales (s_i, s_w), dequantised by
@@ -246,9 +246,9 @@ def test_fp8_conv_rejects_pairs_and_bf16_input(nk):
     I = synth.small_ints(98, 0, (1, 8, 8, 64))
     W = synth.small_ints(98, 1, (3, 3, 64, 64))
     out = torch.empty(1, 8, 8, 64, device=DEV)
-    with pytest.raises(nk.NkError):
-        nk.nk_conv2d_nhwc_hwcf(dev(I), dev(W), out, pad=(1, 1, 1, 1), precision="fp8",
-                               schedule=(256, 64, 128, 2, 3, 1))
+    for sched in [(256, 64, 128, 2, 3, 1), (128, 64, 128, 2, 3, 1)]:
+        with pytest.raises(nk.NkError):
+            nk.nk_conv2d_nhwc_hwcf(dev(I), dev(W), out, pad=(1, 1, 1, 1), precision="fp8", schedule=sched)
     with pytest.raises(nk.NkError):
         nk.nk_conv2d_nhwc_hwcf(dev(I).to(torch.bfloat16), dev(W), out, pad=(1, 1, 1, 1), precision="fp8")
 

@@ -120,3 +120,44 @@ def test_headline_gemms_keep_the_wide_pair_tile():
     for prec, tk in (("bf16", 64), ("fp8", 128)):
         for n in (4096, 8192):
             assert nt.nk_default_schedule(nt.matmul_problem(n, n, n, prec)) == (256, 512, tk, 2, 4, 1)
+
+
+def test_no_tma_load_is_multicast():
+    """Every TMA load of the library lands in the issuing CTA's own shared
+    memory (a CTA pair's loads signal the even CTA's barrier, but each CTA
+    copies its own operand halves): no cp.async.bulk instruction in the
+    sources carries a .multicast qualifier."""
+    import glob
+    import os
+    import re
+    root = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                        "paper_2307_16080_gb300", "csrc")
+    srcs = glob.glob(os.path.join(root, "*.cu")) + glob.glob(os.path.join(root, "*.cuh"))
+    assert srcs
+    for path in srcs:
+        text = open(path).read()
+        # an asm string may span several adjacent literals: join each asm block
+        for block in re.findall(r"asm\s+volatile\s*\((.*?)\);", text, flags=re.S):
+            if "cp.async.bulk" in block:
+                assert "multicast" not in block, path
+
+
+@pytest.mark.parametrize("prob", [
+    ("mm", 8192, 8192, 8192, "bf16"), ("mm", 300, 520, 700, "bf16"), ("mm", 4096, 4096, 4096, "fp8"),
+    ("mm", 1024, 1024, 4096, "bf16x3"), ("conv", 8, 56, 56, 64, 64, 3, 3, 1, 1), ("conv", 32, 14, 14, 256, 512, 3, 3, 2, 1),
+])
+def test_cluster_two_is_always_a_cta_pair(prob):
+    """cluster 2 only with tile_m 256 (a CTA pair issuing 2-SM MMAs); E4M3
+    convolutions use one CTA per tile."""
+    precs = ["bf16", "fp8"] if prob[0] == "conv" else [prob[-1]]
+    for prec in precs:
+        if prob[0] == "mm":
+            p = nt.matmul_problem(prob[1], prob[2], prob[3], prec)
+        else:
+            p = nt.conv_problem(*prob[1:], precision=prec)
+        scheds = nt.nk_enumerate_schedules(p)
+        assert scheds
+        for s in scheds:
+            if s[3] == 2:
+                assert s[0] == 256, s
+                assert not (prob[0] == "conv" and prec == "fp8"), s
