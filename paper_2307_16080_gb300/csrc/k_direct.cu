@@ -387,6 +387,7 @@ using namespace nk;
 extern "C" nk_status nk_conv2d_nchw_fchw(const nk_tensor* I, const nk_tensor* K, nk_tensor* O,
                                          const int64_t stride[2], const int64_t dilation[2],
                                          const int64_t pad[4], const nk_epilogue* epi, void* stream) {
+  nk::NvtxRange nvtx_range_("nk_conv2d_nchw_fchw");
   nk_status s = NK_OK;
   if (!I || !K || !O || !stride || !dilation || !pad) return fail(NK_ERR_INVALID_ARG, "null argument");
   if (I->rank != 4 || K->rank != 4 || O->rank != 4) return fail(NK_ERR_INVALID_ARG, "I, K, O must have rank 4");

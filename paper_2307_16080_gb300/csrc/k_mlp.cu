@@ -224,6 +224,7 @@ size_t nk_mlp_workspace_size(int64_t B) {
 }
 
 nk_status nk_mlp_forward(const float* params, const float* X, int64_t B, float* y, void* stream) {
+  nk::NvtxRange nvtx_range_("nk_mlp_forward");
   nk_status s = require_device();
   if (s != NK_OK) return s;
   if (B < 0) return fail(NK_ERR_INVALID_ARG, "negative batch");
@@ -237,6 +238,7 @@ nk_status nk_mlp_forward(const float* params, const float* X, int64_t B, float* 
 
 nk_status nk_mlp_grad(const float* params, const float* X, const float* t, int64_t B, float* grad, float* loss,
                       void* ws, size_t ws_bytes, void* stream) {
+  nk::NvtxRange nvtx_range_("nk_mlp_grad");
   nk_status s = require_device();
   if (s != NK_OK) return s;
   if (B <= 0) return fail(NK_ERR_INVALID_ARG, "batch must be positive");
@@ -255,6 +257,7 @@ nk_status nk_mlp_grad(const float* params, const float* X, const float* t, int64
 
 nk_status nk_mlp_adam(float* params, const float* grad, float* m, float* v, int32_t step, float lr, float beta1,
                       float beta2, float eps, void* stream) {
+  nk::NvtxRange nvtx_range_("nk_mlp_adam");
   nk_status s = require_device();
   if (s != NK_OK) return s;
   if (step < 1) return fail(NK_ERR_INVALID_ARG, "Adam step counts from 1");

@@ -518,6 +518,7 @@ extern "C" nk_status nk_matmul_f32_splitk_noalloc(const float* A, int64_t lda, c
                                                   int64_t ldb, float* C, int64_t ldc, int32_t M,
                                                   int32_t N, int32_t K, int32_t split_k,
                                                   void* stream) {
+  nk::NvtxRange nvtx_range_("nk_matmul_f32_splitk_noalloc");
   using namespace nk;
   int sms = 0;
   nk_status s = require_device(&sms);

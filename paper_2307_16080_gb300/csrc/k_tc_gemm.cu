@@ -1378,6 +1378,7 @@ nk_status nk_grouped_workspace_size(int32_t G, const nk_gemm_group* groups, int3
 
 nk_status nk_grouped_plan_create(int32_t G, const nk_gemm_group* groups, int32_t precision,
                                  const nk_schedule* sched, nk_grouped_plan** out) {
+  nk::NvtxRange nvtx_range_("nk_grouped_plan_create");
   if (!out) return fail(NK_ERR_INVALID_ARG, "plan is NULL");
   *out = nullptr;
   auto* plan = new nk_grouped_plan();
@@ -1400,6 +1401,7 @@ nk_status nk_grouped_plan_create(int32_t G, const nk_gemm_group* groups, int32_t
 
 nk_status nk_conv2d_grouped_plan_create(int32_t G, const nk_conv_group* groups, const nk_schedule* sched,
                                         nk_grouped_plan** out) {
+  nk::NvtxRange nvtx_range_("nk_conv2d_grouped_plan_create");
   if (!out) return fail(NK_ERR_INVALID_ARG, "plan is NULL");
   *out = nullptr;
   auto* plan = new nk_grouped_plan();
@@ -1421,6 +1423,7 @@ nk_status nk_conv2d_grouped_plan_create(int32_t G, const nk_conv_group* groups, 
 }
 
 nk_status nk_grouped_plan_run(const nk_grouped_plan* plan, void* stream) {
+  nk::NvtxRange nvtx_range_("nk_grouped_plan_run");
   if (!plan) return fail(NK_ERR_INVALID_ARG, "plan is NULL");
   if (plan->units == 0) return NK_OK;
   if (plan->conv)
@@ -1439,6 +1442,7 @@ nk_status nk_grouped_plan_destroy(nk_grouped_plan* plan) {
 
 nk_status nk_batch_matmul_grouped(int32_t G, const nk_gemm_group* groups, int32_t precision,
                                   const nk_schedule* sched, void* ws, size_t ws_bytes, void* stream) {
+  nk::NvtxRange nvtx_range_("nk_batch_matmul_grouped");
   const size_t bytes = grouped_bytes(G);
   if (G > 0 && (!ws || ws_bytes < bytes))
     return fail(NK_ERR_WORKSPACE, "grouped GEMM needs %zu bytes of workspace", bytes);

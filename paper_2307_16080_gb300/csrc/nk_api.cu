@@ -374,6 +374,7 @@ nk_status nk_matmul_workspace_size(const nk_tensor* A, const nk_tensor* B, const
 nk_status nk_matmul(const nk_tensor* A, const nk_tensor* B, nk_tensor* C, int32_t precision,
                     const nk_epilogue* epi, const nk_schedule* sched, void* ws, size_t ws_bytes,
                     void* stream) {
+  nk::NvtxRange nvtx_range_("nk_matmul");
   MatmulPlan P;
   nk_status s = plan_matmul(A, B, C, precision, sched, P);
   if (s != NK_OK) return s;
@@ -621,6 +622,7 @@ nk_status nk_conv2d_nhwc_hwcf(const nk_tensor* I, const nk_tensor* W, nk_tensor*
                               const int64_t stride[2], const int64_t dilation[2],
                               const int64_t pad[4], int32_t precision, const nk_epilogue* epi,
                               const nk_schedule* sched, void* ws, size_t ws_bytes, void* stream) {
+  nk::NvtxRange nvtx_range_("nk_conv2d_nhwc_hwcf");
   ConvGeom g;
   nk_status s = plan_conv(I, W, O, stride, dilation, pad, g);
   if (s != NK_OK) return s;
@@ -709,6 +711,7 @@ nk_status nk_conv2d_nhwc_hwcf(const nk_tensor* I, const nk_tensor* W, nk_tensor*
 }
 
 nk_status nk_conv2d_pack_weights(const nk_tensor* W, void* Wp, int64_t ldw, void* stream) {
+  nk::NvtxRange nvtx_range_("nk_conv2d_pack_weights");
   if (!W || !Wp) return fail(NK_ERR_INVALID_ARG, "W and Wp must be non-NULL");
   if (W->rank != 4 || W->dtype != NK_F32) return fail(NK_ERR_INVALID_ARG, "W must be a rank-4 FP32 tensor");
   if (W->stride[3] != 1 || W->stride[2] != W->shape[3] || W->stride[1] != W->shape[2] * W->shape[3] ||
@@ -726,6 +729,7 @@ nk_status nk_conv2d_pack_weights(const nk_tensor* W, void* Wp, int64_t ldw, void
 
 // ------------------------------------------------------------- elementwise
 nk_status nk_elementwise(const nk_tensor* X, nk_tensor* Y, const nk_ew_program* prog, void* stream) {
+  nk::NvtxRange nvtx_range_("nk_elementwise");
   if (!X || !Y) return fail(NK_ERR_INVALID_ARG, "X and Y must be non-NULL");
   if (X->rank < 1 || X->rank > 4 || Y->rank != X->rank)
     return fail(NK_ERR_INVALID_ARG, "X and Y need the same rank, 1..4");
@@ -751,6 +755,7 @@ nk_status nk_elementwise(const nk_tensor* X, nk_tensor* Y, const nk_ew_program* 
 size_t nk_prep_workspace_size(int64_t n) { return prep_amax_ws(n); }
 
 nk_status nk_amax(const float* x, int64_t n, float* amax, void* ws, size_t ws_bytes, void* stream) {
+  nk::NvtxRange nvtx_range_("nk_amax");
   nk_status s = require_device();
   if (s != NK_OK) return s;
   if (n < 0) return fail(NK_ERR_INVALID_ARG, "negative length");
@@ -769,6 +774,7 @@ static nk_status check_cast(const float* in, int64_t rows, int64_t cols, int64_t
 
 nk_status nk_cast_bf16(const float* in, int64_t rows, int64_t cols, int64_t ld_in, void* out,
                        int64_t ld_out, int32_t transpose, void* stream) {
+  nk::NvtxRange nvtx_range_("nk_cast_bf16");
   nk_status s = check_cast(in, rows, cols, ld_in, out, ld_out, transpose);
   if (s != NK_OK) return s;
   return prep_cast(0, in, rows, cols, ld_in, nullptr, out, nullptr, ld_out, transpose, nullptr,
@@ -777,6 +783,7 @@ nk_status nk_cast_bf16(const float* in, int64_t rows, int64_t cols, int64_t ld_i
 
 nk_status nk_cast_fp8(const float* in, int64_t rows, int64_t cols, int64_t ld_in, const float* amax,
                       void* out, int64_t ld_out, int32_t transpose, float* scale_out, void* stream) {
+  nk::NvtxRange nvtx_range_("nk_cast_fp8");
   nk_status s = check_cast(in, rows, cols, ld_in, out, ld_out, transpose);
   if (s != NK_OK) return s;
   if (!amax) return fail(NK_ERR_INVALID_ARG, "amax is NULL");
@@ -786,6 +793,7 @@ nk_status nk_cast_fp8(const float* in, int64_t rows, int64_t cols, int64_t ld_in
 
 nk_status nk_split_bf16x3(const float* in, int64_t rows, int64_t cols, int64_t ld_in, void* hi,
                           void* lo, int64_t ld_out, int32_t transpose, void* stream) {
+  nk::NvtxRange nvtx_range_("nk_split_bf16x3");
   nk_status s = check_cast(in, rows, cols, ld_in, hi, ld_out, transpose);
   if (s != NK_OK) return s;
   if (!lo && rows * cols) return fail(NK_ERR_INVALID_ARG, "lo is NULL");
@@ -798,6 +806,7 @@ size_t nk_norm_workspace_size(int64_t M, int64_t N) { return norm_ws(M, N); }
 
 nk_status nk_rel_frobenius(const float* C, int64_t ldc, const double* R, int64_t ldr, int64_t M,
                            int64_t N, double* sumsq, void* ws, size_t ws_bytes, void* stream) {
+  nk::NvtxRange nvtx_range_("nk_rel_frobenius");
   nk_status s = require_device();
   if (s != NK_OK) return s;
   if (M < 0 || N < 0) return fail(NK_ERR_INVALID_ARG, "negative extent");

@@ -6,6 +6,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <functional>
@@ -16,6 +17,18 @@
 #include "ew.cuh"
 
 namespace nk {
+
+// ------------------------------------------------------------------ NVTX
+// A named range on the calling host thread for as long as the object lives:
+// every public compute call and each phase of the schedule search opens one,
+// so a profiler's timeline shows which library call issued which kernels.
+// NVTX is header-only here; without an attached tool a range costs a branch.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // ----------------------------------------------------------------- errors
 nk_status fail(nk_status s, const char* fmt, ...);

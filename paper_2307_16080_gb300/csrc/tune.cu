@@ -595,6 +595,7 @@ nk_status nk_workspace_size(const nk_problem* p, const nk_schedule* sched, size_
 
 nk_status nk_grouped_tune(int32_t G, const nk_gemm_group* groups, int32_t precision, int32_t reps,
                           nk_schedule* best, nk_tune_report* rep, void* stream) {
+  nk::NvtxRange nvtx_range_("nk_grouped_tune");
   if (!best) return fail(NK_ERR_INVALID_ARG, "best is NULL");
   if (G < 1 || !groups) return fail(NK_ERR_INVALID_ARG, "need at least one group");
   nk_status st = require_device();
@@ -647,6 +648,7 @@ nk_status nk_grouped_tune(int32_t G, const nk_gemm_group* groups, int32_t precis
 
 nk_status nk_conv2d_grouped_tune(int32_t G, const nk_conv_group* groups, int32_t reps, nk_schedule* best,
                                  nk_tune_report* rep, void* stream) {
+  nk::NvtxRange nvtx_range_("nk_conv2d_grouped_tune");
   if (!best) return fail(NK_ERR_INVALID_ARG, "best is NULL");
   if (G < 1 || !groups) return fail(NK_ERR_INVALID_ARG, "need at least one group");
   nk_status st = require_device();
@@ -698,6 +700,7 @@ nk_status nk_conv2d_grouped_tune(int32_t G, const nk_conv_group* groups, int32_t
 
 nk_status nk_time_schedule(const nk_problem* p, const nk_schedule* s, int32_t reps, float* median_ms,
                            void* stream) {
+  nk::NvtxRange nvtx_range_("nk_time_schedule");
   nk_status st = check_problem(p);
   if (st != NK_OK) return st;
   if ((st = require_device()) != NK_OK) return st;
@@ -717,6 +720,7 @@ nk_status nk_tune_release(void) {
 
 nk_status nk_tune(const nk_problem* p, int32_t mode, int32_t topk, const float* mlp_params, int32_t reps,
                   nk_schedule* best, nk_tune_report* rep, void* stream) {
+  nk::NvtxRange nvtx_range_("nk_tune");
   nk_status st = check_problem(p);
   if (st != NK_OK) return st;
   if ((st = require_device()) != NK_OK) return st;
@@ -731,6 +735,7 @@ nk_status nk_tune(const nk_problem* p, int32_t mode, int32_t topk, const float* 
   if (cand.empty()) return fail(NK_ERR_NO_SCHEDULE, "no legal schedule");
   if (mode == NK_TUNE_EVOLUTION) {
     std::lock_guard<std::mutex> lk(g_mu);
+    nk::NvtxRange phase("nk_tune: evolution search");
     int bi = 0;
     float bms = 0.f;
     st = evolve(p, cand, topk, reps, cs, &bi, &bms);
@@ -750,6 +755,7 @@ nk_status nk_tune(const nk_problem* p, int32_t mode, int32_t topk, const float* 
   std::vector<int> order(cand.size());
   for (size_t i = 0; i < cand.size(); ++i) order[i] = (int)i;
   if (mode == NK_TUNE_MODEL_TOPK) {
+    nk::NvtxRange phase("nk_tune: cost-model ranking");
     const int sms = sm_count();
     std::vector<float> feat(cand.size() * NK_TUNE_FEATURES);
     for (size_t i = 0; i < cand.size(); ++i) features(p, cand[i], sms, feat.data() + i * NK_TUNE_FEATURES);
@@ -772,14 +778,18 @@ nk_status nk_tune(const nk_problem* p, int32_t mode, int32_t topk, const float* 
   std::lock_guard<std::mutex> lk(g_mu);
   float best_ms = INFINITY;
   int best_i = -1;
-  for (int i : order) {
-    float ms = 0.f;
-    st = time_one(p, cand[i], reps, &ms, cs);
-    if (st != NK_OK) return st;
-    if (ms < best_ms) { best_ms = ms; best_i = i; }
+  {
+    nk::NvtxRange phase(mode == NK_TUNE_MODEL_TOPK ? "nk_tune: timing the top-k" : "nk_tune: timing every candidate");
+    for (int i : order) {
+      float ms = 0.f;
+      st = time_one(p, cand[i], reps, &ms, cs);
+      if (st != NK_OK) return st;
+      if (ms < best_ms) { best_ms = ms; best_i = i; }
+    }
   }
   *best = cand[best_i];
   if (rep) {
+    nk::NvtxRange phase("nk_tune: timing the built-in default");
     rep->candidates = (int32_t)cand.size();
     rep->timed = (int32_t)order.size();
     rep->best_ms = best_ms;

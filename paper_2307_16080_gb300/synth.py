@@ -64,13 +64,15 @@ def uniform(seed: int, stream: int, shape, lo: float = -1.0, hi: float = 1.0) ->
     return (lo + (hi - lo) * u).astype(np.float32).reshape(shape)
 
 
-def normal(seed: int, stream: int, shape, sigma: float = 1.0) -> np.ndarray:
-    """Box-Muller normals: z = sqrt(-2 ln(1-u1)) cos(2 pi u2), in FP64 then FP32."""
+def normal(seed: int, stream: int, shape, sigma: float = 1.0, offset: int = 0) -> np.ndarray:
+    """Box-Muller normals: z = sqrt(-2 ln(1-u1)) cos(2 pi u2), in FP64 then FP32.
+    `offset` skips that many normals of the stream (element `offset` of a
+    larger tensor drawn from the same stream comes first)."""
     n = int(np.prod(shape))
     out = np.empty(n, dtype=np.float32)
     for a in range(0, n, _CHUNK):
         b = min(n, a + _CHUNK)
-        u = uniform01(seed, stream, 2 * (b - a), 2 * a)
+        u = uniform01(seed, stream, 2 * (b - a), 2 * (offset + a))
         r = np.sqrt(-2.0 * np.log1p(-u[0::2]))
         out[a:b] = (sigma * r * np.cos(2.0 * math.pi * u[1::2])).astype(np.float32)
     return out.reshape(shape)
@@ -81,13 +83,14 @@ def half_normal(seed: int, stream: int, shape, sigma: float = 1.0) -> np.ndarray
 
 
 def outlier_normal(seed: int, stream: int, shape, p: float = 0.01,
-                   factor: float = 100.0) -> np.ndarray:
-    """N(0,1) with each entry independently scaled by ``factor`` with prob. ``p``."""
-    z = normal(seed, stream, shape).reshape(-1)
+                   factor: float = 100.0, offset: int = 0) -> np.ndarray:
+    """N(0,1) with each entry independently scaled by ``factor`` with prob. ``p``
+    (`offset` as for `normal`)."""
+    z = normal(seed, stream, shape, offset=offset).reshape(-1)
     n = z.size
     for a in range(0, n, _CHUNK):
         b = min(n, a + _CHUNK)
-        hit = uniform01(seed, stream + 1_000_003, b - a, a) < p
+        hit = uniform01(seed, stream + 1_000_003, b - a, offset + a) < p
         z[a:b][hit] *= np.float32(factor)
     return z.reshape(shape)
 
@@ -123,9 +126,12 @@ def matmul_uniform(M: int, N: int, K: int, seed: int = SEED_MATMUL_256):
     return A, B
 
 
-def matmul_outlier(M: int, N: int, K: int, seed: int = SEED_SWEEP):
-    """A, B ~ N(0,1) with 1% of entries scaled by 100 (precision sweep recipe)."""
-    A = outlier_normal(seed, 10 + 2 * (M % 997), (M, K))
+def matmul_outlier(M: int, N: int, K: int, seed: int = SEED_SWEEP, rows=None):
+    """A, B ~ N(0,1) with 1% of entries scaled by 100 (precision sweep recipe).
+    rows = (r0, r1) draws only rows r0..r1-1 of the M-row A (a row block of
+    the same matrix, for one rank of a row-sharded matmul)."""
+    r0, r1 = (0, M) if rows is None else rows
+    A = outlier_normal(seed, 10 + 2 * (M % 997), (r1 - r0, K), offset=r0 * K)
     B = outlier_normal(seed, 11 + 2 * (N % 997), (K, N))
     return A, B
 
