@@ -183,7 +183,11 @@ nk_status nk_elementwise(const nk_tensor* X, nk_tensor* Y, const nk_ew_program* 
  * stage, stages = shared-memory ring depth, split_k =
  * number of K slices reduced by a separate fixed-order pass.  Any field 0
  * means "choose".  For the shared-window convolution (tile_k = 64*KH*KW,
- * see nk_conv2d_nhwc_hwcf) stages counts window slots and split_k is 1.    */
+ * or 64*KH with the KW taps of a kernel row side by side along N; see
+ * nk_conv2d_nhwc_hwcf) stages counts window slots and split_k is 1; with
+ * stacked kernel rows tile_m 128 keeps one accumulator buffer (two CTAs per
+ * SM, 1-4 slots) and tile_m 256 two (one CTA per SM, 2-8 slots), so the
+ * epilogue of a tile overlaps the MMAs of the next.                       */
 typedef struct {
   int32_t tile_m, tile_n, tile_k, cluster, stages, split_k;
 } nk_schedule;
@@ -255,8 +259,12 @@ nk_status nk_grouped_workspace_size(int32_t G, const nk_gemm_group* groups,
 /* ------------------------------------------------------------------ conv */
 
 /* linalg.conv_2d_nhwc_hwcf with zero padding and the epilogue.
- * I: [N,H,W,C], W: [KH,KW,C,F], O: [N,OH,OW,F] FP32; I and O with unit
- * stride in the last dimension.  OH = (H + pt + pb - dh*(KH-1) - 1)/sh + 1
+ * I: [N,H,W,C], W: [KH,KW,C,F], O: [N,OH,OW,F]; I and O with unit
+ * stride in the last dimension.  O is FP32, or -- at NK_PREC_BF16 and
+ * NK_PREC_FP8 -- BF16: the epilogue (bias, ReLU, accumulate, program)
+ * computes in FP32 and each result is rounded to BF16 (RNE) as it is
+ * stored, so the output can feed the next layer as its BF16 input (with
+ * accumulate = 1 the BF16 O is read as C_in).  OH = (H + pt + pb - dh*(KH-1) - 1)/sh + 1
  * (same for OW).  stride = {sh, sw}, dilation = {dh, dw},
  * pad = {top, bottom, left, right}.
  * Precisions: NK_PREC_F32 (CUDA cores), NK_PREC_BF16, NK_PREC_FP8 (E4M3

@@ -10,6 +10,7 @@
 // base also locates its operands.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -74,6 +75,52 @@ static __device__ __noinline__ float ew_run(const EwProg& e, float x, int64_t of
 // given).
 static __device__ __noinline__ void ew_apply(const EwProg& e, float* buf, int n, int64_t off0) {
   for (int j = 0; j < n; ++j) buf[j] = ew_run(e, buf[j], off0 + j);
+}
+
+// 32-byte stores (one whole L2 sector per thread; the address must be
+// 32-byte aligned).  The epilogues write one output row per lane, so a warp
+// store touches 32 rows: with 16-byte stores each row's sector arrives in
+// two halves, with these in one piece, and the L2 sees half the requests.
+__device__ __forceinline__ void st_v8_f32(float* p, float a0, float a1, float a2, float a3, float a4, float a5,
+                                          float a6, float a7) {
+  asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "f"(a0), "f"(a1), "f"(a2),
+               "f"(a3), "f"(a4), "f"(a5), "f"(a6), "f"(a7)
+               : "memory");
+}
+__device__ __forceinline__ void st_v8_b32(void* p, const uint32_t* w) {
+  asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "r"(w[0]), "r"(w[1]), "r"(w[2]),
+               "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7])
+               : "memory");
+}
+// 32 consecutive FP32 values to a 32-byte aligned row segment.
+__device__ __forceinline__ void store32_f32_v8(float* dst, const float* v) {
+#pragma unroll
+  for (int j = 0; j < 32; j += 8) st_v8_f32(dst + j, v[j], v[j + 1], v[j + 2], v[j + 3], v[j + 4], v[j + 5], v[j + 6], v[j + 7]);
+}
+
+// BF16 outputs (a convolution whose result feeds the next layer directly):
+// the epilogue computes in FP32 as for an FP32 output, then rounds each
+// value to BF16 with round-to-nearest-even (CUDA's conversion intrinsic).
+// 32 consecutive values to a 16-byte aligned row segment: four 16-byte
+// stores of eight BF16 each.
+__device__ __forceinline__ void store32_bf16(__nv_bfloat16* dst, const float* v) {
+#pragma unroll
+  for (int j = 0; j < 32; j += 8) {
+    __nv_bfloat162 h[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) h[e] = __floats2bfloat162_rn(v[j + 2 * e], v[j + 2 * e + 1]);
+    *reinterpret_cast<uint4*>(dst + j) = *reinterpret_cast<const uint4*>(h);
+  }
+}
+// The same to a 32-byte aligned segment in two 32-byte stores.
+__device__ __forceinline__ void store32_bf16_v8(__nv_bfloat16* dst, const float* v) {
+#pragma unroll
+  for (int j = 0; j < 32; j += 16) {
+    __nv_bfloat162 h[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) h[e] = __floats2bfloat162_rn(v[j + 2 * e], v[j + 2 * e + 1]);
+    st_v8_b32(dst + j, reinterpret_cast<const uint32_t*>(h));
+  }
 }
 #endif
 

@@ -362,13 +362,16 @@ __global__ void splitk_reduce_kernel(const __grid_constant__ SplitReduce r, int 
       if (off < S) v += __shfl_xor_sync(0xffffffffu, v, off);
     if (s == 0 && idx < total) {
       const int m = (int)(idx / r.N), n = (int)(idx % r.N);
-      float* c = r.C + (int64_t)m * r.scm + (int64_t)n * r.scn;
+      const int64_t off = (int64_t)m * r.scm + (int64_t)n * r.scn;
+      float* c = r.C + off;
+      __nv_bfloat16* ch = reinterpret_cast<__nv_bfloat16*>(r.C) + off;
       float o = alpha * v;
-      if (r.beta != 0.f) o = fmaf(r.beta, *c, o);
+      if (r.beta != 0.f) o = fmaf(r.beta, r.out_bf16 ? __bfloat162float(*ch) : *c, o);
       if (r.bias) o += r.bias[r.bias_on_m ? m : n];
       if (r.relu) o = (o > 0.f || o != o) ? o : 0.f;
-      if (EW && r.ew.n) o = ew_run(r.ew, o, (int64_t)m * r.scm + (int64_t)n * r.scn);
-      *c = o;
+      if (EW && r.ew.n) o = ew_run(r.ew, o, off);
+      if (r.out_bf16) *ch = __float2bfloat16_rn(o);
+      else *c = o;
     }
   }
 }

@@ -97,6 +97,7 @@ struct TcParams {
   CUtensorMap tmC;
   int c_tma;
   EwProg ew;                    // fused elementwise program (offsets from C), single launches
+  int out_bf16;                 // single convolutions: C holds BF16 (RNE of the FP32 result)
 };
 
 // Epilogue staging: one 32 x 32 FP32 box (4 KB, 128B-swizzled) per epilogue warp.
@@ -548,6 +549,31 @@ __global__ void __launch_bounds__(WIDE ? 320 : 192, 1) tc_gemm_kernel(const __gr
               if (col0 + j < p.N) dst[j] = v[j];
           }
           continue;
+        }
+        if constexpr (CONV && !GROUPED) {
+          if (p.out_bf16) {
+            // BF16 output: the FP32 epilogue, then one RNE rounding per value
+            __nv_bfloat16* dh = reinterpret_cast<__nv_bfloat16*>(t.C) + (int64_t)row * t.ldc + col0;
+            const int ncol = t.N - col0 < 32 ? t.N - col0 : 32;
+            float buf[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              float x = alpha * v[j];
+              if (j < ncol) {
+                if (t.beta != 0.f) x = fmaf(t.beta, __bfloat162float(dh[j]), x);
+                if (t.bias) x += __ldg(t.bias + col0 + j);
+                if (t.relu) x = (x > 0.f || x != x) ? x : 0.f;
+              }
+              buf[j] = x;
+            }
+            if (p.ew.n) ew_apply(p.ew, buf, ncol, (int64_t)row * t.ldc + col0);
+            if (p.c_vec && ncol == 32) {
+              store32_bf16(dh, buf);
+            } else {
+              for (int j = 0; j < ncol; ++j) dh[j] = __float2bfloat16_rn(buf[j]);
+            }
+            continue;
+          }
         }
         float* dst = t.C + (int64_t)row * t.ldc + col0;
         const float bm = (t.bias && p.bias_on_m) ? __ldg(t.bias + row) : 0.f;
@@ -1069,7 +1095,9 @@ nk_status tc_conv(const TcConv& c, const nk_schedule& s, void* ws, size_t ws_byt
   p.scale_b = c.scale_w;
   p.ew = c.ew;
   p.budget = wait_budget();
-  p.c_vec = ((reinterpret_cast<uintptr_t>(c.O) & 15) == 0 && c.F % 4 == 0 &&
+  p.out_bf16 = c.out_bf16;
+  // vector stores: 16-byte aligned rows (FP32: F % 4, BF16: F % 8) and partials
+  p.c_vec = ((reinterpret_cast<uintptr_t>(c.O) & 15) == 0 && c.F % (c.out_bf16 ? 8 : 4) == 0 &&
              (splits == 1 || (reinterpret_cast<uintptr_t>(ws) & 15) == 0)) ? 1 : 0;
   const int smem = smem_of(kind, s);
   if (smem > kMaxSmem) return fail(NK_ERR_NO_SCHEDULE, "conv schedule needs %d bytes of shared memory", smem);
@@ -1101,6 +1129,7 @@ nk_status tc_conv(const TcConv& c, const nk_schedule& s, void* ws, size_t ws_byt
   r.scale_a = c.scale_i;
   r.scale_b = c.scale_w;
   r.ew = c.ew;
+  r.out_bf16 = c.out_bf16;
   return splitk_reduce(r, st);
 }
 

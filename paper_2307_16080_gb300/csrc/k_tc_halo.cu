@@ -72,7 +72,8 @@ uint32_t halo_read_and_clear_errors() {
 
 namespace {
 
-constexpr int kThreads = 192;
+constexpr int kThreads = 192;       // producer, MMA issuer, 4 epilogue warps
+constexpr int kThreadsDB = 320;     // double-buffered stacked kernel: 8 epilogue warps
 constexpr int kRow = 128;            // bytes per pixel row (64 BF16 channels) / per filter row
 constexpr int kMaxSmem = 232448;     // 227 KB opt-in limit
 constexpr int kBarBytes = 1024;      // barriers (at most 127), TMEM slot and abort flag
@@ -101,9 +102,11 @@ struct HaloParams {
   const float* bias;
   int relu;
   float beta;
-  int c_vec;
+  int c_vec;             // 16-byte aligned output rows
+  int c_vec32;           // 32-byte aligned output rows (one-sector stores)
   int64_t budget;
   EwProg ew;             // fused elementwise program (offsets from O)
+  int out_bf16;          // O holds BF16 (RNE of the FP32 epilogue result)
 };
 
 // First GEMM row a tap reads: tap (kh, kw) sees the window kh*dh rows down
@@ -118,11 +121,20 @@ __device__ __forceinline__ int tap_offset(const HaloTile& t, int tap) {
 // does the work of KW narrow ones.  Accumulator column kw * 64 + f of row m
 // holds the tap-kw partial sum of output row m - kw * dw; the epilogue adds
 // them with warp shuffles.  The window row pitch P divides 32, so a shifted
-// row never leaves its warp.  One accumulator buffer (TMEM for two CTAs).
-template <int MCH, bool STK>
-__global__ void __launch_bounds__(kThreads, 1) halo_conv_kernel(const __grid_constant__ HaloParams p) {
+// row never leaves its warp.  One accumulator buffer (TMEM for two CTAs), or
+// with DB two buffers in all 512 columns (one CTA per SM): the epilogue of a
+// tile then overlaps the next tile's MMAs, and the CTA holds the filters
+// once beside a deeper ring of window slots.  With one CTA per SM the
+// epilogue is the longer half of a tile (a single warp per SM sub-partition
+// runs its dependent loads, shuffles and stores with nothing to hide their
+// latency), so DB gives it twice the warps: two per TMEM lane quarter, each
+// taking every other 32-column segment.
+template <int MCH, bool STK, bool DB = false>
+__global__ void __launch_bounds__(DB ? kThreadsDB : kThreads, 1) halo_conv_kernel(const __grid_constant__ HaloParams p) {
   static_assert(!STK || MCH == 1, "stacked kernel rows use one chain");
-  constexpr int NACC = STK ? 1 : 2;   // accumulator buffers
+  static_assert(!DB || STK, "the double-buffered variant is a stacked-row kernel");
+  constexpr int NACC = (STK && !DB) ? 1 : 2;   // accumulator buffers
+  constexpr int EPW = DB ? 2 : 1;              // epilogue warps per TMEM lane quarter
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = ptx::smem_u32(smem_raw);
   const uint32_t base = (raw + 1023) & ~1023u;
@@ -158,8 +170,9 @@ __global__ void __launch_bounds__(kThreads, 1) halo_conv_kernel(const __grid_con
   const int warp = threadIdx.x / 32;
   const int lane = threadIdx.x % 32;
   const uint32_t acc_cols = (uint32_t)(MCH * p.bn * nst);
-  // 128, 256 or 512 columns: a power of two >= 32 (stacked: 64 * KW rounded up)
-  const uint32_t tmem_cols = STK ? (acc_cols <= 128u ? 128u : 256u) : 2u * acc_cols;
+  // 128, 256 or 512 columns: a power of two >= 32 (stacked: 64 * KW rounded
+  // up, or all 512 for two buffers)
+  const uint32_t tmem_cols = STK ? (DB ? 512u : (acc_cols <= 128u ? 128u : 256u)) : 2u * acc_cols;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < WS; ++s) {
@@ -172,7 +185,7 @@ __global__ void __launch_bounds__(kThreads, 1) halo_conv_kernel(const __grid_con
     }
     for (int b = 0; b < 2; ++b) {
       ptx::mbar_init(tfull(b), 1);
-      ptx::mbar_init(tempty(b), 4);   // one arrival per epilogue warp
+      ptx::mbar_init(tempty(b), 4 * EPW);   // one arrival per epilogue warp
     }
     ptx::mbar_init(drain_bar, 1);
     *abort_flag = 0;
@@ -293,6 +306,7 @@ __global__ void __launch_bounds__(kThreads, 1) halo_conv_kernel(const __grid_con
     // ---------------------------------------------------------- epilogue
     const int q = warp & 3;   // TMEM lane quarter this warp may read
     const int img_rows = t.WR * t.P;
+    const int cfirst = ((warp - 2) / 4) * 32;     // this warp's first 32-column segment
     int tc = 0;
     for (int u = blockIdx.x; u < p.units; u += gridDim.x, ++tc) {
       const int tn = u / p.tiles_m, tm = u - tn * p.tiles_m;
@@ -309,9 +323,29 @@ __global__ void __launch_bounds__(kThreads, 1) halo_conv_kernel(const __grid_con
         const bool row_ok = b < t.NB && y < t.R && x < t.Q && n < t.N && oh < t.OH && ow < t.OW;
         const int64_t orow_off = ((int64_t)(n * t.OH + oh) * t.OW + ow) * p.F;
         float* orow = p.O + orow_off;
-        for (int c0 = 0; c0 < p.bn; c0 += 32) {
+        for (int c0 = cfirst; c0 < p.bn; c0 += 32 * EPW) {
           float v[32];
           const uint32_t lane_base = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)acc * acc_cols;
+          if constexpr (DB) {
+            // every tap's columns in flight before one wait, then the shifts
+            // (the one-buffer variant keeps one tap in flight: its register
+            // budget must leave room for two CTAs per SM)
+            uint32_t r0[32], rt[3][32];
+            ptx::tmem_ld32_async(lane_base + (uint32_t)c0, r0);
+#pragma unroll
+            for (int j = 1; j < 4; ++j)
+              if (j < nst) ptx::tmem_ld32_async(lane_base + (uint32_t)(j * p.bn + c0), rt[j - 1]);
+            ptx::tmem_wait_ld();
+#pragma unroll
+            for (int e = 0; e < 32; ++e) v[e] = __uint_as_float(r0[e]);
+#pragma unroll
+            for (int j = 1; j < 4; ++j) {
+              if (j >= nst) break;
+              const int sh = j * t.dw;
+#pragma unroll
+              for (int e = 0; e < 32; ++e) v[e] += __shfl_down_sync(0xffffffffu, __uint_as_float(rt[j - 1][e]), sh);
+            }
+          } else {
           ptx::tmem_ld32(lane_base + (uint32_t)(ch * p.bn + c0), v);
           if (STK) {
             // output row m = tap-0 row m + tap-kw row m + kw * dw, same warp
@@ -323,8 +357,51 @@ __global__ void __launch_bounds__(kThreads, 1) halo_conv_kernel(const __grid_con
               for (int e = 0; e < 32; ++e) v[e] += __shfl_down_sync(0xffffffffu, w[e], sh);
             }
           }
+          }
           const int col0 = tn * p.bn + c0;
           if (!row_ok || col0 >= p.F) continue;
+          if (p.out_bf16) {
+            // BF16 output: the FP32 epilogue, then one RNE rounding per value
+            __nv_bfloat16* dh = reinterpret_cast<__nv_bfloat16*>(p.O) + orow_off + col0;
+            const int ncol = p.F - col0 < 32 ? p.F - col0 : 32;
+            if (p.ew.n) {
+              // the program runs out of line on a local buffer (see below)
+              float buf[32];
+#pragma unroll
+              for (int j = 0; j < 32; ++j) {
+                float xv = v[j];
+                if (j < ncol) {
+                  if (p.beta != 0.f) xv = fmaf(p.beta, __bfloat162float(dh[j]), xv);
+                  if (p.bias) xv += __ldg(p.bias + col0 + j);
+                  if (p.relu) xv = (xv > 0.f || xv != xv) ? xv : 0.f;
+                }
+                buf[j] = xv;
+              }
+              ew_apply(p.ew, buf, ncol, orow_off + col0);
+              for (int j = 0; j < ncol; ++j) dh[j] = __float2bfloat16_rn(buf[j]);
+            } else {
+#pragma unroll
+              for (int j = 0; j < 32; ++j) {
+                float xv = v[j];
+                if (col0 + j < p.F) {
+                  if (p.beta != 0.f) xv = fmaf(p.beta, __bfloat162float(dh[j]), xv);
+                  if (p.bias) xv += __ldg(p.bias + col0 + j);
+                  if (p.relu) xv = (xv > 0.f || xv != xv) ? xv : 0.f;
+                }
+                v[j] = xv;
+              }
+              if (p.c_vec32 && ncol == 32) {
+                store32_bf16_v8(dh, v);
+              } else if (p.c_vec && ncol == 32) {
+                store32_bf16(dh, v);
+              } else {
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                  if (j < ncol) dh[j] = __float2bfloat16_rn(v[j]);
+              }
+            }
+            continue;
+          }
           float* dst = orow + col0;
           if (p.ew.n) {
             // A program runs out of line: the segment goes through a local
@@ -344,6 +421,15 @@ __global__ void __launch_bounds__(kThreads, 1) halo_conv_kernel(const __grid_con
             }
             ew_apply(p.ew, buf, ncol, orow_off + col0);
             for (int j = 0; j < ncol; ++j) dst[j] = buf[j];
+          } else if (p.c_vec32 && p.beta == 0.f && col0 + 32 <= p.F) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              float xv = v[j];
+              if (p.bias) xv += __ldg(p.bias + col0 + j);
+              if (p.relu) xv = (xv > 0.f || xv != xv) ? xv : 0.f;
+              v[j] = xv;
+            }
+            store32_f32_v8(dst, v);
           } else if (p.c_vec && col0 + 32 <= p.F) {
 #pragma unroll
             for (int j = 0; j < 32; j += 4) {
@@ -402,7 +488,6 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 int taps_of(const ConvGeom& g) { return g.kh * g.kw; }
-int chains_of(const nk_schedule& s) { return s.tile_m / 128; }
 
 // Kernel-row stacking: tile_k = 64 * KH (one K block per kernel row and
 // 64-channel block) selects the window kernel with the KW taps of a kernel
@@ -413,6 +498,15 @@ bool stacked_schedule(const ConvGeom& g, const nk_schedule& s) {
   return g.kh >= 2 && g.kw >= 2 && g.kw <= 4 && s.tile_k == 64 * g.kh;
 }
 
+// Stacked kernel rows with tile_m 256: one 128-row tile at a time, but two
+// accumulator buffers (all 512 TMEM columns, one CTA per SM) so the
+// epilogue of a tile overlaps the MMAs of the next.
+bool stacked_db(const ConvGeom& g, const nk_schedule& s) { return stacked_schedule(g, s) && s.tile_m == 256; }
+
+// Accumulator chains of a window schedule: tile_m / 128 stacked 128-row
+// tiles for the plain window; stacked kernel rows always use one.
+int chains_of(const ConvGeom& g, const nk_schedule& s) { return stacked_schedule(g, s) ? 1 : s.tile_m / 128; }
+
 // Largest row offset the A operand reads, in GEMM rows (stacked: the kw
 // shifts move to the epilogue).
 int max_offset(const ConvGeom& g, int P, bool stk) {
@@ -420,9 +514,10 @@ int max_offset(const ConvGeom& g, int P, bool stk) {
 }
 
 // TMEM columns one CTA allocates: two accumulator buffers of mch * bn, or
-// (stacked) one buffer of 64 * KW rounded up to a power of two.
-int halo_tmem_cols(int mch, int bn, int stk) {
-  return stk > 1 ? (bn * stk <= 128 ? 128 : 256) : 2 * mch * bn;
+// (stacked) one buffer of 64 * KW rounded up to a power of two, or (stacked,
+// double-buffered) all 512.
+int halo_tmem_cols(int mch, int bn, int stk, bool db) {
+  return stk > 1 ? (db ? 512 : (bn * stk <= 128 ? 128 : 256)) : 2 * mch * bn;
 }
 
 // Window tile for `mch` chains: the fewest tiles whose valid output rows
@@ -529,10 +624,10 @@ int halo_ctas(int smem, int tmem_cols) {
 // the two, the layout that lets more CTAs (independent MMA chains) share an
 // SM wins; on a tie, resident weights.
 bool halo_layout(const ConvGeom& g, int F, const nk_schedule& s, HaloLayout* L) {
-  const int mch = chains_of(s);
+  const int mch = chains_of(g, s);
   const bool stk = stacked_schedule(g, s);
   if (!cached_halo_tile(g, mch, stk, &L->t)) return false;
-  const int tcols = halo_tmem_cols(mch, s.tile_n, L->t.stk);
+  const int tcols = halo_tmem_cols(mch, s.tile_n, L->t.stk, stacked_db(g, s));
   L->slot_bytes = (uint32_t)((L->t.slot_rows * kRow + 1023) / 1024 * 1024);
   L->wslots = s.stages;
   const int fixed = 1024 + s.stages * (int)L->slot_bytes + kBarBytes;
@@ -557,9 +652,9 @@ bool halo_layout(const ConvGeom& g, int F, const nk_schedule& s, HaloLayout* L) 
   return L->smem <= kMaxSmem;
 }
 
-template <int MCH, bool STK = false>
+template <int MCH, bool STK = false, bool DB = false>
 nk_status launch(const HaloParams& p, int grid, int smem, cudaStream_t st) {
-  auto kern = halo_conv_kernel<MCH, STK>;
+  auto kern = halo_conv_kernel<MCH, STK, DB>;
   static int set_bytes[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
@@ -568,7 +663,7 @@ nk_status launch(const HaloParams& p, int grid, int smem, cudaStream_t st) {
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(halo_conv_kernel)");
     if (dev >= 0 && dev < 64) set_bytes[dev] = smem;
   }
-  (void)nk::launch_k(kern, dim3(grid), dim3(kThreads), smem, st, 1, p);
+  (void)nk::launch_k(kern, dim3(grid), dim3(DB ? kThreadsDB : kThreads), smem, st, 1, p);
   return check_launch("halo_conv_kernel");
 }
 
@@ -583,10 +678,12 @@ bool halo_schedule_valid(const ConvGeom& g, int F, const nk_schedule& s) {
   if (g.sh != 1 || g.sw != 1) return false;
   if (s.tile_m != 128 && s.tile_m != 256 && s.tile_m != 512) return false;
   if (s.tile_n != 64 && s.tile_n != 128 && s.tile_n != 256) return false;
-  if (chains_of(s) * s.tile_n > 256) return false;   // two accumulator buffers in 512 TMEM columns
-  if (stacked_schedule(g, s) && (s.tile_m != 128 || s.tile_n != 64)) return false;   // N = 64 * KW
+  if (chains_of(g, s) * s.tile_n > 256) return false;   // two accumulator buffers in 512 TMEM columns
+  // stacked: N = 64 * KW; tile_m 128 (one buffer) or 256 (two buffers)
+  if (stacked_schedule(g, s) && (s.tile_m > 256 || s.tile_n != 64)) return false;
   if (s.cluster != 1 || s.split_k != 1) return false;
-  if (s.stages < 1 || s.stages > 4) return false;
+  // window slots: up to 4, up to 8 beside the two buffers of one CTA per SM
+  if (s.stages < 1 || s.stages > (stacked_db(g, s) ? 8 : 4)) return false;
   HaloLayout L;
   return halo_layout(g, F, s, &L);
 }
@@ -597,7 +694,7 @@ bool halo_tile_info(const ConvGeom& g, int F, const nk_schedule& s, int32_t out[
   if (!halo_schedule_valid(g, F, s) || !halo_layout(g, F, s, &L)) return false;
   const HaloTile& t = L.t;
   const int32_t v[10] = {t.P, t.Q, t.R, t.NB, t.WR, t.rows, t.slot_rows, t.stk,
-                         t.tiles_w * t.tiles_h * t.tiles_b, chains_of(s)};
+                         t.tiles_w * t.tiles_h * t.tiles_b, chains_of(g, s)};
   for (int i = 0; i < 10; ++i) out[i] = v[i];
   return true;
 }
@@ -681,12 +778,16 @@ nk_status tc_halo_conv(const TcConv& c, const nk_schedule& s, cudaStream_t st) {
   p.relu = c.relu;
   p.beta = c.beta;
   p.ew = c.ew;
-  p.c_vec = ((reinterpret_cast<uintptr_t>(c.O) & 15) == 0 && c.F % 4 == 0) ? 1 : 0;
+  p.out_bf16 = c.out_bf16;
+  p.c_vec = ((reinterpret_cast<uintptr_t>(c.O) & 15) == 0 && c.F % (c.out_bf16 ? 8 : 4) == 0) ? 1 : 0;
+  p.c_vec32 = ((reinterpret_cast<uintptr_t>(c.O) & 31) == 0 && c.F % (c.out_bf16 ? 16 : 8) == 0) ? 1 : 0;
   p.budget = wait_budget();
   if (p.units == 0) return NK_OK;
-  const int grid = std::min(p.units, sms * halo_ctas(L.smem, halo_tmem_cols(chains_of(s), s.tile_n, t.stk)));
-  if (t.stk > 1) return launch<1, true>(p, grid, L.smem, st);
-  switch (chains_of(s)) {
+  const bool db = stacked_db(g, s);
+  const int grid =
+      std::min(p.units, sms * halo_ctas(L.smem, halo_tmem_cols(chains_of(g, s), s.tile_n, t.stk, db)));
+  if (t.stk > 1) return db ? launch<1, true, true>(p, grid, L.smem, st) : launch<1, true>(p, grid, L.smem, st);
+  switch (chains_of(g, s)) {
     case 1: return launch<1>(p, grid, L.smem, st);
     case 2: return launch<2>(p, grid, L.smem, st);
     default: return launch<4>(p, grid, L.smem, st);

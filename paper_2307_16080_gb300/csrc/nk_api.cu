@@ -482,7 +482,7 @@ static nk_status plan_conv(const nk_tensor* I, const nk_tensor* W, const nk_tens
   if (I->rank != 4 || W->rank != 4 || O->rank != 4) return fail(NK_ERR_INVALID_ARG, "I, W, O must have rank 4");
   if (I->stride[3] != 1 || O->stride[3] != 1)
     return fail(NK_ERR_UNSUPPORTED, "the last dimension of I and O must have unit stride");
-  if (O->dtype != NK_F32) return fail(NK_ERR_UNSUPPORTED, "O must be FP32");
+  if (O->dtype != NK_F32 && O->dtype != NK_BF16) return fail(NK_ERR_UNSUPPORTED, "O must be FP32 or BF16");
   if ((I->dtype != NK_F32 && I->dtype != NK_BF16) || (W->dtype != NK_F32 && W->dtype != NK_BF16))
     return fail(NK_ERR_INVALID_ARG, "I and W must be FP32 or BF16");
   for (int i = 0; i < 2; ++i)
@@ -686,6 +686,9 @@ nk_status nk_conv2d_nhwc_hwcf(const nk_tensor* I, const nk_tensor* W, nk_tensor*
       c.sW_f = W->stride[3];
     }
     c.O = static_cast<float*>(O->ptr);
+    c.out_bf16 = O->dtype == NK_BF16 ? 1 : 0;
+    if (c.out_bf16 && (reinterpret_cast<uintptr_t>(O->ptr) & 1))
+      return fail(NK_ERR_MISALIGNED, "a BF16 O must be 2-byte aligned");
     c.bias = E.bias;
     c.relu = E.relu;
     c.beta = E.accumulate ? 1.f : 0.f;
@@ -695,6 +698,7 @@ nk_status nk_conv2d_nhwc_hwcf(const nk_tensor* I, const nk_tensor* W, nk_tensor*
   if (precision != NK_PREC_F32 || I->dtype != NK_F32 || W->dtype != NK_F32)
     return fail(NK_ERR_UNSUPPORTED, "conv precision %d with I dtype %d / W dtype %d not available", precision,
                 I->dtype, W->dtype);
+  if (O->dtype != NK_F32) return fail(NK_ERR_UNSUPPORTED, "the FP32 convolution writes an FP32 O");
   SimtGemm p{};
   p.A = static_cast<const float*>(I->ptr);
   p.B = static_cast<const float*>(W->ptr);

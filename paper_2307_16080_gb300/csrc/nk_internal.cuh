@@ -156,6 +156,7 @@ struct SplitReduce {
   const float* scale_a;  // when set, alpha = 1/(*scale_a * *scale_b) (device scalars)
   const float* scale_b;
   EwProg ew;             // epilogue program (offsets from C)
+  int out_bf16;          // C holds BF16 (RNE of the FP32 result) instead of FP32
 };
 nk_status splitk_reduce(const SplitReduce& r, cudaStream_t st);
 
@@ -221,7 +222,8 @@ nk_status tc_gemm(const TcGemm& g, const nk_schedule& s, void* ws, size_t ws_byt
 // channel c at f*sW_f + t*ldw + c (K-major per filter tap; ldw, sW_f 16-byte
 // multiples); O: FP32 [N*OH*OW, F] row-major.  E4M3: scale_i, scale_w are
 // the device scalars s_i, s_w the operands were quantised with (the epilogue
-// multiplies by 1/(s_i*s_w)); null for BF16.
+// multiplies by 1/(s_i*s_w)); null for BF16.  out_bf16: O holds BF16, the
+// epilogue's FP32 result rounded to nearest even (same [N*OH*OW, F] layout).
 struct TcConv {
   int kind;
   const void* I;
@@ -238,6 +240,7 @@ struct TcConv {
   const float* scale_i;
   const float* scale_w;
   EwProg ew;              // epilogue program (offsets from O)
+  int out_bf16;
 };
 // tc_conv dispatches a window schedule (see below) to tc_halo_conv.
 nk_status tc_conv(const TcConv& c, const nk_schedule& s, void* ws, size_t ws_bytes, cudaStream_t st);

@@ -135,9 +135,14 @@ std::vector<nk_schedule> enumerate(const nk_problem* p) {
           nk_schedule s{tm, tn, 64 * p->kh * p->kw, 1, st, 1};
           if (halo_schedule_valid(g, p->f, s)) out.push_back(s);
         }
-    // kernel rows stacked along N (tile_k = 64 * KH)
+    // kernel rows stacked along N (tile_k = 64 * KH): one accumulator buffer
+    // (tile_m 128, two CTAs per SM) or two (tile_m 256, one CTA per SM)
     for (int st = 1; st <= 4; ++st) {
       nk_schedule s{128, 64, 64 * p->kh, 1, st, 1};
+      if (p->kh >= 2 && p->kw >= 2 && halo_schedule_valid(g, p->f, s)) out.push_back(s);
+    }
+    for (int st = 2; st <= 8; ++st) {
+      nk_schedule s{256, 64, 64 * p->kh, 1, st, 1};
       if (p->kh >= 2 && p->kw >= 2 && halo_schedule_valid(g, p->f, s)) out.push_back(s);
     }
   }

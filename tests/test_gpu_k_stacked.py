@@ -66,6 +66,52 @@ def test_bf16_conv_stacked_bitwise(nk, case, stages):
     np.testing.assert_array_equal(got, O.conv2d_nhwc_hwcf(I, W, (1, 1), dl, pad))
 
 
+def _legal(nk, case, sched):
+    from paper_2307_16080_gb300 import nk_tune as nt
+    N, H, Wd, C, F, KH, KW, dl, pad = case
+    try:
+        nt.nk_conv_window_tile(N, H, Wd, C, F, KH, KW, dl, pad, sched)
+        return True
+    except nk.NkError:
+        return False
+
+
+@pytest.mark.parametrize("case", STACK_CASES)
+@pytest.mark.parametrize("stages", [2, 5, 8])
+def test_bf16_conv_stacked_double_buffered_bitwise(nk, case, stages):
+    """tile_m 256: the same stacked tiles with two accumulator buffers and a
+    deeper window ring (one CTA per SM); bit-exact on small integers."""
+    N, H, Wd, C, F, KH, KW, dl, pad = case
+    sched = (256, 64, 64 * KH, 1, stages, 1)
+    if not _legal(nk, case, sched):
+        pytest.skip("no room for this many window slots beside the filters")
+    I = synth.small_ints(91, H * 100 + C, (N, H, Wd, C))
+    W = synth.small_ints(91, F * 100 + KH * 10 + KW, (KH, KW, C, F))
+    got = _conv(nk, I, W, dl, pad, sched)
+    np.testing.assert_array_equal(got, O.conv2d_nhwc_hwcf(I, W, (1, 1), dl, pad))
+
+
+def test_double_buffered_schedules_exist_for_the_resnet_layers(nk):
+    """Every stride-1 3x3 layer of the stack has at least one legal
+    double-buffered stacked schedule with two or more window slots."""
+    for L in synth.resnet_stack(8):
+        if L["stride"] != 1 or L["KH"] != 3:
+            continue
+        case = (L["N"], L["H"], L["W"], L["C"], L["F"], 3, 3, (1, 1), (1, 1, 1, 1))
+        assert any(_legal(nk, case, (256, 64, 192, 1, st, 1)) for st in range(2, 9)), L
+
+
+@pytest.mark.parametrize("N", [1, 8, 32])
+@pytest.mark.parametrize("tile_m,stages", [(256, 4)])
+def test_bf16_conv_stacked_double_buffered_resnet_layer(nk, N, tile_m, stages):
+    I, W, bias = synth.conv_resnet_block(N=N)
+    i16, wp, b = dev(I).to(torch.bfloat16), nk.nk_conv2d_pack_weights(dev(W)), dev(bias)
+    got = _conv(nk, I, W, (1, 1), (1, 1, 1, 1), (tile_m, 64, 192, 1, stages, 1), i_dev=i16, w_dev=wp, bias=b,
+                relu=True)
+    plain = _conv(nk, I, W, (1, 1), (1, 1, 1, 1), (128, 64, 576, 1, 1, 1), i_dev=i16, w_dev=wp, bias=b, relu=True)
+    assert O.rel_frobenius(got, plain) <= 1e-5
+
+
 @pytest.mark.parametrize("N", [1, 8, 32])
 def test_bf16_conv_stacked_resnet_layer(nk, N):
     """The 56x56x64 3x3 layer of the ResNet-style stack, packed weights,
@@ -100,7 +146,8 @@ def test_bf16_conv_stacked_epilogue_and_program(nk):
 
 @pytest.mark.parametrize("sched,stride,k", [
     ((128, 128, 192, 1, 1, 1), 1, 3),    # stacked N is 64 filters per tile
-    ((256, 64, 192, 1, 1, 1), 1, 3),     # one chain only
+    ((512, 64, 192, 1, 2, 1), 1, 3),     # one chain, at most two accumulator buffers
+    ((256, 64, 192, 1, 9, 1), 1, 3),     # at most 8 window slots
     ((128, 64, 192, 1, 1, 1), 2, 3),     # stride 1 only
     ((128, 64, 320, 1, 1, 1), 1, 5),     # KW = 5 would need N = 320
 ])

@@ -14,7 +14,8 @@ def _stacked(p):
 def test_stacked_schedules_for_stride1_3x3():
     p = nt.conv_problem(8, 56, 56, 64, 64, 3, 3, 1, 1)
     got = _stacked(p)
-    assert got == [(128, 64, 192, 1, st, 1) for st in (1, 2, 3, 4)]
+    # one accumulator buffer, 1-4 window slots; two buffers, 2-8 slots
+    assert got == [(128, 64, 192, 1, st, 1) for st in (1, 2, 3, 4)] + [(256, 64, 192, 1, st, 1) for st in range(2, 9)]
     plain = nt.nk_workspace_size(p, (128, 64, 576, 1, 1, 1))
     assert all(nt.nk_workspace_size(p, s) == plain for s in got)
 
