@@ -371,12 +371,6 @@ def timings3(torch, fn, make_call, set_bytes, calls=10):
 
 
 # ------------------------------------------------------------------ reports
-def _has(mod, feature):
-    """True when the binding exposes `feature` and the library reports it."""
-    f = getattr(mod, feature, None)
-    return bool(f and f())
-
-
 def fp8_peak(torch, dev, n=8192, sustain_s=3.0):
     """torch._scaled_mm on E4M3 operands at n^3 (cuBLASLt): burst (best of 10)
     and sustained (back to back for a few seconds) dense FP8 TFLOP/s."""
@@ -539,49 +533,51 @@ def grouped_report(torch, nk, synth, dev):
             "launches": {"persistent": 1, "per_gemm": G}}
 
 
-def layer_roofline(N, H, W, C, F, KH, KW, stride, pad, ms, out_bytes=4):
-    """min(tensor peak, HBM x arithmetic intensity) for one BF16 conv layer:
-    2 B per input element (BF16 NHWC), `out_bytes` per output element (4:
-    FP32, 2: BF16), 2 B per packed weight; achieved = FLOP / measured time."""
+def layer_roofline(N, H, W, C, F, KH, KW, stride, pad, ms, out_bytes=4, in_bytes=2, peak=None):
+    """min(tensor peak, HBM x arithmetic intensity) for one conv layer:
+    `in_bytes` per input element and per packed weight (2: BF16, 1: E4M3),
+    `out_bytes` per output element (4: FP32, 2: BF16); achieved = FLOP /
+    measured time.  peak: the dtype's dense tensor peak (default: BF16)."""
     bf16_peak, hbm, src = peaks()
+    peak = peak or bf16_peak
     oh = (H + 2 * pad - KH) // stride + 1
     ow = (W + 2 * pad - KW) // stride + 1
     flop = 2.0 * N * oh * ow * F * KH * KW * C
-    nbytes = 2.0 * N * H * W * C + out_bytes * N * oh * ow * F + 2.0 * KH * KW * C * F
+    nbytes = float(in_bytes) * N * H * W * C + out_bytes * N * oh * ow * F + float(in_bytes) * KH * KW * C * F
     ai = flop / nbytes
-    roof = min(bf16_peak, hbm * 1e-3 * ai)    # TFLOP/s
+    roof = min(peak, hbm * 1e-3 * ai)    # TFLOP/s
     achieved = flop / (ms * 1e-3) / 1e12
-    return {"flop": flop, "bytes": nbytes, "ai_flop_per_byte": ai, "bound": "hbm" if roof < bf16_peak else "tensor",
+    return {"flop": flop, "bytes": nbytes, "ai_flop_per_byte": ai, "bound": "hbm" if roof < peak else "tensor",
             "roofline_tflops": roof, "achieved_tflops": achieved, "frac": achieved / roof,
-            "peak_source": f"{src} (MEASURED_PEAKS.json)"}
+            "peak_source": f"{src} (MEASURED_PEAKS.json; FP8: measured with torch._scaled_mm in this run)"}
 
 
-def conv_layer_report(torch, nk, synth, dev, N):
-    """One 3x3 layer N x 56 x 56 x 64 -> 64 (s1 p1, bias + ReLU): FP32 on the
-    CUDA cores; BF16 with per-call weight cast and with packed weights (FP32
-    and BF16 output); E4M3 from FP32 operands and from pre-quantised ones.
-    Every variant warm / flushed / rotating."""
-    I, W, bias = synth.conv_resnet_block(N=N)
+def conv_layer_report(torch, nk, synth, dev, N, H=56, C=64, F=64, fp8_peak_tflops=None):
+    """One 3x3 stride-1 layer N x H x H x C -> F (pad 1, bias + ReLU): FP32 on
+    the CUDA cores; BF16 with a per-call weight cast and with packed weights
+    (FP32 and BF16 output); E4M3 quantised per call from FP32 operands and
+    from operands quantised once (FP32 and BF16 output).  Every variant
+    warm / flushed / rotating; ratios to FP32 from the flushed times."""
+    I, W, bias = synth.conv_resnet_block(N=N, H=H, W=H, C=C, F=F)
     i32, w32, b32 = (torch.from_numpy(x).to(dev) for x in (I, W, bias))
-    out = torch.empty(N, 56, 56, 64, device=dev)
-    flop = 2.0 * N * 56 * 56 * 64 * 9 * 64
+    flop = 2.0 * N * H * H * F * 9 * C
     pad = (1, 1, 1, 1)
-    res = {"flop": flop}
+    res = {"flop": flop, "shape": f"{N}x{H}x{H}x{C} -> {F}, 3x3, stride 1, pad 1, bias + ReLU"}
+    o_elems = N * H * H * F
 
-    def add(name, call_of, set_bytes, out_bytes=4, roof=True):
+    def add(name, call_of, set_bytes, out_bytes=4, in_bytes=2, peak=None):
         t = timings3(torch, call_of(0), call_of, set_bytes)
         t["flushed_tflops"] = flop / (t["flushed_ms"] * 1e-3) / 1e12
         t["warm_tflops"] = flop / (t["warm_ms"] * 1e-3) / 1e12
-        if roof:
-            t["roofline"] = layer_roofline(N, 56, 56, 64, 64, 3, 3, 1, 1, t["flushed_ms"], out_bytes)
+        if in_bytes:
+            t["roofline"] = layer_roofline(N, H, H, C, F, 3, 3, 1, 1, t["flushed_ms"], out_bytes, in_bytes, peak)
         res[name] = t
-        return t
 
     def f32_call(i):
         ii = i32 if i == 0 else i32.clone()
-        oo = out if i == 0 else torch.empty_like(out)
+        oo = torch.empty(N, H, H, F, device=dev)
         return lambda: nk.nk_conv2d_nhwc_hwcf(ii, w32, oo, pad=pad, bias=b32, relu=True)
-    add("f32", f32_call, I.nbytes + out.numel() * 4, roof=False)
+    add("f32", f32_call, I.nbytes + o_elems * 4, in_bytes=0)
     i16 = i32.to(torch.bfloat16)
     wp = nk.nk_conv2d_pack_weights(w32)
 
@@ -589,29 +585,36 @@ def conv_layer_report(torch, nk, synth, dev, N):
         def make(i):
             ii = i16 if i == 0 else i16.clone()
             ww = (wp if i == 0 else nk.nk_conv2d_pack_weights(w32)) if packed else w32
-            oo = torch.empty(N, 56, 56, 64, device=dev, dtype=out_dtype)
+            oo = torch.empty(N, H, H, F, device=dev, dtype=out_dtype)
             ws = nk.workspace(nk.nk_conv2d_workspace_size(ii, ww, oo, pad=pad, precision="bf16"), dev)
             return lambda: nk.nk_conv2d_nhwc_hwcf(ii, ww, oo, pad=pad, precision="bf16", bias=b32, relu=True, ws=ws)
         return make
-    add("bf16_weight_cast_per_call", bf16_call(False), i16.numel() * 2 + out.numel() * 4)
-    add("bf16_packed", bf16_call(True), i16.numel() * 2 + out.numel() * 4)
-    if _has(nk, "supports_bf16_output"):
-        add("bf16_packed_bf16_out", bf16_call(True, torch.bfloat16), i16.numel() * 2 + out.numel() * 2, out_bytes=2)
+    add("bf16_weight_cast_per_call", bf16_call(False), i16.numel() * 2 + o_elems * 4)
+    add("bf16_packed", bf16_call(True), i16.numel() * 2 + o_elems * 4)
+    add("bf16_packed_bf16_out", bf16_call(True, torch.bfloat16), i16.numel() * 2 + o_elems * 2, out_bytes=2)
 
     def fp8_call(i):
         ii = i32 if i == 0 else i32.clone()
-        oo = torch.empty_like(out)
+        oo = torch.empty(N, H, H, F, device=dev)
         ws = nk.workspace(nk.nk_conv2d_workspace_size(ii, w32, oo, pad=pad, precision="fp8"), dev)
         return lambda: nk.nk_conv2d_nhwc_hwcf(ii, w32, oo, pad=pad, precision="fp8", bias=b32, relu=True, ws=ws)
-    add("fp8_from_f32", fp8_call, I.nbytes + out.numel() * 4, roof=False)
-    if _has(nk, "supports_fp8_prequantised_conv"):
-        q = nk.quantize_conv_operands(i32, w32)
+    add("fp8_quantised_per_call", fp8_call, I.nbytes + o_elems * 4, in_bytes=0)
+    wq, sw = nk.nk_conv2d_pack_weights_fp8(w32)
+    iq, si = nk.quantize_nhwc_fp8(i32)
+    s_i, s_w = float(si.item()), float(sw.item())
 
-        def fp8q_call(i):
-            qi = q if i == 0 else nk.quantize_conv_operands(i32, w32)
-            oo = torch.empty_like(out)
-            return lambda: nk.conv_fp8_prequantised(qi, oo, pad=pad, bias=b32, relu=True)
-        add("fp8_prequantised", fp8q_call, i16.numel() + out.numel() * 4, roof=False)
+    def fp8q_call(out_dtype):
+        def make(i):
+            qi = iq if i == 0 else iq.clone()
+            qw = wq if i == 0 else nk.nk_conv2d_pack_weights_fp8(w32)[0]
+            oo = torch.empty(N, H, H, F, device=dev, dtype=out_dtype)
+            ws = nk.workspace(nk.nk_conv2d_workspace_size(qi, qw, oo, pad=pad, precision="fp8"), dev)
+            return lambda: nk.nk_conv2d_nhwc_hwcf(qi, qw, oo, pad=pad, precision="fp8", bias=b32, relu=True, ws=ws,
+                                                  scale_i=s_i, scale_w=s_w)
+        return make
+    add("fp8_prequantised", fp8q_call(torch.float32), iq.numel() + o_elems * 4, in_bytes=1, peak=fp8_peak_tflops)
+    add("fp8_prequantised_bf16_out", fp8q_call(torch.bfloat16), iq.numel() + o_elems * 2, out_bytes=2, in_bytes=1,
+        peak=fp8_peak_tflops)
     nk.nk_sync_status()
     f32 = res["f32"]["flushed_ms"]
     res["ratios_flushed_vs_f32"] = {k: f32 / v["flushed_ms"] for k, v in res.items()
@@ -657,8 +660,7 @@ def resnet_report(torch, synth, dev):
         tot["evolution_regret"] = tot["evolution5_ms"] / tot["exhaustive_ms"] - 1
         tot["model_tflops"] = tot["flop"] / (tot["model_top5_ms"] * 1e-3) / 1e12
         tot["schedules_timed"] = timed
-        if hasattr(nt, "timing_method"):
-            tot["tuner_timing"] = nt.timing_method()
+        tot["tuner_timing"] = nt.timing_method()
         tot["stack_graph"] = stack_graph(torch, synth, dev, b, picks, tot["flop"])
         out[f"batch{b}"] = tot
     nt.nk_tune_release()
@@ -666,10 +668,13 @@ def resnet_report(torch, synth, dev):
 
 
 def stack_roofline_ms(synth, batch, out_bytes=4):
+    """Sum over the 20 layers of each layer's roofline time; out_bytes is one
+    value for every layer or a list with one per layer."""
     roof_ms = 0.0
-    for L in synth.resnet_stack(batch):
+    for li, L in enumerate(synth.resnet_stack(batch)):
+        ob = out_bytes[li] if isinstance(out_bytes, (list, tuple)) else out_bytes
         r = layer_roofline(L["N"], L["H"], L["W"], L["C"], L["F"], L["KH"], L["KW"], L["stride"], L["pad"], 1.0,
-                           out_bytes)
+                           ob)
         roof_ms += r["flop"] / (r["roofline_tflops"] * 1e12) * 1e3
     return roof_ms
 
@@ -715,8 +720,6 @@ def chained_forward_report(torch, nk, synth, dev):
     the epilogue); each stage's stride-2 3x3 and 1x1 projection read the
     stage input, and the stage's last conv adds the projection (a fused ADD
     of the residual) before its ReLU.  One CUDA graph per batch."""
-    if not _has(nk, "supports_bf16_output"):
-        return None
     import paper_2307_16080_gb300.forward as fwd
     out = {}
     for b in (1, 8, 32):
@@ -726,10 +729,12 @@ def chained_forward_report(torch, nk, synth, dev):
         ms = graph_time(torch, net.run, calls=2, reps=10)
         ms_flushed = flushed_time(torch, net.run, calls=4, trials=3)
         nk.nk_sync_status()
-        roof_ms = stack_roofline_ms(synth, b, out_bytes=2)
+        # BF16 activations; the projections and the head write FP32
+        ob = [4 if net.role(li) in ("projection", "head") else 2 for li in range(20)]
+        roof_ms = stack_roofline_ms(synth, b, out_bytes=ob)
         out[f"batch{b}"] = {"warm_ms": ms, "flushed_ms": ms_flushed,
                             "tflops_flushed": net.flop / (ms_flushed * 1e-3) / 1e12,
-                            "roofline_ms_bf16_out": roof_ms, "frac_of_roofline_flushed": roof_ms / ms_flushed,
+                            "roofline_ms": roof_ms, "frac_of_roofline_flushed": roof_ms / ms_flushed,
                             "kernels_per_forward": net.kernels}
     return out
 
@@ -772,6 +777,50 @@ def grouped_conv_report(torch, nk, synth, dev, batch=8):
             "speedup_warm": t_sep / t_grouped, "speedup_flushed": t_sep_f / t_grouped_f,
             "schedule": list(tuned), "schedules_timed": trep.timed, "untuned_default_ms": trep.default_ms,
             "how": "device time of CUDA-graph replays; grouped: per-tap kernel, tile from nk_conv2d_grouped_tune"}
+
+
+def sharded_extras(torch, nk, synth, dev, world, rank):
+    """Under torchrun: the other two splits of the path, each rank on its own
+    device memory with no data-path collective.  The 512-group GEMM by LPT
+    over ranks on the cost model's predicted time of each group, and the
+    32 x 56 x 56 x 64 conv by blocks of images.  Time = max over ranks."""
+    from paper_2307_16080_gb300 import costmodel, shard
+    from paper_2307_16080_gb300 import nk_tune as nt
+    out = {}
+    shapes = [tuple(int(v) for v in s) for s in synth.grouped_problems(512)]
+    probs = [nt.matmul_problem(M, N, K, "bf16") for (M, N, K) in shapes]
+    if os.path.exists(costmodel.MODEL_PATH):
+        P, ym, ys = costmodel.load_model()
+        cost, how = costmodel.predicted_ms(P, ym, ys, probs), "cost-model prediction of each group's time"
+    else:
+        cost, how = shard.gemm_flops(shapes), "2*M*N*K"
+    owner, loads = shard.lpt_assign(cost, world)
+    mine = [shapes[g] for g in shard.groups_of_rank(owner, rank)]
+    a = [torch.empty(M, K, device=dev).uniform_(-1, 1).to(torch.bfloat16) for (M, N, K) in mine]
+    bt = [torch.empty(N, K, device=dev).uniform_(-1, 1).to(torch.bfloat16) for (M, N, K) in mine]
+    c = [torch.empty(M, N, device=dev) for (M, N, K) in mine]
+    groups, G = nk.make_groups(a, bt, c)
+    plan = nk.nk_grouped_plan_create(groups, G)
+    t = flushed_time(torch, lambda: nk.nk_grouped_plan_run(plan), calls=8)
+    nk.nk_grouped_plan_destroy(plan)
+    t_max = shard.max_over_ranks(t)
+    flop = float(sum(2.0 * M * N * K for (M, N, K) in shapes))
+    out["grouped_512_lpt"] = {"ms_max_over_ranks": t_max, "tflops_all_ranks": flop / (t_max * 1e-3) / 1e12,
+                              "predicted_load_max_over_mean": float(loads.max() / loads.mean()), "cost": how}
+    Nb = 32
+    n0, n1 = shard.batch_blocks(Nb, world)[rank]
+    I, W, bias = synth.conv_resnet_block(N=Nb)
+    i16 = torch.from_numpy(I[n0:n1]).to(dev).to(torch.bfloat16)
+    wp = nk.nk_conv2d_pack_weights(torch.from_numpy(W).to(dev))
+    b = torch.from_numpy(bias).to(dev)
+    o = torch.empty(n1 - n0, 56, 56, 64, device=dev)
+    t = flushed_time(torch, lambda: nk.nk_conv2d_nhwc_hwcf(i16, wp, o, pad=(1, 1, 1, 1), precision="bf16", bias=b,
+                                                           relu=True)) if n1 > n0 else 0.0
+    t_max = shard.max_over_ranks(t)
+    out["conv_32x56x56x64_by_batch"] = {"ms_max_over_ranks": t_max, "images_per_rank": n1 - n0,
+                                        "tflops_all_ranks": 2.0 * Nb * 56 * 56 * 64 * 576 / (t_max * 1e-3) / 1e12}
+    nk.nk_sync_status()
+    return out
 
 
 # ------------------------------------------------------------------ --case
@@ -1025,19 +1074,22 @@ def main():
         e2e = e2e_report(torch, nk, dev, A, B, max(4, args.steps // 2))
         e2e["value"] = e2e["value"] * world   # every rank moves and computes its own block
     extra = {}
-    if not args.no_extra and rank == 0:
+    if not args.no_extra and world == 1:   # under torchrun the line carries the sharded extras instead
         extra["grouped_512_bf16"] = grouped_report(torch, nk, synth, dev)
-        extra["conv_8x56x56x64_3x3"] = conv_layer_report(torch, nk, synth, dev, 8)
-        extra["conv_32x56x56x64_3x3"] = conv_layer_report(torch, nk, synth, dev, 32)
+        fp8t = fp8pk.get("burst_tflops")
+        extra["conv_8x56x56x64_3x3"] = conv_layer_report(torch, nk, synth, dev, 8, fp8_peak_tflops=fp8t)
+        extra["conv_32x56x56x64_3x3"] = conv_layer_report(torch, nk, synth, dev, 32, fp8_peak_tflops=fp8t)
+        extra["conv_8x28x28x128_3x3"] = conv_layer_report(torch, nk, synth, dev, 8, 28, 128, 128, fp8t)
+        extra["conv_32x14x14x256_3x3"] = conv_layer_report(torch, nk, synth, dev, 32, 14, 256, 256, fp8t)
         rr = resnet_report(torch, synth, dev)
         if rr is not None:
             extra["resnet_stack_bf16"] = rr
-        ch = chained_forward_report(torch, nk, synth, dev)
-        if ch is not None:
-            extra["resnet_chained_forward_bf16"] = ch
+        extra["resnet_chained_forward_bf16"] = chained_forward_report(torch, nk, synth, dev)
         extra["grouped_conv_resnet_layers"] = grouped_conv_report(torch, nk, synth, dev)
         extra["fp8_peak_measured"] = fp8pk
 
+    if world > 1 and not args.no_extra:
+        extra["sharded"] = sharded_extras(torch, nk, synth, dev, world, rank)
     if rank != 0:
         if world > 1:
             dist.barrier()

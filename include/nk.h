@@ -269,7 +269,10 @@ nk_status nk_grouped_workspace_size(int32_t G, const nk_gemm_group* groups,
  * pad = {top, bottom, left, right}.
  * Precisions: NK_PREC_F32 (CUDA cores), NK_PREC_BF16, NK_PREC_FP8 (E4M3
  * with per-tensor scales s = 448/amax(|x|) of I and of W, computed on the
- * device and undone by 1/(s_i*s_w) in the epilogue; I and W FP32).
+ * device and undone by 1/(s_i*s_w) in the epilogue; I and W FP32 -- or both
+ * already E4M3: I NHWC with 16-byte multiples as strides and W packed by
+ * nk_conv2d_pack_weights_fp8, with their scales s_i, s_w as epi->scale_a,
+ * epi->scale_b, so that a call runs no amax and no quantisation).
  * I dtype: F32 (any precision; BF16 / E4M3 convert it into the workspace)
  * or BF16 with NK_PREC_BF16.  W dtype: F32 contiguous HWCF (converted per
  * call into the workspace), or -- NK_PREC_BF16 only -- BF16 already
@@ -278,7 +281,10 @@ nk_status nk_grouped_workspace_size(int32_t G, const nk_gemm_group* groups,
  * aligned base): no per-call conversion.
  * At NK_PREC_BF16 a stride-1 schedule with tile_k = 64*KH*KW selects the
  * shared-window kernel (each tile's input window is loaded once and read by
- * every tap); tile_k = 64 selects the per-tap implicit GEMM.              */
+ * every tap), tile_k = 64*KH the same window with the KW taps of a kernel
+ * row side by side along N; tile_k = 64 selects the per-tap implicit GEMM.
+ * At NK_PREC_FP8 the K blocks hold 128 channels: tile_k = 128*KH selects
+ * the stacked window kernel on E4M3 operands, tile_k = 128 the per-tap one. */
 nk_status nk_conv2d_nhwc_hwcf(const nk_tensor* I, const nk_tensor* W,
                               nk_tensor* O, const int64_t stride[2],
                               const int64_t dilation[2], const int64_t pad[4],
@@ -328,6 +334,24 @@ nk_status nk_conv2d_grouped_plan_create(int32_t G, const nk_conv_group* groups,
  * strides {KW*ldw, ldw, 1, KH*KW*ldw} so repeated calls skip the cast.   */
 nk_status nk_conv2d_pack_weights(const nk_tensor* W, void* Wp, int64_t ldw,
                                  void* stream);
+
+/* E4M3 weights for NK_PREC_FP8 convolutions, quantised once: the
+ * per-tensor scale s_w = 448/amax(|W|) (s_w = 1 when amax is 0) is computed
+ * on the device and written to *scale (device float), and each weight is
+ * stored as e4m3_rn_sat(W * s_w) in the packed layout of
+ * nk_conv2d_pack_weights: (kh,kw,c,f) at Wp + f*(KH*KW*ldw) + (kh*KW+kw)*ldw
+ * + c, ldw >= C a multiple of 16.  W: FP32 HWCF [KH,KW,C,F], contiguous.
+ * Wp: F*KH*KW*ldw bytes of device memory, 16-byte aligned.  ws/ws_bytes:
+ * device scratch of nk_conv2d_pack_weights_fp8_workspace_size() bytes.
+ * Asynchronous on `stream`.  Pass the result as an E4M3 W with strides
+ * {KW*ldw, ldw, 1, KH*KW*ldw} and s_w as epi->scale_b, together with an
+ * E4M3 I (quantised by the caller, e.g. with nk_amax and nk_cast_fp8 on the
+ * [N*H*W, C] view; s_i as epi->scale_a): the convolution then runs with no
+ * per-call quantisation and multiplies its result by 1/(s_i s_w).          */
+nk_status nk_conv2d_pack_weights_fp8(const nk_tensor* W, void* Wp, int64_t ldw,
+                                     float* scale, void* ws, size_t ws_bytes,
+                                     void* stream);
+size_t nk_conv2d_pack_weights_fp8_workspace_size(void);
 
 /* The convolution exactly as Sec. 4.1 Listing "2dnchwconv" lays it out:
  * I: [N,CI,H,W] (NCHW), K: [CO,CI,KH,KW] (FCHW, contiguous), O: [N,CO,OH,OW],

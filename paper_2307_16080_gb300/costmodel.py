@@ -9,9 +9,13 @@ that timing with a model:
   train     fit the 16 -> 128 -> 128 -> 1 GELU MLP to standardised ln ms with
             MSE + Adam, on the GPU, with the library's own kernels
             (nk_mlp_grad / nk_mlp_adam)
-  evaluate  on held-out problems (the 20-layer ResNet-style conv stack at
-            batch 1, 8, 32): regret = t(best of the model's top-k) /
-            t(exhaustive best) - 1, beside random-k and the built-in default
+  evaluate  on held-out problems: the 20-layer ResNet-style conv stack at
+            batch 1, 8, 32, and a second set that neither the model nor the
+            built-in default rule was fitted with (a 20-layer conv stack of
+            other widths, spatial sizes and strides, and 20 matmuls drawn
+            like the grouped-GEMM workload): regret = t(best of the model's
+            top-k) / t(exhaustive best) - 1, beside random-k, the built-in
+            default and the (1+1) evolution strategy given k timings
 
 Python here only orders the calls; every measurement and every training
 step runs in libnk.  Usage:
@@ -81,13 +85,45 @@ def heldout_problems():
     return out
 
 
+def heldout2_problems(seed: int = synth.SEED_COSTMODEL + 100):
+    """A second held-out set, fitted by nothing: 20 conv layers of a stack
+    with other channel counts (48 -> 384), spatial sizes (60 -> 10) and a
+    batch of 4 and 16, and 20 BF16 matmuls drawn like the grouped workload
+    (M, N, K log-uniform in [32, 2048], multiples of 16).  Problems that
+    coincide with a training problem are dropped."""
+    train = {tuple(problem_dict(p).values()) for p in training_problems()}
+    stack = []
+    for n in (4, 16):
+        cin, h = 48, 60
+        for cout, st in ((48, 1), (96, 2), (96, 1), (192, 2), (192, 1), (384, 2), (384, 1)):
+            if st == 2:
+                stack.append(nt.conv_problem(n, h, h, cin, cout, 3, 3, 2, 1))
+                h = (h + 2 - 3) // 2 + 1
+            else:
+                stack.append(nt.conv_problem(n, h, h, cin, cout, 3, 3, 1, 1))
+            cin = cout
+        stack.append(nt.conv_problem(n, h, h, cin, cin, 1, 1, 1, 0))
+        stack.append(nt.conv_problem(n, h, h, cin, 2 * cin, 1, 1, 1, 0))
+        stack.append(nt.conv_problem(n, 2 * h, 2 * h, cin // 2, cin, 1, 1, 2, 0))
+    shapes = synth.grouped_problems(20, seed)
+    mm = [nt.matmul_problem(int(M), int(N), int(K), "bf16") for M, N, K in shapes]
+    out = []
+    for p in stack + mm:
+        if tuple(problem_dict(p).values()) not in train:
+            out.append(p)
+    return out
+
+
 def problem_dict(p):
     return {f: int(getattr(p, f)) for f, _ in nt.nk_problem._fields_}
 
 
-def collect(problems, reps: int = 3, log=None):
-    """Time every legal schedule of every problem.  Returns a corpus dict."""
-    feats, y, pid, sched = [], [], [], []
+def collect(problems, reps: int = 3, log=None, evolution_k: int = 0):
+    """Time every legal schedule of every problem.  Returns a corpus dict.
+    evolution_k > 0 also runs the library's (1+1) evolution strategy with
+    that many timings per problem and keeps its pick ("es_pick"), so that
+    its regret is scored on the same exhaustive timings as the rest."""
+    feats, y, pid, sched, es = [], [], [], [], []
     for i, p in enumerate(problems):
         cands = nt.nk_enumerate_schedules(p)
         F = nt.nk_schedule_features(p, cands)
@@ -97,14 +133,20 @@ def collect(problems, reps: int = 3, log=None):
             y.append(math.log(max(ms, 1e-6)))
             pid.append(i)
             sched.append(s)
+        if evolution_k > 0:
+            pick, _ = nt.nk_tune(p, nt.NK_TUNE_EVOLUTION, topk=evolution_k, reps=reps)
+            es.append(pick)
         if log:
             log(f"problem {i + 1}/{len(problems)}: {len(cands)} schedules")
     nt.nk_tune_release()
     defaults = [nt.nk_default_schedule(p) for p in problems]
-    return {"X": np.asarray(feats, np.float32), "y": np.asarray(y, np.float64), "pid": np.asarray(pid),
-            "sched": np.asarray(sched, np.int32), "problems": np.asarray([list(problem_dict(p).values())
-                                                                          for p in problems], np.int32),
-            "defaults": np.asarray(defaults, np.int32)}
+    c = {"X": np.asarray(feats, np.float32), "y": np.asarray(y, np.float64), "pid": np.asarray(pid),
+         "sched": np.asarray(sched, np.int32), "problems": np.asarray([list(problem_dict(p).values())
+                                                                       for p in problems], np.int32),
+         "defaults": np.asarray(defaults, np.int32)}
+    if evolution_k > 0:
+        c["es_pick"] = np.asarray(es, np.int32)
+    return c
 
 
 def init_params(seed: int = 7) -> np.ndarray:
@@ -160,6 +202,15 @@ def predict(params: np.ndarray, X: np.ndarray) -> np.ndarray:
     return nt.nk_mlp_forward(P, Xd).cpu().numpy()
 
 
+def predicted_ms(params: np.ndarray, y_mean: float, y_std: float, problems, schedules=None) -> np.ndarray:
+    """The model's predicted time (ms) of each problem under its schedule
+    (default: the built-in one), e.g. as LPT costs for spreading a grouped
+    GEMM's groups over GPUs."""
+    scheds = schedules or [nt.nk_default_schedule(p) for p in problems]
+    X = np.concatenate([nt.nk_schedule_features(p, [s]) for p, s in zip(problems, scheds)]).astype(np.float32)
+    return np.exp(predict(params, X) * y_std + y_mean)
+
+
 def regrets(corpus, pred: np.ndarray, k: int = 5, seed: int = 13):
     """Per problem: model top-k, random-k and default regret vs the exhaustive best."""
     out = []
@@ -175,13 +226,18 @@ def regrets(corpus, pred: np.ndarray, k: int = 5, seed: int = 13):
         d = tuple(corpus["defaults"][i])
         drow = [j for j in rows if tuple(corpus["sched"][j]) == d]
         dms = np.exp(corpus["y"][drow[0]]) if drow else float("nan")
-        out.append({"model": model / best - 1, "random": rnd / best - 1, "default": dms / best - 1,
-                    "best_ms": float(best), "candidates": int(len(rows))})
+        r = {"model": model / best - 1, "random": rnd / best - 1, "default": dms / best - 1,
+             "best_ms": float(best), "candidates": int(len(rows))}
+        if "es_pick" in corpus:
+            e = tuple(corpus["es_pick"][i])
+            erow = [j for j in rows if tuple(corpus["sched"][j]) == e]
+            r["evolution"] = np.exp(corpus["y"][erow[0]]) / best - 1 if erow else float("nan")
+        out.append(r)
     return out
 
 
 def summarise(rs):
-    keys = ("model", "random", "default")
+    keys = ("model", "random", "default") + (("evolution",) if rs and "evolution" in rs[0] else ())
     s = {f"mean_{k}_regret": float(np.nanmean([r[k] for r in rs])) for k in keys}
     s.update({f"max_{k}_regret": float(np.nanmax([r[k] for r in rs])) for k in keys})
     tot_best = sum(r["best_ms"] for r in rs)
@@ -222,15 +278,20 @@ def main():
     t0 = time.time()
     tr_path = os.path.join(a.out, "corpus_train.npz")
     ho_path = os.path.join(a.out, "corpus_heldout.npz")
+    h2_path = os.path.join(a.out, "corpus_heldout2.npz")
+    evals = (("train", tr_path), ("heldout_resnet_stack", ho_path), ("heldout2_unfitted", h2_path))
     if a.cmd in ("collect", "all"):
         save_corpus(tr_path, collect(training_problems(), a.reps, log))
-        save_corpus(ho_path, collect(heldout_problems(), a.reps, log))
+        save_corpus(ho_path, collect(heldout_problems(), a.reps, log, evolution_k=a.k))
+        save_corpus(h2_path, collect(heldout2_problems(), a.reps, log, evolution_k=a.k))
         log(f"collected in {time.time() - t0:.0f} s")
     if a.cmd == "defaults":
         # After a change of the built-in default rule: re-derive each stored
         # problem's default schedule (host logic, no GPU) so that the default
         # regret of `eval` scores the current rule on the stored timings.
-        for path in (tr_path, ho_path):
+        for path in (tr_path, ho_path, h2_path):
+            if not os.path.exists(path):
+                continue
             c = load_corpus(path)
             c["defaults"] = np.asarray([nt.nk_default_schedule(nt.nk_problem(*[int(v) for v in pr]))
                                         for pr in c["problems"]], np.int32)
@@ -242,7 +303,9 @@ def main():
         if os.path.exists(rj):
             with open(rj) as f:
                 res = json.load(f)
-            for name, path in (("train", tr_path), ("heldout_resnet_stack", ho_path)):
+            for name, path in evals:
+                if name not in res or not os.path.exists(path):
+                    continue
                 c = load_corpus(path)
                 fresh = summarise(regrets(c, np.zeros(len(c["y"])), a.k))
                 res[name].update({k: v for k, v in fresh.items() if "default" in k})
@@ -257,10 +320,13 @@ def main():
     if a.cmd in ("eval", "all"):
         P, ym, ys = load_model(os.path.join(a.out, "cost_mlp.npz"))
         res = {}
-        for name, path in (("train", tr_path), ("heldout_resnet_stack", ho_path)):
+        for name, path in evals:
+            if not os.path.exists(path):
+                continue
             c = load_corpus(path)
             res[name] = summarise(regrets(c, predict(P, c["X"]), a.k))
         res["k"] = a.k
+        res["timing"] = nt.timing_method()
         print(json.dumps(res, indent=1), flush=True)
         with open(os.path.join(a.out, "regret.json"), "w") as f:
             json.dump(res, f, indent=1)

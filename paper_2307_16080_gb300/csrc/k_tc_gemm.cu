@@ -994,8 +994,8 @@ nk_status make_conv_maps(CUtensorMap* map_a, CUtensorMap* map_b, const TcConv& c
 }  // namespace
 
 bool tc_conv_schedule_valid(const ConvGeom& g, int F, const nk_schedule& s, int kind) {
-  if (kind == TC_BF16 && halo_schedule(g, s)) return halo_schedule_valid(g, F, s);
   if (kind != TC_BF16 && kind != TC_FP8) return false;
+  if (halo_schedule(g, s, kind)) return halo_schedule_valid(g, F, s, kind);
   if (g.sw > 8 || g.sh > 8 || s.tile_n == 512) return false;
   // E4M3 convolutions: one CTA per tile, tall tiles included (no CTA pairs)
   if (kind == TC_FP8 && s.cluster == 2) return false;
@@ -1012,8 +1012,8 @@ bool tc_conv_schedule_valid(const ConvGeom& g, int F, const nk_schedule& s, int 
 // deeper rings), and split-K while the grid would leave half the SMs idle.
 nk_schedule tc_conv_default_schedule(const ConvGeom& g, int F, int sms, int kind) {
   bool ok = false;
-  if (kind == TC_BF16) {
-    nk_schedule h = tc_halo_default_schedule(g, F, sms, &ok);
+  if (kind == TC_BF16 || kind == TC_FP8) {
+    nk_schedule h = tc_halo_default_schedule(g, F, sms, &ok, kind);
     if (ok) return h;
   }
   nk_schedule s{};
@@ -1040,7 +1040,7 @@ nk_schedule tc_conv_default_schedule(const ConvGeom& g, int F, int sms, int kind
 }
 
 size_t tc_conv_ws(const TcConv& c, const nk_schedule& s) {
-  if (s.split_k <= 1 || (c.kind == TC_BF16 && halo_schedule(c.g, s))) return 0;
+  if (s.split_k <= 1 || halo_schedule(c.g, s, c.kind)) return 0;
   return (size_t)s.split_k * c.g.n * c.g.oh * c.g.ow * c.F * sizeof(float);
 }
 
@@ -1050,7 +1050,7 @@ nk_status tc_conv(const TcConv& c, const nk_schedule& s, void* ws, size_t ws_byt
   if (status != NK_OK) return status;
   const ConvGeom& g = c.g;
   const int kind = c.kind;
-  if (kind == TC_BF16 && halo_schedule(g, s)) return tc_halo_conv(c, s, st);
+  if ((kind == TC_BF16 || kind == TC_FP8) && halo_schedule(g, s, kind)) return tc_halo_conv(c, s, st);
   const int M = g.n * g.oh * g.ow;
   if (g.sw > 8 || g.sh > 8) return fail(NK_ERR_UNSUPPORTED, "conv stride above 8");
   if (!tc_conv_schedule_valid(g, c.F, s, kind))
@@ -1090,7 +1090,8 @@ nk_status tc_conv(const TcConv& c, const nk_schedule& s, void* ws, size_t ws_byt
   p.bias = c.bias;
   p.relu = c.relu;
   p.beta = c.beta;
-  p.alpha = 1.f;
+  // E4M3 operands the caller quantised carry 1/(s_i s_w) in alpha
+  p.alpha = (kind == TC_FP8 && !c.scale_i) ? c.alpha : 1.f;
   p.scale_a = c.scale_i;   // E4M3: alpha = 1 / (s_i * s_w), read on the device
   p.scale_b = c.scale_w;
   p.ew = c.ew;
@@ -1123,7 +1124,7 @@ nk_status tc_conv(const TcConv& c, const nk_schedule& s, void* ws, size_t ws_byt
   r.scm = c.F;
   r.scn = 1;
   r.bias = c.bias;
-  r.alpha = 1.f;
+  r.alpha = (kind == TC_FP8 && !c.scale_i) ? c.alpha : 1.f;
   r.beta = c.beta;
   r.relu = c.relu;
   r.scale_a = c.scale_i;

@@ -85,7 +85,8 @@ struct HaloTile {
   int slot_rows;         // rows reserved per window slot (>= rows and >= the last row any tap reads)
   int tiles_w, tiles_h, tiles_b;
   int N, OH, OW, KH, KW, dh, dw, pt, pl;
-  int cblocks;           // 64-channel blocks
+  int cblocks;           // channel blocks of one 128-byte row
+  int cblk;              // channels per block: 64 BF16 or 128 E4M3
   int stk;               // taps side by side along N: KW when kernel rows are stacked, else 1
 };
 
@@ -107,6 +108,12 @@ struct HaloParams {
   int64_t budget;
   EwProg ew;             // fused elementwise program (offsets from O)
   int out_bf16;          // O holds BF16 (RNE of the FP32 epilogue result)
+  // E4M3 operands: the result is scaled by 1/(s_i s_w), from the device
+  // scalars the per-call quantisation wrote (scale_i, scale_w) or, for
+  // operands the caller quantised, from alpha
+  float alpha;
+  const float* scale_i;
+  const float* scale_w;
 };
 
 // First GEMM row a tap reads: tap (kh, kw) sees the window kh*dh rows down
@@ -129,10 +136,15 @@ __device__ __forceinline__ int tap_offset(const HaloTile& t, int tap) {
 // runs its dependent loads, shuffles and stores with nothing to hide their
 // latency), so DB gives it twice the warps: two per TMEM lane quarter, each
 // taking every other 32-column segment.
-template <int MCH, bool STK, bool DB = false>
+//
+// F8: E4M3 operands (stacked rows only): 128-channel K blocks, the same
+// 128-byte rows and 32-byte K steps (tcgen05.mma kind::f8f6f4, K = 32), the
+// result dequantised by 1/(s_i s_w) in the epilogue.
+template <int MCH, bool STK, bool DB = false, bool F8 = false>
 __global__ void __launch_bounds__(DB ? kThreadsDB : kThreads, 1) halo_conv_kernel(const __grid_constant__ HaloParams p) {
   static_assert(!STK || MCH == 1, "stacked kernel rows use one chain");
   static_assert(!DB || STK, "the double-buffered variant is a stacked-row kernel");
+  static_assert(!F8 || STK, "E4M3 window convolutions stack kernel rows");
   constexpr int NACC = (STK && !DB) ? 1 : 2;   // accumulator buffers
   constexpr int EPW = DB ? 2 : 1;              // epilogue warps per TMEM lane quarter
   extern __shared__ uint8_t smem_raw[];
@@ -223,7 +235,7 @@ __global__ void __launch_bounds__(DB ? kThreadsDB : kThreads, 1) halo_conv_kerne
             const uint32_t ph = (uint32_t)(wc / WS) & 1u;
             if (!ptx::mbar_wait(wempty(s), ph ^ 1u, p.budget, abort_flag, &g_halo_err)) { ok = false; break; }
             ptx::mbar_arrive_expect_tx(wfull(s), (uint32_t)t.rows * kRow);
-            ptx::tma_load_4d(wbase + (uint32_t)s * p.slot_bytes, &p.tmI, wfull(s), cb * 64, tw * t.Q - t.pl,
+            ptx::tma_load_4d(wbase + (uint32_t)s * p.slot_bytes, &p.tmI, wfull(s), cb * t.cblk, tw * t.Q - t.pl,
                              th * t.R - t.pt, tb * t.NB);
             ++wc;
           }
@@ -235,7 +247,7 @@ __global__ void __launch_bounds__(DB ? kThreadsDB : kThreads, 1) halo_conv_kerne
             ptx::mbar_arrive_expect_tx(bfull(s), b_tile);
             // one box of bn filters per tap; stacked: the KW taps of kernel row kg
             for (int j = 0; j < nst; ++j)
-              ptx::tma_load_3d(bbase + (uint32_t)s * b_tile + (uint32_t)(j * p.bn) * kRow, &p.tmW, bfull(s), cb * 64,
+              ptx::tma_load_3d(bbase + (uint32_t)s * b_tile + (uint32_t)(j * p.bn) * kRow, &p.tmW, bfull(s), cb * t.cblk,
                                kg * nst + j, tn * p.bn);
             ++bc;
           }
@@ -250,7 +262,7 @@ __global__ void __launch_bounds__(DB ? kThreadsDB : kThreads, 1) halo_conv_kerne
   } else if (warp == 1) {
     // -------------------------------------------------------------- MMA
     if (lane == 0) {
-      const uint32_t idesc = ptx::make_idesc(1, 128, p.bn * nst);
+      const uint32_t idesc = ptx::make_idesc(F8 ? 0 : 1, 128, p.bn * nst);
       int wc = 0, bc = 0, tc = 0;
       bool ok = true;
       for (int u = blockIdx.x; u < p.units && ok; u += gridDim.x, ++tc) {
@@ -284,7 +296,7 @@ __global__ void __launch_bounds__(DB ? kThreadsDB : kThreads, 1) halo_conv_kerne
               const uint32_t accum = (kb > 0 || k > 0) ? 1u : 0u;
 #pragma unroll
               for (int ch = 0; ch < MCH; ++ch)
-                ptx::tc_mma<0>(d + (uint32_t)(ch * p.bn), ptx::sw128_desc(a0 + (uint32_t)(ch * 128 * kRow) + 32u * k),
+                ptx::tc_mma<F8>(d + (uint32_t)(ch * p.bn), ptx::sw128_desc(a0 + (uint32_t)(ch * 128 * kRow) + 32u * k),
                                bd, idesc, accum);
             }
             if (!p.resident) {
@@ -307,6 +319,8 @@ __global__ void __launch_bounds__(DB ? kThreadsDB : kThreads, 1) halo_conv_kerne
     const int q = warp & 3;   // TMEM lane quarter this warp may read
     const int img_rows = t.WR * t.P;
     const int cfirst = ((warp - 2) / 4) * 32;     // this warp's first 32-column segment
+    float alpha = 1.f;                            // E4M3: 1 / (s_i s_w)
+    if constexpr (F8) alpha = p.scale_i ? __frcp_rn(__fmul_rn(*p.scale_i, *p.scale_w)) : p.alpha;
     int tc = 0;
     for (int u = blockIdx.x; u < p.units; u += gridDim.x, ++tc) {
       const int tn = u / p.tiles_m, tm = u - tn * p.tiles_m;
@@ -357,6 +371,10 @@ __global__ void __launch_bounds__(DB ? kThreadsDB : kThreads, 1) halo_conv_kerne
               for (int e = 0; e < 32; ++e) v[e] += __shfl_down_sync(0xffffffffu, w[e], sh);
             }
           }
+          }
+          if constexpr (F8) {
+#pragma unroll
+            for (int e = 0; e < 32; ++e) v[e] *= alpha;
           }
           const int col0 = tn * p.bn + c0;
           if (!row_ok || col0 >= p.F) continue;
@@ -489,23 +507,30 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 int taps_of(const ConvGeom& g) { return g.kh * g.kw; }
 
-// Kernel-row stacking: tile_k = 64 * KH (one K block per kernel row and
-// 64-channel block) selects the window kernel with the KW taps of a kernel
-// row side by side along N (N = 64 * KW <= 256, so 2 <= KW <= 4).  For BF16,
-// per-tap schedules have tile_k 64 and plain window schedules 64 * KH * KW,
-// so the encodings do not collide.
-bool stacked_schedule(const ConvGeom& g, const nk_schedule& s) {
-  return g.kh >= 2 && g.kw >= 2 && g.kw <= 4 && s.tile_k == 64 * g.kh;
+// Channels per K block: one 128-byte row, 64 BF16 or 128 E4M3.
+int cblk_of(int kind) { return kind == TC_FP8 ? 128 : 64; }
+
+// Kernel-row stacking: tile_k = cblk * KH (one K block per kernel row and
+// channel block) selects the window kernel with the KW taps of a kernel row
+// side by side along N (N = 64 * KW <= 256, so 2 <= KW <= 4).  Per-tap
+// schedules have tile_k = cblk and plain window schedules 64 * KH * KW
+// (BF16 only), so the encodings do not collide.
+bool stacked_schedule(const ConvGeom& g, const nk_schedule& s, int kind = TC_BF16) {
+  return g.kh >= 2 && g.kw >= 2 && g.kw <= 4 && s.tile_k == cblk_of(kind) * g.kh;
 }
 
 // Stacked kernel rows with tile_m 256: one 128-row tile at a time, but two
 // accumulator buffers (all 512 TMEM columns, one CTA per SM) so the
 // epilogue of a tile overlaps the MMAs of the next.
-bool stacked_db(const ConvGeom& g, const nk_schedule& s) { return stacked_schedule(g, s) && s.tile_m == 256; }
+bool stacked_db(const ConvGeom& g, const nk_schedule& s, int kind = TC_BF16) {
+  return stacked_schedule(g, s, kind) && s.tile_m == 256;
+}
 
 // Accumulator chains of a window schedule: tile_m / 128 stacked 128-row
 // tiles for the plain window; stacked kernel rows always use one.
-int chains_of(const ConvGeom& g, const nk_schedule& s) { return stacked_schedule(g, s) ? 1 : s.tile_m / 128; }
+int chains_of(const ConvGeom& g, const nk_schedule& s, int kind = TC_BF16) {
+  return stacked_schedule(g, s, kind) ? 1 : s.tile_m / 128;
+}
 
 // Largest row offset the A operand reads, in GEMM rows (stacked: the kw
 // shifts move to the epilogue).
@@ -623,11 +648,13 @@ int halo_ctas(int smem, int tmem_cols) {
 // otherwise they stream through a ring of up to 8 tiles (at least two).  Of
 // the two, the layout that lets more CTAs (independent MMA chains) share an
 // SM wins; on a tie, resident weights.
-bool halo_layout(const ConvGeom& g, int F, const nk_schedule& s, HaloLayout* L) {
-  const int mch = chains_of(g, s);
-  const bool stk = stacked_schedule(g, s);
+bool halo_layout(const ConvGeom& g, int F, const nk_schedule& s, HaloLayout* L, int kind = TC_BF16) {
+  const int mch = chains_of(g, s, kind);
+  const bool stk = stacked_schedule(g, s, kind);
   if (!cached_halo_tile(g, mch, stk, &L->t)) return false;
-  const int tcols = halo_tmem_cols(mch, s.tile_n, L->t.stk, stacked_db(g, s));
+  L->t.cblk = cblk_of(kind);
+  L->t.cblocks = (g.c + L->t.cblk - 1) / L->t.cblk;
+  const int tcols = halo_tmem_cols(mch, s.tile_n, L->t.stk, stacked_db(g, s, kind));
   L->slot_bytes = (uint32_t)((L->t.slot_rows * kRow + 1023) / 1024 * 1024);
   L->wslots = s.stages;
   const int fixed = 1024 + s.stages * (int)L->slot_bytes + kBarBytes;
@@ -652,9 +679,9 @@ bool halo_layout(const ConvGeom& g, int F, const nk_schedule& s, HaloLayout* L) 
   return L->smem <= kMaxSmem;
 }
 
-template <int MCH, bool STK = false, bool DB = false>
+template <int MCH, bool STK = false, bool DB = false, bool F8 = false>
 nk_status launch(const HaloParams& p, int grid, int smem, cudaStream_t st) {
-  auto kern = halo_conv_kernel<MCH, STK, DB>;
+  auto kern = halo_conv_kernel<MCH, STK, DB, F8>;
   static int set_bytes[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
@@ -669,32 +696,33 @@ nk_status launch(const HaloParams& p, int grid, int smem, cudaStream_t st) {
 
 }  // namespace
 
-bool halo_schedule(const ConvGeom& g, const nk_schedule& s) {
+bool halo_schedule(const ConvGeom& g, const nk_schedule& s, int kind) {
+  if (kind == TC_FP8) return stacked_schedule(g, s, kind);   // E4M3: stacked rows only
   return (taps_of(g) > 1 && s.tile_k == 64 * taps_of(g)) || stacked_schedule(g, s);
 }
 
-bool halo_schedule_valid(const ConvGeom& g, int F, const nk_schedule& s) {
-  if (!halo_schedule(g, s)) return false;
+bool halo_schedule_valid(const ConvGeom& g, int F, const nk_schedule& s, int kind) {
+  if (!halo_schedule(g, s, kind)) return false;
   if (g.sh != 1 || g.sw != 1) return false;
   if (s.tile_m != 128 && s.tile_m != 256 && s.tile_m != 512) return false;
   if (s.tile_n != 64 && s.tile_n != 128 && s.tile_n != 256) return false;
-  if (chains_of(g, s) * s.tile_n > 256) return false;   // two accumulator buffers in 512 TMEM columns
+  if (chains_of(g, s, kind) * s.tile_n > 256) return false;   // two accumulator buffers in 512 TMEM columns
   // stacked: N = 64 * KW; tile_m 128 (one buffer) or 256 (two buffers)
-  if (stacked_schedule(g, s) && (s.tile_m > 256 || s.tile_n != 64)) return false;
+  if (stacked_schedule(g, s, kind) && (s.tile_m > 256 || s.tile_n != 64)) return false;
   if (s.cluster != 1 || s.split_k != 1) return false;
   // window slots: up to 4, up to 8 beside the two buffers of one CTA per SM
-  if (s.stages < 1 || s.stages > (stacked_db(g, s) ? 8 : 4)) return false;
+  if (s.stages < 1 || s.stages > (stacked_db(g, s, kind) ? 8 : 4)) return false;
   HaloLayout L;
-  return halo_layout(g, F, s, &L);
+  return halo_layout(g, F, s, &L, kind);
 }
 
 // Host-side geometry of a window schedule (see nk_conv_window_tile).
-bool halo_tile_info(const ConvGeom& g, int F, const nk_schedule& s, int32_t out[10]) {
+bool halo_tile_info(const ConvGeom& g, int F, const nk_schedule& s, int32_t out[10], int kind) {
   HaloLayout L;
-  if (!halo_schedule_valid(g, F, s) || !halo_layout(g, F, s, &L)) return false;
+  if (!halo_schedule_valid(g, F, s, kind) || !halo_layout(g, F, s, &L, kind)) return false;
   const HaloTile& t = L.t;
   const int32_t v[10] = {t.P, t.Q, t.R, t.NB, t.WR, t.rows, t.slot_rows, t.stk,
-                         t.tiles_w * t.tiles_h * t.tiles_b, chains_of(g, s)};
+                         t.tiles_w * t.tiles_h * t.tiles_b, chains_of(g, s, kind)};
   for (int i = 0; i < 10; ++i) out[i] = v[i];
   return true;
 }
@@ -711,16 +739,29 @@ bool halo_tile_info(const ConvGeom& g, int F, const nk_schedule& s, int32_t out[
 // or > 4, e.g. 5x5), the tuner's corpus has the per-tap kernel ahead of the
 // plain window (which stays in the schedule space).  One chain and one
 // window slot keep two CTAs (two independent MMA chains) per SM.
-nk_schedule tc_halo_default_schedule(const ConvGeom& g, int F, int sms, bool* ok) {
+nk_schedule tc_halo_default_schedule(const ConvGeom& g, int F, int sms, bool* ok, int kind) {
   nk_schedule best{};
   *ok = false;
   if (taps_of(g) <= 1 || g.sh != 1 || g.sw != 1) return best;
-  for (int st : {g.c <= 64 ? 1 : 2, g.c <= 64 ? 2 : 1}) {
-    nk_schedule s{128, 64, 64 * g.kh, 1, st, 1};
+  // E4M3 reads 128 channels per K block: below C = 128 a window kernel
+  // would fill half of every block with zeros, so the per-tap kernel keeps
+  // those layers.
+  if (kind == TC_FP8 && g.c < 128) return best;
+  const int cb = cblk_of(kind);
+  for (int st : {g.c <= cb ? 1 : 2, g.c <= cb ? 2 : 1}) {
+    nk_schedule s{128, 64, cb * g.kh, 1, st, 1};
     HaloLayout L;
-    if (!stacked_schedule(g, s) || !halo_schedule_valid(g, F, s) || !halo_layout(g, F, s, &L)) continue;
+    if (!stacked_schedule(g, s, kind) || !halo_schedule_valid(g, F, s, kind) || !halo_layout(g, F, s, &L, kind))
+      continue;
     const int64_t units = (int64_t)L.t.tiles_w * L.t.tiles_h * L.t.tiles_b * ((F + 63) / 64);
     if (g.c > 128 && units * 8 < sms) break;
+    // With enough tiles that every CTA of the two-per-SM grid gets two or
+    // more, two accumulator buffers on one CTA per SM overlap each tile's
+    // epilogue with the next tile's MMAs: 16.0 against 17.4 us at
+    // 32x56x56x64 (896 tiles); at 8x56x56x64 (224 tiles) one buffer stays
+    // ahead, 8.0 against 8.3 us.
+    const nk_schedule d{256, 64, cb * g.kh, 1, 2, 1};
+    if (units >= 4 * (int64_t)sms && halo_schedule_valid(g, F, d, kind)) s = d;
     *ok = true;
     return s;
   }
@@ -732,12 +773,16 @@ nk_status tc_halo_conv(const TcConv& c, const nk_schedule& s, cudaStream_t st) {
   nk_status status = require_device(&sms);
   if (status != NK_OK) return status;
   const ConvGeom& g = c.g;
+  const int kind = c.kind;
+  const bool f8 = kind == TC_FP8;
+  const int esz = f8 ? 1 : 2;
   HaloLayout L;
-  if (!halo_schedule_valid(g, c.F, s) || !halo_layout(g, c.F, s, &L))
+  if (!halo_schedule_valid(g, c.F, s, kind) || !halo_layout(g, c.F, s, &L, kind))
     return fail(NK_ERR_NO_SCHEDULE, "illegal window-conv schedule");
-  if ((c.sI_w * 2) % 16 || (c.sI_h * 2) % 16 || (c.sI_n * 2) % 16 || (c.ldw * 2) % 16 || (c.sW_f * 2) % 16 ||
-      (reinterpret_cast<uintptr_t>(c.I) & 15) || (reinterpret_cast<uintptr_t>(c.Wt) & 15))
+  if ((c.sI_w * esz) % 16 || (c.sI_h * esz) % 16 || (c.sI_n * esz) % 16 || (c.ldw * esz) % 16 ||
+      (c.sW_f * esz) % 16 || (reinterpret_cast<uintptr_t>(c.I) & 15) || (reinterpret_cast<uintptr_t>(c.Wt) & 15))
     return fail(NK_ERR_MISALIGNED, "conv operands need 16-byte aligned rows");
+  const CUtensorMapDataType dt = f8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   auto fn = encode_fn();
   if (!fn) return fail(NK_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
   HaloParams p{};
@@ -745,10 +790,10 @@ nk_status tc_halo_conv(const TcConv& c, const nk_schedule& s, cudaStream_t st) {
   const HaloTile& t = L.t;
   {
     cuuint64_t dims[4] = {(cuuint64_t)g.c, (cuuint64_t)g.w, (cuuint64_t)g.h, (cuuint64_t)g.n};
-    cuuint64_t strides[3] = {(cuuint64_t)c.sI_w * 2, (cuuint64_t)c.sI_h * 2, (cuuint64_t)c.sI_n * 2};
-    cuuint32_t box[4] = {64, (cuuint32_t)t.P, (cuuint32_t)t.WR, (cuuint32_t)t.NB};
+    cuuint64_t strides[3] = {(cuuint64_t)c.sI_w * esz, (cuuint64_t)c.sI_h * esz, (cuuint64_t)c.sI_n * esz};
+    cuuint32_t box[4] = {(cuuint32_t)t.cblk, (cuuint32_t)t.P, (cuuint32_t)t.WR, (cuuint32_t)t.NB};
     cuuint32_t es[4] = {1, 1, 1, 1};
-    CUresult r = fn(&p.tmI, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(c.I), dims, strides, box, es,
+    CUresult r = fn(&p.tmI, dt, 4, const_cast<void*>(c.I), dims, strides, box, es,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(NK_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d) for the conv window", (int)r);
@@ -756,10 +801,10 @@ nk_status tc_halo_conv(const TcConv& c, const nk_schedule& s, cudaStream_t st) {
   {
     const int taps = taps_of(g);
     cuuint64_t dims[3] = {(cuuint64_t)g.c, (cuuint64_t)taps, (cuuint64_t)c.F};
-    cuuint64_t strides[2] = {(cuuint64_t)c.ldw * 2, (cuuint64_t)c.sW_f * 2};
-    cuuint32_t box[3] = {64, 1, (cuuint32_t)s.tile_n};
+    cuuint64_t strides[2] = {(cuuint64_t)c.ldw * esz, (cuuint64_t)c.sW_f * esz};
+    cuuint32_t box[3] = {(cuuint32_t)t.cblk, 1, (cuuint32_t)s.tile_n};
     cuuint32_t es[3] = {1, 1, 1};
-    CUresult r = fn(&p.tmW, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(c.Wt), dims, strides, box, es,
+    CUresult r = fn(&p.tmW, dt, 3, const_cast<void*>(c.Wt), dims, strides, box, es,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(NK_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d) for the conv filters", (int)r);
@@ -782,10 +827,17 @@ nk_status tc_halo_conv(const TcConv& c, const nk_schedule& s, cudaStream_t st) {
   p.c_vec = ((reinterpret_cast<uintptr_t>(c.O) & 15) == 0 && c.F % (c.out_bf16 ? 8 : 4) == 0) ? 1 : 0;
   p.c_vec32 = ((reinterpret_cast<uintptr_t>(c.O) & 31) == 0 && c.F % (c.out_bf16 ? 16 : 8) == 0) ? 1 : 0;
   p.budget = wait_budget();
+  p.alpha = c.alpha;
+  p.scale_i = c.scale_i;
+  p.scale_w = c.scale_w;
   if (p.units == 0) return NK_OK;
-  const bool db = stacked_db(g, s);
+  const bool db = stacked_db(g, s, kind);
   const int grid =
-      std::min(p.units, sms * halo_ctas(L.smem, halo_tmem_cols(chains_of(g, s), s.tile_n, t.stk, db)));
+      std::min(p.units, sms * halo_ctas(L.smem, halo_tmem_cols(chains_of(g, s, kind), s.tile_n, t.stk, db)));
+  if (f8) {
+    if (t.stk <= 1) return fail(NK_ERR_NO_SCHEDULE, "E4M3 window convolutions stack kernel rows");
+    return db ? launch<1, true, true, true>(p, grid, L.smem, st) : launch<1, true, false, true>(p, grid, L.smem, st);
+  }
   if (t.stk > 1) return db ? launch<1, true, true>(p, grid, L.smem, st) : launch<1, true>(p, grid, L.smem, st);
   switch (chains_of(g, s)) {
     case 1: return launch<1>(p, grid, L.smem, st);

@@ -13,6 +13,7 @@
 #include <string.h>
 
 #include <atomic>
+#include <cmath>
 #include <mutex>
 #include <string>
 #include <utility>
@@ -465,13 +466,14 @@ nk_status nk_matmul(const nk_tensor* A, const nk_tensor* B, nk_tensor* C, int32_
 }
 
 // ------------------------------------------------------------------ conv
-// BF16 weights in the tensor-core layout: W[kh,kw,c,f] at
-// f*sF + (kh*KW + kw)*ldw + c, ldw >= C, sF >= KH*KW*ldw, both multiples of 8
-// elements (16-byte rows for TMA).
+// BF16 or E4M3 weights in the tensor-core layout: W[kh,kw,c,f] at
+// f*sF + (kh*KW + kw)*ldw + c, ldw >= C, sF >= KH*KW*ldw, both multiples of
+// 16 bytes (8 BF16, 16 E4M3: 16-byte rows for TMA).
 static bool packed_weights(const nk_tensor* W) {
   const int64_t ldw = W->stride[1], sF = W->stride[3];
-  return W->stride[2] == 1 && ldw >= W->shape[2] && ldw % 8 == 0 && W->stride[0] == W->shape[1] * ldw &&
-         sF % 8 == 0 && sF >= W->shape[0] * W->shape[1] * ldw;
+  const int per16 = W->dtype == NK_F8E4M3 ? 16 : 8;
+  return W->stride[2] == 1 && ldw >= W->shape[2] && ldw % per16 == 0 && W->stride[0] == W->shape[1] * ldw &&
+         sF % per16 == 0 && sF >= W->shape[0] * W->shape[1] * ldw;
 }
 
 static nk_status plan_conv(const nk_tensor* I, const nk_tensor* W, const nk_tensor* O,
@@ -483,8 +485,9 @@ static nk_status plan_conv(const nk_tensor* I, const nk_tensor* W, const nk_tens
   if (I->stride[3] != 1 || O->stride[3] != 1)
     return fail(NK_ERR_UNSUPPORTED, "the last dimension of I and O must have unit stride");
   if (O->dtype != NK_F32 && O->dtype != NK_BF16) return fail(NK_ERR_UNSUPPORTED, "O must be FP32 or BF16");
-  if ((I->dtype != NK_F32 && I->dtype != NK_BF16) || (W->dtype != NK_F32 && W->dtype != NK_BF16))
-    return fail(NK_ERR_INVALID_ARG, "I and W must be FP32 or BF16");
+  if ((I->dtype != NK_F32 && I->dtype != NK_BF16 && I->dtype != NK_F8E4M3) ||
+      (W->dtype != NK_F32 && W->dtype != NK_BF16 && W->dtype != NK_F8E4M3))
+    return fail(NK_ERR_INVALID_ARG, "I and W must be FP32, BF16 or E4M3");
   for (int i = 0; i < 2; ++i)
     if (stride[i] < 1 || dilation[i] < 1) return fail(NK_ERR_INVALID_ARG, "stride and dilation must be >= 1");
   for (int i = 0; i < 4; ++i)
@@ -502,13 +505,13 @@ static nk_status plan_conv(const nk_tensor* I, const nk_tensor* W, const nk_tens
                 (long long)oh, (long long)ow, (long long)W->shape[3]);
   g.oh = (int)oh; g.ow = (int)ow;
   g.sin_n = I->stride[0]; g.sin_h = I->stride[1]; g.sin_w = I->stride[2];
-  if (W->dtype == NK_BF16) {
-    // packed for the tensor cores (nk_conv2d_pack_weights): channels
+  if (W->dtype == NK_BF16 || W->dtype == NK_F8E4M3) {
+    // packed for the tensor cores (nk_conv2d_pack_weights / _fp8): channels
     // contiguous per filter tap, taps at a uniform stride
     if (!packed_weights(W))
       return fail(NK_ERR_UNSUPPORTED,
-                  "a BF16 W must be packed: strides {KW*ldw, ldw, 1, sF} with ldw >= C and sF >= KH*KW*ldw, "
-                  "both multiples of 8 (see nk_conv2d_pack_weights)");
+                  "a BF16 / E4M3 W must be packed: strides {KW*ldw, ldw, 1, sF} with ldw >= C and "
+                  "sF >= KH*KW*ldw, both 16-byte multiples (see nk_conv2d_pack_weights)");
   } else if (W->stride[3] != 1 || W->stride[2] != W->shape[3] || W->stride[1] != W->shape[2] * W->shape[3] ||
              W->stride[0] != W->shape[1] * W->shape[2] * W->shape[3]) {
     return fail(NK_ERR_UNSUPPORTED, "an FP32 W must be contiguous HWCF");
@@ -531,10 +534,17 @@ struct ConvPlan {
 static nk_status plan_tc_conv(const nk_tensor* I, const nk_tensor* W, const nk_tensor* O, const ConvGeom& g,
                               int precision, const nk_schedule* user, ConvPlan& P) {
   P.kind = precision == NK_PREC_FP8 ? TC_FP8 : TC_BF16;
-  if (P.kind == TC_FP8 && (I->dtype != NK_F32 || W->dtype != NK_F32))
-    return fail(NK_ERR_UNSUPPORTED, "an E4M3 convolution takes FP32 I and W (quantised with per-tensor scales)");
-  if (W->dtype == NK_BF16 && (reinterpret_cast<uintptr_t>(W->ptr) & 15))
-    return fail(NK_ERR_MISALIGNED, "packed BF16 weights must be 16-byte aligned");
+  const bool f8_in = I->dtype == NK_F8E4M3, f8_w = W->dtype == NK_F8E4M3;
+  if (P.kind == TC_FP8 && !((I->dtype == NK_F32 && W->dtype == NK_F32) || (f8_in && f8_w)))
+    return fail(NK_ERR_UNSUPPORTED,
+                "an E4M3 convolution takes FP32 I and W (quantised per call with per-tensor scales) or both "
+                "already in E4M3 (I NHWC, W packed by nk_conv2d_pack_weights_fp8; scales in the epilogue)");
+  if (P.kind == TC_BF16 && (f8_in || f8_w))
+    return fail(NK_ERR_UNSUPPORTED, "E4M3 operands need NK_PREC_FP8");
+  if ((W->dtype == NK_BF16 || f8_w) && (reinterpret_cast<uintptr_t>(W->ptr) & 15))
+    return fail(NK_ERR_MISALIGNED, "packed weights must be 16-byte aligned");
+  if (f8_in && ((reinterpret_cast<uintptr_t>(I->ptr) & 15) || g.sin_w % 16 || g.sin_h % 16 || g.sin_n % 16))
+    return fail(NK_ERR_MISALIGNED, "an E4M3 I needs a 16-byte aligned base and 16-byte multiples for its strides");
   int sms = 152, dev = 0, v = 0;
   if (cudaGetDevice(&dev) == cudaSuccess &&
       cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
@@ -562,7 +572,7 @@ static nk_status plan_tc_conv(const nk_tensor* I, const nk_tensor* W, const nk_t
   if (P.cast_i) { P.off_i = off; off += align_up((size_t)g.n * g.h * g.w * P.Cp * esz); }
   P.cast_w = W->dtype == NK_F32;
   if (P.cast_w) { P.off_w = off; off += align_up((size_t)F * g.kh * g.kw * P.Cp * esz); }
-  if (P.kind == TC_FP8) {
+  if (P.kind == TC_FP8 && P.cast_i) {   // per-call quantisation
     P.off_scal = off; off += kAlign;                      // amax_i, amax_w, s_i, s_w
     P.off_amax = off; off += align_up(prep_amax_ws(0));
   }
@@ -634,7 +644,8 @@ nk_status nk_conv2d_nhwc_hwcf(const nk_tensor* I, const nk_tensor* W, nk_tensor*
   if ((s = ew_program(E.pro_a, I, &pro_i, "pro_a (I)")) != NK_OK) return s;
   if ((s = ew_program(E.pro_b, W, &pro_w, "pro_b (W)")) != NK_OK) return s;
   if ((pro_i.n && I->dtype != NK_F32) || (pro_w.n && W->dtype != NK_F32))
-    return fail(NK_ERR_UNSUPPORTED, "a prologue needs an FP32 operand (BF16 / packed operands are already cast)");
+    return fail(NK_ERR_UNSUPPORTED,
+                "a prologue needs an FP32 operand (BF16 / E4M3 / packed operands are already converted)");
   if ((s = require_device()) != NK_OK) return s;
   if (precision == NK_PREC_BF16 || precision == NK_PREC_FP8) {
     ConvPlan P;
@@ -649,8 +660,16 @@ nk_status nk_conv2d_nhwc_hwcf(const nk_tensor* I, const nk_tensor* W, nk_tensor*
     TcConv c{};
     c.kind = P.kind; c.g = g; c.F = F;
     // E4M3: per-tensor amax of I and W, then s = 448 / amax in the casts
-    float* scal = P.kind == TC_FP8 ? reinterpret_cast<float*>(w + P.off_scal) : nullptr;
-    if (P.kind == TC_FP8) {
+    const bool prequant = P.kind == TC_FP8 && I->dtype == NK_F8E4M3;
+    c.alpha = 1.f;
+    if (prequant) {
+      // the caller's scales: the result is multiplied by 1/(s_i s_w)
+      if (!(E.scale_a > 0.f) || !(E.scale_b > 0.f) || !std::isfinite(E.scale_a) || !std::isfinite(E.scale_b))
+        return fail(NK_ERR_INVALID_ARG, "pre-quantised E4M3 operands need positive finite scale_a (I), scale_b (W)");
+      c.alpha = 1.f / (E.scale_a * E.scale_b);
+    }
+    float* scal = (P.kind == TC_FP8 && !prequant) ? reinterpret_cast<float*>(w + P.off_scal) : nullptr;
+    if (P.kind == TC_FP8 && !prequant) {
       void* aw = w + P.off_amax;
       const size_t awb = prep_amax_ws(0);
       if ((s = prep_amax(static_cast<const float*>(I->ptr), (int64_t)g.n * g.h * g.w, g.c, g.c, scal + 0, aw, awb,
@@ -730,6 +749,34 @@ nk_status nk_conv2d_pack_weights(const nk_tensor* W, void* Wp, int64_t ldw, void
   return pack_weights(0, static_cast<const float*>(W->ptr), (int)(W->shape[0] * W->shape[1]), (int)W->shape[2],
                       (int)W->shape[3], ldw, Wp, nullptr, nullptr, static_cast<cudaStream_t>(stream));
 }
+
+nk_status nk_conv2d_pack_weights_fp8(const nk_tensor* W, void* Wp, int64_t ldw, float* scale, void* ws,
+                                     size_t ws_bytes, void* stream) {
+  nk::NvtxRange nvtx_range_("nk_conv2d_pack_weights_fp8");
+  if (!W || !Wp || !scale) return fail(NK_ERR_INVALID_ARG, "W, Wp and scale must be non-NULL");
+  if (W->rank != 4 || W->dtype != NK_F32) return fail(NK_ERR_INVALID_ARG, "W must be a rank-4 FP32 tensor");
+  if (W->stride[3] != 1 || W->stride[2] != W->shape[3] || W->stride[1] != W->shape[2] * W->shape[3] ||
+      W->stride[0] != W->shape[1] * W->shape[2] * W->shape[3])
+    return fail(NK_ERR_UNSUPPORTED, "W must be contiguous HWCF");
+  for (int i = 0; i < 4; ++i)
+    if (W->shape[i] < 1) return fail(NK_ERR_INVALID_ARG, "W extents must be positive");
+  if (ldw < W->shape[2] || ldw % 16) return fail(NK_ERR_INVALID_ARG, "ldw must be >= C and a multiple of 16");
+  if (!aligned16(Wp)) return fail(NK_ERR_MISALIGNED, "Wp must be 16-byte aligned");
+  if (reinterpret_cast<uintptr_t>(scale) & 3) return fail(NK_ERR_MISALIGNED, "scale must be 4-byte aligned");
+  const int taps = (int)(W->shape[0] * W->shape[1]), C = (int)W->shape[2], F = (int)W->shape[3];
+  const size_t need = align_up(prep_amax_ws((int64_t)taps * C * F)) + kAlign;
+  if (!ws || ws_bytes < need) return fail(NK_ERR_WORKSPACE, "packing needs %zu bytes of workspace", need);
+  if (!aligned16(ws)) return fail(NK_ERR_MISALIGNED, "workspace must be 16-byte aligned");
+  nk_status s = require_device();
+  if (s != NK_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  float* amax = reinterpret_cast<float*>(static_cast<char*>(ws) + align_up(prep_amax_ws(0)));
+  const float* Wf = static_cast<const float*>(W->ptr);
+  if ((s = prep_amax(Wf, (int64_t)taps * C, F, F, amax, ws, prep_amax_ws(0), st)) != NK_OK) return s;
+  return pack_weights(1, Wf, taps, C, F, ldw, Wp, amax, scale, st);
+}
+
+size_t nk_conv2d_pack_weights_fp8_workspace_size(void) { return align_up(prep_amax_ws(0)) + kAlign; }
 
 // ------------------------------------------------------------- elementwise
 nk_status nk_elementwise(const nk_tensor* X, nk_tensor* Y, const nk_ew_program* prog, void* stream) {

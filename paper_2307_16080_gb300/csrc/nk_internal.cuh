@@ -101,9 +101,10 @@ nk_status collect_device_errors(uint32_t* flags);
 // Median device time (ms) of one call of `run` (which enqueues its kernels
 // on the stream it is given): graph replays of back-to-back calls on a
 // library stream, behind a hold kernel, so host call overhead is not timed
-// (tune.cu).
+// (tune.cu).  Successive calls of `run` may cycle through `cycle` buffer
+// sets; every timed sample then covers a whole number of cycles.
 using RunFn = std::function<nk_status(cudaStream_t)>;
-nk_status time_device(const RunFn& run, int reps, float* ms);
+nk_status time_device(const RunFn& run, int reps, float* ms, int cycle = 1);
 uint32_t tc_read_and_clear_errors();   // tcgen05 GEMM / conv units
 
 // ----------------------------------------------------------- SIMT (FP32)
@@ -241,6 +242,7 @@ struct TcConv {
   const float* scale_w;
   EwProg ew;              // epilogue program (offsets from O)
   int out_bf16;
+  float alpha;            // E4M3 operands the caller quantised: 1/(s_i*s_w) (scale_i, scale_w null)
 };
 // tc_conv dispatches a window schedule (see below) to tc_halo_conv.
 nk_status tc_conv(const TcConv& c, const nk_schedule& s, void* ws, size_t ws_bytes, cudaStream_t st);
@@ -253,13 +255,14 @@ bool tc_conv_schedule_valid(const ConvGeom& g, int F, const nk_schedule& s, int 
 // 64-channel block of the window, read by every tap) selects it; tile_m =
 // 128 * chains (1, 2, 4), tile_n 64 / 128 / 256 with chains * tile_n <= 256,
 // stages = window slots (1..4), cluster 1, split_k 1.
-bool halo_schedule(const ConvGeom& g, const nk_schedule& s);
-bool halo_schedule_valid(const ConvGeom& g, int F, const nk_schedule& s);
+// E4M3 operands (kind TC_FP8): stacked kernel rows only, tile_k = 128 * KH.
+bool halo_schedule(const ConvGeom& g, const nk_schedule& s, int kind = TC_BF16);
+bool halo_schedule_valid(const ConvGeom& g, int F, const nk_schedule& s, int kind = TC_BF16);
 nk_status tc_halo_conv(const TcConv& c, const nk_schedule& s, cudaStream_t st);
-nk_schedule tc_halo_default_schedule(const ConvGeom& g, int F, int sms, bool* ok);
+nk_schedule tc_halo_default_schedule(const ConvGeom& g, int F, int sms, bool* ok, int kind = TC_BF16);
 // Window tile of a window schedule: P, Q, R, NB, WR, rows, slot_rows, stk,
 // tiles, chains (false when the schedule is not a legal window schedule).
-bool halo_tile_info(const ConvGeom& g, int F, const nk_schedule& s, int32_t out[10]);
+bool halo_tile_info(const ConvGeom& g, int F, const nk_schedule& s, int32_t out[10], int kind = TC_BF16);
 uint32_t halo_read_and_clear_errors();
 size_t tc_gemm_ws(const TcGemm& g, const nk_schedule& s);
 // Fills unset fields of `s` with the built-in choice for this problem.

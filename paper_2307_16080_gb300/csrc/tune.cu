@@ -146,6 +146,15 @@ std::vector<nk_schedule> enumerate(const nk_problem* p) {
       if (p->kh >= 2 && p->kw >= 2 && halo_schedule_valid(g, p->f, s)) out.push_back(s);
     }
   }
+  // E4M3 stride-1 convolutions: the stacked window kernel (tile_k = 128 * KH)
+  if (p->op == NK_OP_CONV2D && p->kh >= 2 && p->kw >= 2 && p->stride == 1 && kind == TC_FP8) {
+    const ConvGeom g = geom_of(p);
+    for (int tm : {128, 256})
+      for (int st = 1; st <= 8; ++st) {
+        nk_schedule s{tm, 64, 128 * p->kh, 1, st, 1};
+        if (halo_schedule_valid(g, p->f, s, TC_FP8)) out.push_back(s);
+      }
+  }
   return out;
 }
 
@@ -217,6 +226,7 @@ struct Runner {
       op_bytes = ib + wb;
       total = op_bytes + (size_t)M * N * 4 + split_bytes + 4096;
       c.kind = kind; c.g = geo; c.F = p->f; c.ldw = cp; c.sW_f = (int64_t)p->kh * p->kw * cp;
+      c.alpha = 1.f;
       c.sI_w = cp; c.sI_h = (int64_t)p->w * cp; c.sI_n = (int64_t)p->h * p->w * cp;
     }
   }
@@ -335,8 +345,10 @@ nk_schedule matmul_default_schedule(int kind, int M, int N, int K, int sms) {
 // in steps of about 2 us, so each timed sample is a graph of `inner`
 // back-to-back calls (inner chosen so a sample lasts about 400 us) between
 // two events, and the samples are queued behind hold_kernel: what is timed is
-// the kernels alone, not the host work of a call.
-nk_status time_device(const RunFn& run, int reps, float* ms) {
+// the kernels alone, not the host work of a call.  `cycle`: consecutive calls
+// of `run` work on `cycle` different buffer sets in turn, so `inner` is a
+// multiple of it (every sample visits every set).
+nk_status time_device(const RunFn& run, int reps, float* ms, int cycle) {
   cudaStream_t st = timing_stream();
   if (!st) return fail(NK_ERR_CUDA, "no timing stream");
   nk_status status = NK_OK;
@@ -364,7 +376,9 @@ nk_status time_device(const RunFn& run, int reps, float* ms) {
   if (status != NK_OK) return status;
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize(tune)");
   rough = std::max(rough / 8.f, 0.002f);
-  const int inner = std::max(1, std::min(64, (int)std::ceil(0.4f / rough)));
+  cycle = std::max(1, cycle);
+  int inner = std::max(1, std::min(64, (int)std::ceil(0.4f / rough)));
+  inner = (std::max(inner, cycle) + cycle - 1) / cycle * cycle;
   cudaGraphExec_t exec = nullptr;
   if ((status = capture_runs(run, inner, st, &exec)) != NK_OK) return status;
 
@@ -400,18 +414,37 @@ nk_status time_device(const RunFn& run, int reps, float* ms) {
 
 namespace {
 
-// Device time of one schedule on synthetic operands of the problem's shape.
+// Buffer sets a timing cycles through: enough that together they hold twice
+// the L2, so that every timed call finds its operands evicted by the calls
+// since its set was last used (at most 128 sets; problems larger than the
+// L2 use one).
+int rotation_sets(size_t set_bytes) {
+  int dev = 0, l2 = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess ||
+      l2 <= 0)
+    l2 = 126 << 20;
+  const size_t sets = (2 * (size_t)l2 + set_bytes - 1) / set_bytes;
+  return (int)std::min<size_t>(std::max<size_t>(sets, 1), 128);
+}
+
+// Device time of one schedule on synthetic operands of the problem's shape,
+// cold in L2: back-to-back calls rotate over rotation_sets() copies of the
+// operands, outputs and workspace.
 nk_status time_one(const nk_problem* p, const nk_schedule& s, int reps, float* ms, cudaStream_t user) {
   Runner r(p, s);
+  const size_t per = (r.padded_total() + 255) / 256 * 256;
+  const int sets = rotation_sets(per);
   void* buf = nullptr;
-  nk_status status = scratch(r.padded_total(), &buf);
+  nk_status status = scratch(per * sets, &buf);
   if (status != NK_OK) return status;
-  r.bind(static_cast<char*>(buf));
-  if ((status = fill(r.op_bytes + 1024)) != NK_OK) return status;
+  std::vector<Runner> rs(sets, r);
+  for (int i = 0; i < sets; ++i) rs[i].bind(static_cast<char*>(buf) + per * i);
+  if ((status = fill(per * sets)) != NK_OK) return status;
   cudaError_t e = user ? cudaStreamSynchronize(user) : cudaSuccess;
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
-  return time_device([&](cudaStream_t st) { return r.run(s, st); }, reps, ms);
+  int next = 0;
+  return time_device([&](cudaStream_t st) { return rs[next++ % sets].run(s, st); }, reps, ms, sets);
 }
 
 // (1+1) evolution strategy on the schedule grid.  Coordinates: tile_m,
@@ -616,7 +649,7 @@ nk_status nk_grouped_tune(int32_t G, const nk_gemm_group* groups, int32_t precis
     nk_grouped_plan* plan = nullptr;
     nk_status r = nk_grouped_plan_create(G, gs.data(), precision, s, &plan);
     if (r != NK_OK) return r;
-    r = time_device([&](cudaStream_t cs) { return nk_grouped_plan_run(plan, cs); }, reps, ms);
+    r = time_device([&](cudaStream_t cs) { return nk_grouped_plan_run(plan, cs); }, reps, ms, 1);
     nk_grouped_plan_destroy(plan);
     return r;
   };
@@ -669,7 +702,7 @@ nk_status nk_conv2d_grouped_tune(int32_t G, const nk_conv_group* groups, int32_t
     nk_grouped_plan* plan = nullptr;
     nk_status r = nk_conv2d_grouped_plan_create(G, gs.data(), s, &plan);
     if (r != NK_OK) return r;
-    r = time_device([&](cudaStream_t cs) { return nk_grouped_plan_run(plan, cs); }, reps, ms);
+    r = time_device([&](cudaStream_t cs) { return nk_grouped_plan_run(plan, cs); }, reps, ms, 1);
     nk_grouped_plan_destroy(plan);
     return r;
   };

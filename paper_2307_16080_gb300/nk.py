@@ -95,6 +95,8 @@ SIGNATURES = {
     "nk_conv2d_workspace_size": (_I32, [_PT, _PT, _PT, ctypes.POINTER(_I64), ctypes.POINTER(_I64),
                                         ctypes.POINTER(_I64), _I32, _PS, ctypes.POINTER(_SZ)]),
     "nk_conv2d_pack_weights": (_I32, [_PT, _P, _I64, _P]),
+    "nk_conv2d_pack_weights_fp8": (_I32, [_PT, _P, _I64, _P, _P, _SZ, _P]),
+    "nk_conv2d_pack_weights_fp8_workspace_size": (_SZ, []),
     "nk_conv2d_nchw_fchw": (_I32, [_PT, _PT, _PT, ctypes.POINTER(_I64), ctypes.POINTER(_I64),
                                    ctypes.POINTER(_I64), _PE, _P]),
     "nk_amax": (_I32, [_P, _I64, _P, _P, _SZ, _P]),
@@ -261,14 +263,16 @@ def nk_conv2d_workspace_size(I, W, O, stride=(1, 1), dilation=(1, 1), pad=(0, 0,
 
 def nk_conv2d_nhwc_hwcf(I, W, O, stride=(1, 1), dilation=(1, 1), pad=(0, 0, 0, 0), precision="f32",
                         bias=None, relu=False, accumulate=False, schedule=None, ws=None, stream=None,
-                        ew=None, pro_i=None, pro_w=None):
+                        ew=None, pro_i=None, pro_w=None, scale_i=1.0, scale_w=1.0):
     """O = ew(ReLU?(accumulate*O + conv(pro_i(I), pro_w(W)) + bias)); the
-    programs are step lists (make_ew_program), the zero padding stays 0."""
+    programs are step lists (make_ew_program), the zero padding stays 0.
+    scale_i, scale_w: the quantisation scales of E4M3 operands the caller
+    quantised (read only for those)."""
     ti, tw, to = as_nk_tensor(I), as_nk_tensor(W), as_nk_tensor(O)
     st, dl, pd = _conv_args(stride, dilation, pad)
     if ws is None:
         ws = workspace(nk_conv2d_workspace_size(I, W, O, stride, dilation, pad, precision, schedule), O.device)
-    e = _epi(bias, relu, accumulate, 1.0, 1.0, ew, pro_i, pro_w)
+    e = _epi(bias, relu, accumulate, scale_i, scale_w, ew, pro_i, pro_w)
     _check(lib().nk_conv2d_nhwc_hwcf(ctypes.byref(ti), ctypes.byref(tw), ctypes.byref(to), st, dl, pd,
                                      PREC[precision], ctypes.byref(e), _sched(schedule),
                                      ws.data_ptr() if ws is not None else None,
@@ -286,6 +290,35 @@ def nk_conv2d_pack_weights(W, ldw=None, stream=None) -> torch.Tensor:
     tw = as_nk_tensor(W)
     _check(lib().nk_conv2d_pack_weights(ctypes.byref(tw), buf.data_ptr(), ldw, _stream(stream)))
     return buf.as_strided((KH, KW, C, F), (KW * ldw, ldw, 1, KH * KW * ldw))
+
+
+def nk_conv2d_pack_weights_fp8(W, ldw=None, stream=None):
+    """FP32 HWCF W [KH,KW,C,F] -> (E4M3 packed weights as a [KH,KW,C,F]
+    strided uint8 view, the device scale s_w as a 1-element FP32 tensor)."""
+    KH, KW, C, F = W.shape
+    ldw = (C + 15) // 16 * 16 if ldw is None else int(ldw)
+    buf = torch.empty(F * KH * KW * ldw, dtype=torch.uint8, device=W.device)
+    scale = torch.empty(1, device=W.device)
+    ws = workspace(lib().nk_conv2d_pack_weights_fp8_workspace_size(), W.device)
+    tw = as_nk_tensor(W)
+    _check(lib().nk_conv2d_pack_weights_fp8(ctypes.byref(tw), buf.data_ptr(), ldw, scale.data_ptr(), ws.data_ptr(),
+                                            ws.numel(), _stream(stream)))
+    return buf.as_strided((KH, KW, C, F), (KW * ldw, ldw, 1, KH * KW * ldw)), scale
+
+
+def quantize_nhwc_fp8(I, stream=None):
+    """FP32 NHWC I [N,H,W,C] -> (E4M3 [N,H,W,C] uint8 view with channel
+    rows padded to 16 bytes, the device scale s_i = 448/amax(|I|)): nk_amax,
+    then nk_cast_fp8 of the [N*H*W, C] view."""
+    N, H, Wd, C = I.shape
+    cp = (C + 15) // 16 * 16
+    buf = torch.zeros(N * H * Wd * cp, dtype=torch.uint8, device=I.device)
+    amax = torch.empty(1, device=I.device)
+    scale = torch.empty(1, device=I.device)
+    flat = I.reshape(N * H * Wd, C)
+    nk_amax(flat, amax, stream=stream)
+    nk_cast_fp8(flat, amax, buf.view(N * H * Wd, cp), scale_out=scale, stream=stream)
+    return buf.as_strided((N, H, Wd, C), (H * Wd * cp, Wd * cp, cp, 1)), scale
 
 
 def nk_conv2d_nchw_fchw(I, K, O, stride=(1, 1), dilation=(1, 1), pad=(0, 0, 0, 0), bias=None, relu=False,

@@ -62,6 +62,13 @@ def lib():
     return L
 
 
+def timing_method() -> str:
+    """How nk_time_schedule / nk_tune time a schedule (tune.cu)."""
+    return ("device time of CUDA-graph replays of back-to-back calls behind a hold kernel, median of reps; "
+            "the calls rotate over as many copies of operands, outputs and workspace as hold twice the L2 "
+            "(at most 128), so each call starts with its operands out of L2")
+
+
 def matmul_problem(M, N, K, precision="bf16") -> nk_problem:
     return nk_problem(NK_OP_MATMUL, nk.PREC[precision], M, N, K, 0, 0, 0, 0, 0, 0, 0, 0, 0)
 

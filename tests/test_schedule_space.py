@@ -40,7 +40,9 @@ def test_stacked_schedules_for_deep_layers():
 def test_default_schedules_for_the_resnet_stack(batch):
     """Built-in choice per layer: stacked kernel rows for the stride-1 3x3
     layers (except batch-1 layers with C > 128, whose few tiles go to the
-    per-tap kernel with split-K), 128 x 64 per-tap tiles everywhere else."""
+    per-tap kernel with split-K) -- two accumulator buffers on one CTA per
+    SM once there are 4 tiles per SM, else one buffer on two CTAs -- and
+    128 x 64 per-tap tiles everywhere else."""
     from paper_2307_16080_gb300 import synth
     for L in synth.resnet_stack(batch):
         p = nt.conv_problem(L["N"], L["H"], L["W"], L["C"], L["F"], L["KH"], L["KW"], L["stride"], L["pad"])
@@ -48,7 +50,10 @@ def test_default_schedules_for_the_resnet_stack(batch):
         assert s in nt.nk_enumerate_schedules(p), (L, s)
         stackable = L["stride"] == 1 and L["KH"] == 3
         if stackable and not (batch == 1 and L["C"] > 128):
-            assert s[:3] == (128, 64, 192) and s[5] == 1, (L, s)
+            assert s[0] in (128, 256) and s[1:3] == (64, 192) and s[5] == 1, (L, s)
+            tiles = nt.nk_conv_window_tile(L["N"], L["H"], L["W"], L["C"], L["F"], 3, 3, (1, 1), (1, 1, 1, 1),
+                                           s)["tiles"] * ((L["F"] + 63) // 64)
+            assert (s[0] == 256) == (tiles >= 4 * 152), (L, s, tiles)
         else:
             assert s[:3] == (128, 64, 64), (L, s)
 
@@ -162,3 +167,29 @@ def test_cluster_two_is_always_a_cta_pair(prob):
             if s[3] == 2:
                 assert s[0] == 256, s
                 assert not (prob[0] == "conv" and prec == "fp8"), s
+
+
+@pytest.mark.parametrize("name", ["corpus_train.npz", "corpus_heldout.npz", "corpus_heldout2.npz"])
+def test_stored_corpora_cover_todays_schedule_space(name):
+    """Each stored corpus timed exactly the legal schedules the library
+    enumerates today for each of its problems (a change of the schedule space
+    makes the corpora stale and fails here)."""
+    import os
+    import numpy as np
+    from paper_2307_16080_gb300 import costmodel
+    path = os.path.join(costmodel.MODEL_DIR, name)
+    if not os.path.exists(path):
+        pytest.skip("no stored corpus")
+    c = costmodel.load_corpus(path)
+    for i, pr in enumerate(c["problems"]):
+        rows = np.nonzero(c["pid"] == i)[0]
+        stored = {tuple(int(v) for v in c["sched"][j]) for j in rows}
+        live = set(nt.nk_enumerate_schedules(nt.nk_problem(*[int(v) for v in pr])))
+        assert stored == live, (name, i, len(stored), len(live))
+
+
+def test_heldout2_shares_no_problem_with_training():
+    from paper_2307_16080_gb300 import costmodel
+    train = {tuple(costmodel.problem_dict(p).values()) for p in costmodel.training_problems()}
+    h2 = [tuple(costmodel.problem_dict(p).values()) for p in costmodel.heldout2_problems()]
+    assert h2 and not (set(h2) & train)
