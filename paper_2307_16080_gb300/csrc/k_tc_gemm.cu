@@ -98,6 +98,8 @@ struct TcParams {
   int c_tma;
   EwProg ew;                    // fused elementwise program (offsets from C), single launches
   int out_bf16;                 // single convolutions: C holds BF16 (RNE of the FP32 result)
+  int c_vec32;                  // single convolutions: 32-byte aligned output rows
+  int resid;                    // single convolutions: ew is {ADD t, RELU}, t with 32-byte aligned rows
 };
 
 // Epilogue staging: one 32 x 32 FP32 box (4 KB, 128B-swizzled) per epilogue warp.
@@ -551,6 +553,35 @@ __global__ void __launch_bounds__(WIDE ? 320 : 192, 1) tc_gemm_kernel(const __gr
           continue;
         }
         if constexpr (CONV && !GROUPED) {
+          if (p.c_vec32 && t.beta == 0.f && col0 + 32 <= t.N && (p.ew.n == 0 || p.resid)) {
+            // Full 32-column segment, no accumulate, and no program or the
+            // residual program ADD t, RELU (inline, the interpreter's FP32
+            // steps): one code path for FP32 and BF16 outputs.
+            const int64_t off = (int64_t)row * t.ldc + col0;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              float x = alpha * v[j];
+              if (t.bias) x += __ldg(t.bias + col0 + j);
+              if (t.relu) x = (x > 0.f || x != x) ? x : 0.f;
+              v[j] = x;
+            }
+            if (p.resid) {
+              const float4* tr = reinterpret_cast<const float4*>(p.ew.t[0] + off);
+#pragma unroll
+              for (int j = 0; j < 32; j += 4) {
+                const float4 r4 = __ldg(tr + j / 4);
+                const float rv[4] = {r4.x, r4.y, r4.z, r4.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                  const float x = __fadd_rn(v[j + e], rv[e]);
+                  v[j + e] = (x > 0.f || x != x) ? x : 0.f;
+                }
+              }
+            }
+            if (p.out_bf16) store32_bf16_v8(reinterpret_cast<__nv_bfloat16*>(t.C) + off, v);
+            else store32_f32_v8(t.C + off, v);
+            continue;
+          }
           if (p.out_bf16) {
             // BF16 output: the FP32 epilogue, then one RNE rounding per value
             __nv_bfloat16* dh = reinterpret_cast<__nv_bfloat16*>(t.C) + (int64_t)row * t.ldc + col0;
@@ -1097,6 +1128,9 @@ nk_status tc_conv(const TcConv& c, const nk_schedule& s, void* ws, size_t ws_byt
   p.ew = c.ew;
   p.budget = wait_budget();
   p.out_bf16 = c.out_bf16;
+  p.c_vec32 = (splits == 1 && (reinterpret_cast<uintptr_t>(c.O) & 31) == 0 && c.F % (c.out_bf16 ? 16 : 8) == 0) ? 1 : 0;
+  p.resid = (c.ew.n == 2 && c.ew.op[0] == NK_EW_ADD && c.ew.op[1] == NK_EW_RELU &&
+             (reinterpret_cast<uintptr_t>(c.ew.t[0]) & 31) == 0 && c.F % 8 == 0) ? 1 : 0;
   // vector stores: 16-byte aligned rows (FP32: F % 4, BF16: F % 8) and partials
   p.c_vec = ((reinterpret_cast<uintptr_t>(c.O) & 15) == 0 && c.F % (c.out_bf16 ? 8 : 4) == 0 &&
              (splits == 1 || (reinterpret_cast<uintptr_t>(ws) & 15) == 0)) ? 1 : 0;

@@ -105,6 +105,7 @@ struct HaloParams {
   float beta;
   int c_vec;             // 16-byte aligned output rows
   int c_vec32;           // 32-byte aligned output rows (one-sector stores)
+  int resid;             // ew is the residual program {ADD t, RELU}, t with 32-byte aligned rows
   int64_t budget;
   EwProg ew;             // fused elementwise program (offsets from O)
   int out_bf16;          // O holds BF16 (RNE of the FP32 epilogue result)
@@ -378,6 +379,34 @@ __global__ void __launch_bounds__(DB ? kThreadsDB : kThreads, 1) halo_conv_kerne
           }
           const int col0 = tn * p.bn + c0;
           if (!row_ok || col0 >= p.F) continue;
+          if (p.c_vec32 && p.beta == 0.f && col0 + 32 <= p.F && (p.ew.n == 0 || p.resid)) {
+            // Full 32-column segment, no accumulate, and no program or the
+            // residual program ADD t, RELU (inline, same FP32 steps as the
+            // interpreter): one code path for FP32 and BF16 outputs.
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              float xv = v[j];
+              if (p.bias) xv += __ldg(p.bias + col0 + j);
+              if (p.relu) xv = (xv > 0.f || xv != xv) ? xv : 0.f;
+              v[j] = xv;
+            }
+            if (p.resid) {
+              const float4* tr = reinterpret_cast<const float4*>(p.ew.t[0] + orow_off + col0);
+#pragma unroll
+              for (int j = 0; j < 32; j += 4) {
+                const float4 r4 = __ldg(tr + j / 4);
+                const float rv[4] = {r4.x, r4.y, r4.z, r4.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                  const float xv = __fadd_rn(v[j + e], rv[e]);
+                  v[j + e] = (xv > 0.f || xv != xv) ? xv : 0.f;
+                }
+              }
+            }
+            if (p.out_bf16) store32_bf16_v8(reinterpret_cast<__nv_bfloat16*>(p.O) + orow_off + col0, v);
+            else store32_f32_v8(orow + col0, v);
+            continue;
+          }
           if (p.out_bf16) {
             // BF16 output: the FP32 epilogue, then one RNE rounding per value
             __nv_bfloat16* dh = reinterpret_cast<__nv_bfloat16*>(p.O) + orow_off + col0;
@@ -826,6 +855,8 @@ nk_status tc_halo_conv(const TcConv& c, const nk_schedule& s, cudaStream_t st) {
   p.out_bf16 = c.out_bf16;
   p.c_vec = ((reinterpret_cast<uintptr_t>(c.O) & 15) == 0 && c.F % (c.out_bf16 ? 8 : 4) == 0) ? 1 : 0;
   p.c_vec32 = ((reinterpret_cast<uintptr_t>(c.O) & 31) == 0 && c.F % (c.out_bf16 ? 16 : 8) == 0) ? 1 : 0;
+  p.resid = (c.ew.n == 2 && c.ew.op[0] == NK_EW_ADD && c.ew.op[1] == NK_EW_RELU &&
+             (reinterpret_cast<uintptr_t>(c.ew.t[0]) & 31) == 0 && c.F % 8 == 0) ? 1 : 0;
   p.budget = wait_budget();
   p.alpha = c.alpha;
   p.scale_i = c.scale_i;
