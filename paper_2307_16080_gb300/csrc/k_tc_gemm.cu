@@ -234,8 +234,14 @@ __device__ __forceinline__ int conv_row(const ConvTile& c, int tm, int r) {
 // MCH > 1 (tall tile, one CTA): MCH stacked 128-row tiles of A share one B
 // tile, each with its own accumulator chain, so narrow problems (N = 64, 128)
 // keep several independent MMA chains in flight.
-template <int KIND, int CL, bool GROUPED, bool CONV = false, bool PAIR = false, bool WIDE = false, int MCH = 1>
-__global__ void __launch_bounds__(WIDE ? 320 : 192, 1) tc_gemm_kernel(const __grid_constant__ TcParams p) {
+//
+// EP8 (grouped launches with one CTA per SM): eight epilogue warps, two per
+// TMEM lane quarter, each draining half of a tile's columns -- the
+// epilogue of a 128 x 256 tile would otherwise outlast the next tile's MMAs.
+template <int KIND, int CL, bool GROUPED, bool CONV = false, bool PAIR = false, bool WIDE = false, int MCH = 1,
+          bool EP8 = false>
+__global__ void __launch_bounds__((WIDE || EP8) ? 320 : 192, 1) tc_gemm_kernel(const __grid_constant__ TcParams p) {
+  static_assert(!EP8 || (GROUPED && !WIDE && MCH == 1 && KIND != TC_BF16X3), "eight epilogue warps: grouped tiles");
   static_assert(PAIR == (CL == 2), "a cluster of two is a CTA pair, and a CTA pair is a cluster of two");
   static_assert(!WIDE || (PAIR && KIND != TC_BF16X3 && !GROUPED), "wide tiles are pair tiles");
   static_assert(MCH == 1 || (!PAIR && !GROUPED && KIND != TC_BF16X3 && CL == 1), "tall tiles: one CTA");
@@ -286,7 +292,7 @@ __global__ void __launch_bounds__(WIDE ? 320 : 192, 1) tc_gemm_kernel(const __gr
     }
     for (int b = 0; b < 2; ++b) {
       ptx::mbar_init(tfull_bar(b), 1);
-      ptx::mbar_init(tempty_bar(b), WIDE ? 16 : PAIR ? 8 : 4);   // every epilogue warp of the pair
+      ptx::mbar_init(tempty_bar(b), (WIDE || (PAIR && EP8)) ? 16 : (PAIR || EP8) ? 8 : 4);   // every epilogue warp
     }
     ptx::mbar_init(drain_bar, 1);
     *abort_flag = 0;
@@ -492,8 +498,8 @@ __global__ void __launch_bounds__(WIDE ? 320 : 192, 1) tc_gemm_kernel(const __gr
       const int row = CONV ? conv_row(*t.cv, tmc, q * 32 + lane) : tmc * kBM + q * 32 + lane;
       const bool row_ok = CONV ? row >= 0 : row < t.M;
       // a wide tile has two warps per lane quarter, each draining one chain's 256 columns
-      const int c_begin = WIDE ? ((warp - 2) / 4) * 256 : 0;
-      const int c_end = WIDE ? c_begin + 256 : p.bn;
+      const int c_begin = WIDE ? ((warp - 2) / 4) * 256 : EP8 ? ((warp - 2) / 4) * (p.bn / 2) : 0;
+      const int c_end = WIDE ? c_begin + 256 : EP8 ? c_begin + p.bn / 2 : p.bn;
       for (int c0 = c_begin; c0 < c_end; c0 += 32) {
         float v[32];
         const uint32_t ta =
@@ -609,6 +615,18 @@ __global__ void __launch_bounds__(WIDE ? 320 : 192, 1) tc_gemm_kernel(const __gr
         float* dst = t.C + (int64_t)row * t.ldc + col0;
         const float bm = (t.bias && p.bias_on_m) ? __ldg(t.bias + row) : 0.f;
         const float beta = t.beta;
+        if (!CONV && p.c_vec32 && beta == 0.f && col0 + 32 <= t.N && p.ew.n == 0) {
+          // full 32-column segment of 32-byte aligned rows: 32-byte stores
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            float x = alpha * v[j];
+            if (t.bias) x += p.bias_on_m ? bm : __ldg(t.bias + col0 + j);
+            if (t.relu) x = (x > 0.f || x != x) ? x : 0.f;
+            v[j] = x;
+          }
+          store32_f32_v8(dst, v);
+          continue;
+        }
         if (p.ew.n) {
           // A program runs out of line.  The segment goes through a local
           // buffer: the program reads its operands (which may alias C) before
@@ -731,9 +749,9 @@ int smem_of(int kind, const nk_schedule& s) {
 }
 
 template <int KIND, int CL, bool GROUPED = false, bool CONV = false, bool PAIR = false, bool WIDE = false,
-          int MCH = 1>
+          int MCH = 1, bool EP8 = false>
 nk_status launch(const TcParams& p, int grid, int smem, cudaStream_t st) {
-  auto kern = tc_gemm_kernel<KIND, CL, GROUPED, CONV, PAIR, WIDE, MCH>;
+  auto kern = tc_gemm_kernel<KIND, CL, GROUPED, CONV, PAIR, WIDE, MCH, EP8>;
   // the attribute is set once per device and size (it stays set on the function)
   static int set_bytes[64] = {};
   int dev = 0;
@@ -743,7 +761,7 @@ nk_status launch(const TcParams& p, int grid, int smem, cudaStream_t st) {
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(tc_gemm_kernel)");
     if (dev >= 0 && dev < 64) set_bytes[dev] = smem;
   }
-  const cudaError_t e = nk::launch_k(kern, dim3(grid), dim3(WIDE ? 320 : kThreads), smem, st, CL, p);
+  const cudaError_t e = nk::launch_k(kern, dim3(grid), dim3((WIDE || EP8) ? 320 : kThreads), smem, st, CL, p);
   if (e != cudaSuccess) return cuda_fail(e, "launch tc_gemm_kernel");
   return check_launch("tc_gemm_kernel");
 }
@@ -877,6 +895,7 @@ nk_status tc_gemm(const TcGemm& g, const nk_schedule& s, void* ws, size_t ws_byt
   const bool cvec = ((reinterpret_cast<uintptr_t>(g.C) & 15) == 0) && (g.ldc % 4 == 0) &&
                     (splits == 1 || (g.N % 4 == 0 && (reinterpret_cast<uintptr_t>(ws) & 15) == 0));
   p.c_vec = cvec ? 1 : 0;
+  p.c_vec32 = (splits == 1 && (reinterpret_cast<uintptr_t>(g.C) & 31) == 0 && g.ldc % 8 == 0) ? 1 : 0;
   // TMA-store epilogue: plain overwrite of a 16-byte aligned C in one K slice.
   p.c_tma = 0;
   if (mch == 1 && splits == 1 && g.beta == 0.f && g.ew.n == 0 && (reinterpret_cast<uintptr_t>(g.C) & 15) == 0 &&
@@ -1180,6 +1199,7 @@ struct nk_grouped_plan {
   void* dev = nullptr;     // device table (owned when built by nk_grouped_plan_create)
   bool owned = false;
   bool pair = false;       // 256-row tiles on CTA pairs (cta_group::2)
+  bool ep8 = false;        // GEMM groups on one CTA per SM: eight epilogue warps
   bool conv = false;       // groups are convolutions (implicit GEMM, per-tap loads)
   int units = 0;
   int grid = 0;
@@ -1189,6 +1209,17 @@ struct nk_grouped_plan {
 
 namespace nk {
 namespace {
+
+// One persistent launch of a grouped GEMM plan: CTA pairs or one CTA per
+// tile, with eight epilogue warps when a CTA has the SM to itself.
+nk_status run_grouped_gemm(const nk_grouped_plan& plan, cudaStream_t st) {
+  if (plan.pair) {
+    if (plan.ep8) return launch<TC_BF16, 2, true, false, true, false, 1, true>(plan.p, plan.grid, plan.smem, st);
+    return launch<TC_BF16, 2, true, false, true>(plan.p, plan.grid, plan.smem, st);
+  }
+  if (plan.ep8) return launch<TC_BF16, 1, true, false, false, false, 1, true>(plan.p, plan.grid, plan.smem, st);
+  return launch<TC_BF16, 1, true>(plan.p, plan.grid, plan.smem, st);
+}
 
 size_t grouped_bytes(int G) {
   size_t maps = (size_t)G * 2 * sizeof(CUtensorMap);
@@ -1259,7 +1290,7 @@ nk_status build_grouped(int G, const nk_gemm_group* groups, int precision, const
   const size_t off_start = off_desc + ((size_t)G * sizeof(GroupDesc) + 127) / 128 * 128;
   GroupDesc* descs = reinterpret_cast<GroupDesc*>(host.data() + off_desc);
   int* starts = reinterpret_cast<int*>(host.data() + off_start);
-  bool cvec = true;
+  bool cvec = true, cvec32 = true;
   int64_t total = 0;
   for (int i = 0; i < G; ++i) {
     nk_gemm_group q = groups[order[i]];
@@ -1279,6 +1310,7 @@ nk_status build_grouped(int G, const nk_gemm_group* groups, int precision, const
     total += (int64_t)((q.M + rows - 1) / rows) * d.tiles_n;
     if (total > INT32_MAX) return fail(NK_ERR_UNSUPPORTED, "too many tiles");
     cvec = cvec && ((reinterpret_cast<uintptr_t>(q.C) & 15) == 0) && (q.ldc % 4 == 0);
+    cvec32 = cvec32 && ((reinterpret_cast<uintptr_t>(q.C) & 31) == 0) && (q.ldc % 8 == 0);
   }
   starts[G] = (int)total;
   TcParams& p = plan.p;
@@ -1290,6 +1322,7 @@ nk_status build_grouped(int G, const nk_gemm_group* groups, int precision, const
   p.alpha = 1.f;
   p.budget = wait_budget();
   p.c_vec = cvec ? 1 : 0;
+  p.c_vec32 = cvec32 ? 1 : 0;
   p.G = G;
   uint8_t* db = static_cast<uint8_t*>(dev_base);
   p.gmaps = reinterpret_cast<const CUtensorMap*>(db);
@@ -1297,6 +1330,7 @@ nk_status build_grouped(int G, const nk_gemm_group* groups, int precision, const
   p.tile_start = reinterpret_cast<const int*>(db + off_start);
   plan.units = (int)total;
   plan.pair = pair;
+  plan.ep8 = ctas_per_sm(TC_BF16, s) == 1;
   plan.smem = smem_of(TC_BF16, s);
   const int CL = pair ? 2 : 1;
   int grid = sms * ctas_per_sm(TC_BF16, s) / CL * CL;
@@ -1492,9 +1526,7 @@ nk_status nk_grouped_plan_run(const nk_grouped_plan* plan, void* stream) {
   if (plan->units == 0) return NK_OK;
   if (plan->conv)
     return launch<TC_BF16, 1, true, true>(plan->p, plan->grid, plan->smem, static_cast<cudaStream_t>(stream));
-  if (plan->pair)
-    return launch<TC_BF16, 2, true, false, true>(plan->p, plan->grid, plan->smem, static_cast<cudaStream_t>(stream));
-  return launch<TC_BF16, 1, true>(plan->p, plan->grid, plan->smem, static_cast<cudaStream_t>(stream));
+  return run_grouped_gemm(*plan, static_cast<cudaStream_t>(stream));
 }
 
 nk_status nk_grouped_plan_destroy(nk_grouped_plan* plan) {
@@ -1520,8 +1552,7 @@ nk_status nk_batch_matmul_grouped(int32_t G, const nk_gemm_group* groups, int32_
   cudaError_t e = cudaMemcpyAsync(ws, host.data(), bytes, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(grouped table)");
   // a pageable source is staged before cudaMemcpyAsync returns, so `host` may go
-  if (plan.pair) return launch<TC_BF16, 2, true, false, true>(plan.p, plan.grid, plan.smem, st);
-  return launch<TC_BF16, 1, true>(plan.p, plan.grid, plan.smem, st);
+  return run_grouped_gemm(plan, st);
 }
 
 }  // extern "C"
