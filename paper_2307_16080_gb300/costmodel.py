@@ -87,7 +87,7 @@ def heldout_problems():
 
 def heldout2_problems(seed: int = synth.SEED_COSTMODEL + 100):
     """A second held-out set, fitted by nothing: 20 conv layers of a stack
-    with other channel counts (48 -> 384), spatial sizes (60 -> 10) and a
+    with other channel counts (48 -> 384), spatial sizes (60 -> 8) and a
     batch of 4 and 16, and 20 BF16 matmuls drawn like the grouped workload
     (M, N, K log-uniform in [32, 2048], multiples of 16).  Problems that
     coincide with a training problem are dropped."""
