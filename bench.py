@@ -837,10 +837,11 @@ def _case_emit(name, ms, bytes_=None, flop=None, **kw):
     print(json.dumps(out), flush=True)
 
 
-def run_case(name, reps):
+def run_case(name, reps, schedule=None):
     """One kernel family alone, on a fixed workload (device times of CUDA
     graph replays; the inputs of each are larger than L2, or the timing is
-    the flushed one)."""
+    the flushed one).  schedule: a fixed tile for the grouped case instead
+    of its tuner (so a profiler sees the measured kernel first)."""
     import torch
 
     import paper_2307_16080_gb300.nk as nk
@@ -917,7 +918,7 @@ def run_case(name, reps):
         c = [torch.empty(M, N, device="cuda") for (M, N, K) in shapes]
         groups, G = nk.make_groups(a, bt, c)
         from paper_2307_16080_gb300 import nk_tune as nt
-        best, _ = nt.nk_grouped_tune(groups, G, reps=3)
+        best = schedule if schedule is not None else nt.nk_grouped_tune(groups, G, reps=3)[0]
         plan = nk.nk_grouped_plan_create(groups, G, schedule=best)
         f = float(sum(2.0 * M * N * K for (M, N, K) in shapes))
         _case_emit("grouped 512 bf16 gemms", flushed_time(torch, lambda: nk.nk_grouped_plan_run(plan), 8), flop=f,
@@ -962,6 +963,8 @@ def main():
     ap.add_argument("--ref-rows", type=int, default=128)
     ap.add_argument("--case", choices=CASES, help="time one kernel family alone and exit")
     ap.add_argument("--reps", type=int, default=20, help="replays per --case timing")
+    ap.add_argument("--schedule", default=None,
+                    help="--case grouped: fixed tile_m,tile_n,tile_k,cluster,stages,split_k instead of tuning")
     ap.add_argument("--cpu-legs", type=float, default=None, help=argparse.SUPPRESS)
     ap.add_argument("--no-sweep", action="store_true", help="skip the FP8/BF16x3/FP32 sweep")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
@@ -981,7 +984,8 @@ def main():
         run_reference(args, rank)
         return
     if args.case:
-        run_case(args.case, args.reps)
+        run_case(args.case, args.reps,
+                 tuple(int(v) for v in args.schedule.split(",")) if args.schedule else None)
         return
 
     import torch

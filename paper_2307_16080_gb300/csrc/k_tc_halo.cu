@@ -141,11 +141,17 @@ __device__ __forceinline__ int tap_offset(const HaloTile& t, int tap) {
 // F8: E4M3 operands (stacked rows only): 128-channel K blocks, the same
 // 128-byte rows and 32-byte K steps (tcgen05.mma kind::f8f6f4, K = 32), the
 // result dequantised by 1/(s_i s_w) in the epilogue.
-template <int MCH, bool STK, bool DB = false, bool F8 = false>
+//
+// RES: the output program is the residual ADD t, RELU, applied inline in the
+// fast store path.  A separate instantiation, because the residual loads
+// raised the double-buffered kernel to spilling registers, which slowed
+// every layer without a residual by ~15 %.
+template <int MCH, bool STK, bool DB = false, bool F8 = false, bool RES = false>
 __global__ void __launch_bounds__(DB ? kThreadsDB : kThreads, 1) halo_conv_kernel(const __grid_constant__ HaloParams p) {
   static_assert(!STK || MCH == 1, "stacked kernel rows use one chain");
   static_assert(!DB || STK, "the double-buffered variant is a stacked-row kernel");
   static_assert(!F8 || STK, "E4M3 window convolutions stack kernel rows");
+  static_assert(!RES || (STK && !F8), "the inline residual serves the BF16 stacked kernels");
   constexpr int NACC = (STK && !DB) ? 1 : 2;   // accumulator buffers
   constexpr int EPW = DB ? 2 : 1;              // epilogue warps per TMEM lane quarter
   extern __shared__ uint8_t smem_raw[];
@@ -379,7 +385,7 @@ __global__ void __launch_bounds__(DB ? kThreadsDB : kThreads, 1) halo_conv_kerne
           }
           const int col0 = tn * p.bn + c0;
           if (!row_ok || col0 >= p.F) continue;
-          if (p.c_vec32 && p.beta == 0.f && col0 + 32 <= p.F && (p.ew.n == 0 || p.resid)) {
+          if (p.c_vec32 && p.beta == 0.f && col0 + 32 <= p.F && (RES || p.ew.n == 0)) {
             // Full 32-column segment, no accumulate, and no program or the
             // residual program ADD t, RELU (inline, same FP32 steps as the
             // interpreter): one code path for FP32 and BF16 outputs.
@@ -390,7 +396,7 @@ __global__ void __launch_bounds__(DB ? kThreadsDB : kThreads, 1) halo_conv_kerne
               if (p.relu) xv = (xv > 0.f || xv != xv) ? xv : 0.f;
               v[j] = xv;
             }
-            if (p.resid) {
+            if constexpr (RES) {
               const float4* tr = reinterpret_cast<const float4*>(p.ew.t[0] + orow_off + col0);
 #pragma unroll
               for (int j = 0; j < 32; j += 4) {
@@ -708,9 +714,9 @@ bool halo_layout(const ConvGeom& g, int F, const nk_schedule& s, HaloLayout* L, 
   return L->smem <= kMaxSmem;
 }
 
-template <int MCH, bool STK = false, bool DB = false, bool F8 = false>
+template <int MCH, bool STK = false, bool DB = false, bool F8 = false, bool RES = false>
 nk_status launch(const HaloParams& p, int grid, int smem, cudaStream_t st) {
-  auto kern = halo_conv_kernel<MCH, STK, DB, F8>;
+  auto kern = halo_conv_kernel<MCH, STK, DB, F8, RES>;
   static int set_bytes[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
@@ -869,6 +875,9 @@ nk_status tc_halo_conv(const TcConv& c, const nk_schedule& s, cudaStream_t st) {
     if (t.stk <= 1) return fail(NK_ERR_NO_SCHEDULE, "E4M3 window convolutions stack kernel rows");
     return db ? launch<1, true, true, true>(p, grid, L.smem, st) : launch<1, true, false, true>(p, grid, L.smem, st);
   }
+  if (t.stk > 1 && p.resid)
+    return db ? launch<1, true, true, false, true>(p, grid, L.smem, st)
+              : launch<1, true, false, false, true>(p, grid, L.smem, st);
   if (t.stk > 1) return db ? launch<1, true, true>(p, grid, L.smem, st) : launch<1, true>(p, grid, L.smem, st);
   switch (chains_of(g, s)) {
     case 1: return launch<1>(p, grid, L.smem, st);
