@@ -228,9 +228,12 @@ typedef struct {
   int64_t lda, ldb, ldc;
 } nk_gemm_group;
 
-/* Opaque plan: group table, per-group TMA descriptors and tile table in
- * device memory, built once on the host side and replayed by one persistent
- * launch.  Creating a plan allocates; running it does not (graph-safe).   */
+/* Opaque plan: group table, per-group TMA descriptors (A, B^T and, when
+ * every group overwrites a 16-byte aligned C with 16-byte aligned rows, C
+ * for TMA stores), tile table and the group of every tile (4 bytes per
+ * tile) in device memory, built once on the host side and replayed by one
+ * persistent launch.  Creating a plan allocates; running it does not
+ * (graph-safe).                                                           */
 typedef struct nk_grouped_plan nk_grouped_plan;
 
 /* Build a plan for G groups (host array `groups`, copied) at `precision`

@@ -77,15 +77,21 @@ def test_fp8_window_conv_writes_only_its_output(nk):
     np.testing.assert_array_equal(host(c.t), O.conv2d_nhwc_hwcf(I, W, pad=(1, 1, 1, 1)))
 
 
-def test_grouped_gemm_writes_only_its_outputs(nk):
-    shapes = [(130, 70, 96), (33, 257, 64), (256, 128, 160), (1, 16, 48)]
+# per-lane stores (rows not 16-byte multiples), and TMA stores clipped at
+# each group's ragged edges (every row a 16-byte multiple)
+GROUP_SETS = [[(130, 70, 96), (33, 257, 64), (256, 128, 160), (1, 16, 48)],
+              [(130, 72, 96), (33, 260, 64), (256, 132, 160), (1, 16, 48), (97, 300, 32)]]
+
+
+@pytest.mark.parametrize("shapes", GROUP_SETS)
+def test_grouped_gemm_writes_only_its_outputs(nk, shapes):
     As = [synth.small_ints(143, 2 * g, (M, K)) for g, (M, N, K) in enumerate(shapes)]
     Bs = [synth.small_ints(143, 2 * g + 1, (K, N)) for g, (M, N, K) in enumerate(shapes)]
     cans = [Canary((M, N)) for (M, N, K) in shapes]
     a16 = [dev(a).to(torch.bfloat16) for a in As]
     bt16 = [dev(np.ascontiguousarray(b.T)).to(torch.bfloat16) for b in Bs]
     groups, G = nk.make_groups(a16, bt16, [c.t for c in cans])
-    for sched in [None, (128, 64, 0, 1, 0, 0), (256, 128, 0, 2, 0, 0)]:
+    for sched in [None, (128, 64, 0, 1, 0, 0), (128, 256, 0, 1, 4, 0), (256, 128, 0, 2, 0, 0)]:
         plan = nk.nk_grouped_plan_create(groups, G, schedule=sched)
         nk.nk_grouped_plan_run(plan)
         nk.nk_sync_status()
