@@ -904,13 +904,30 @@ def run_case(name, reps, schedule=None):
                 nk.nk_conv2d_nhwc_hwcf(x, w, o, st, (1, 1), pd, "bf16", bias=bb, relu=True, ws=ws)
         _case_emit("resnet stack batch 8, 20 convs (built-in schedules)", flushed_time(torch, forward, 4, 3),
                    flop=flop, timing="flushed")
-    elif name == "chain8":
+    elif name in ("chain8", "chain32"):
         import paper_2307_16080_gb300.forward as fwd
-        net = fwd.ResNetStack(8, "cuda", seed=5)
-        x = torch.empty(8, 56, 56, 64, device="cuda").uniform_(0, 1).to(torch.bfloat16)
+        nb = 8 if name == "chain8" else 32
+        net = fwd.ResNetStack(nb, "cuda", seed=5)
+        x = torch.empty(nb, 56, 56, 64, device="cuda").uniform_(0, 1).to(torch.bfloat16)
         net.bind(x)
-        _case_emit("chained resnet forward batch 8 (BF16 activations)", flushed_time(torch, net.run, 4, 3),
+        _case_emit(f"chained resnet forward batch {nb} (BF16 activations)", flushed_time(torch, net.run, 4, 3),
                    flop=net.flop, timing="flushed")
+    elif name == "conv_fp8":
+        # E4M3 stacked window kernel on pre-quantised operands, 32 x 14 x 14 x 256 3x3
+        N, H, C, F = 32, 14, 256, 256
+        i32 = torch.randn(N, H, H, C, device="cuda").abs()
+        w32 = torch.randn(3, 3, C, F, device="cuda") * 0.03
+        iq, si = nk.quantize_nhwc_fp8(i32)
+        wq, sw = nk.nk_conv2d_pack_weights_fp8(w32)
+        o = torch.empty(N, H, H, F, device="cuda")
+        ws = nk.workspace(nk.nk_conv2d_workspace_size(iq, wq, o, pad=(1, 1, 1, 1), precision="fp8"))
+        s_i, s_w = float(si.item()), float(sw.item())
+        call = lambda: nk.nk_conv2d_nhwc_hwcf(iq, wq, o, pad=(1, 1, 1, 1), precision="fp8",  # noqa: E731
+                                              relu=True, ws=ws, scale_i=s_i, scale_w=s_w)
+        f = 2.0 * N * H * H * F * 9 * C
+        b = N * H * H * (C + F * 4) + 9 * C * F
+        _case_emit(f"fp8 conv {N}x{H}x{H}x{C} -> {F} 3x3, pre-quantised", flushed_time(torch, call), bytes_=b,
+                   flop=f, timing="flushed", warm_ms=graph_time(torch, call, 10, reps))
     elif name == "grouped":
         shapes = [tuple(int(v) for v in s) for s in synth.grouped_problems(512)]
         a = [torch.empty(M, K, device="cuda").uniform_(-1, 1).to(torch.bfloat16) for (M, N, K) in shapes]
@@ -948,8 +965,8 @@ def run_case(name, reps, schedule=None):
     nk.nk_sync_status()
 
 
-CASES = ("cast", "amax", "direct", "conv", "conv8", "conv_window", "conv_tap", "stack8", "chain8", "grouped",
-         "splitk", "gemm")
+CASES = ("cast", "amax", "direct", "conv", "conv8", "conv_window", "conv_tap", "conv_fp8", "stack8", "chain8",
+         "chain32", "grouped", "splitk", "gemm")
 
 
 # ------------------------------------------------------------------ main
