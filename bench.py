@@ -662,6 +662,8 @@ def resnet_report(torch, synth, dev):
         tot["schedules_timed"] = timed
         tot["tuner_timing"] = nt.timing_method()
         tot["stack_graph"] = stack_graph(torch, synth, dev, b, picks, tot["flop"])
+        tot["model_picks"] = [[int(getattr(pk, f)) for f in ("tile_m", "tile_n", "tile_k", "cluster", "stages",
+                                                             "split_k")] for pk in picks]
         out[f"batch{b}"] = tot
     nt.nk_tune_release()
     return out
@@ -714,28 +716,39 @@ def stack_graph(torch, synth, dev, batch, picks, flop):
                    "flushed: 256 MiB written before each forward, flush time subtracted"}
 
 
-def chained_forward_report(torch, nk, synth, dev):
+def chained_forward_report(torch, nk, synth, dev, picks=None):
     """The ResNet-style stack as a real forward: every 3x3 s1 layer reads the
     BF16 output its predecessor wrote (bias + ReLU fused, rounded to BF16 in
     the epilogue); each stage's stride-2 3x3 and 1x1 projection read the
     stage input, and the stage's last conv adds the projection (a fused ADD
-    of the residual) before its ReLU.  One CUDA graph per batch."""
+    of the residual) before its ReLU.  One CUDA graph per batch, with the
+    built-in schedules and, when given (picks[batch]: one per layer), with
+    the cost model's top-5 picks of the stack report."""
     import paper_2307_16080_gb300.forward as fwd
     out = {}
     for b in (1, 8, 32):
-        net = fwd.ResNetStack(b, dev, seed=5)
-        x = torch.empty(b, 56, 56, 64, device=dev).uniform_(0, 1).to(torch.bfloat16)
-        net.bind(x)
-        ms = graph_time(torch, net.run, calls=2, reps=10)
-        ms_flushed = flushed_time(torch, net.run, calls=4, trials=3)
-        nk.nk_sync_status()
-        # BF16 activations; the projections and the head write FP32
-        ob = [4 if net.role(li) in ("projection", "head") else 2 for li in range(20)]
-        roof_ms = stack_roofline_ms(synth, b, out_bytes=ob)
-        out[f"batch{b}"] = {"warm_ms": ms, "flushed_ms": ms_flushed,
-                            "tflops_flushed": net.flop / (ms_flushed * 1e-3) / 1e12,
-                            "roofline_ms": roof_ms, "frac_of_roofline_flushed": roof_ms / ms_flushed,
-                            "kernels_per_forward": net.kernels}
+        rec = {}
+        runs = [("default", None)]
+        if picks and picks.get(b):
+            runs.append(("model", [tuple(pk) for pk in picks[b]]))
+        for name, scheds in runs:
+            net = fwd.ResNetStack(b, dev, seed=5, schedules=scheds)
+            x = torch.empty(b, 56, 56, 64, device=dev).uniform_(0, 1).to(torch.bfloat16)
+            net.bind(x)
+            ms = graph_time(torch, net.run, calls=2, reps=10)
+            ms_flushed = flushed_time(torch, net.run, calls=4, trials=3)
+            nk.nk_sync_status()
+            # BF16 activations; the projections and the head write FP32
+            ob = [4 if net.role(li) in ("projection", "head") else 2 for li in range(20)]
+            roof_ms = stack_roofline_ms(synth, b, out_bytes=ob)
+            r = {"warm_ms": ms, "flushed_ms": ms_flushed, "tflops_flushed": net.flop / (ms_flushed * 1e-3) / 1e12,
+                 "roofline_ms": roof_ms, "frac_of_roofline_flushed": roof_ms / ms_flushed,
+                 "kernels_per_forward": net.kernels}
+            if name == "default":
+                rec.update(r)
+            else:
+                rec["model_schedules"] = r
+        out[f"batch{b}"] = rec
     return out
 
 
@@ -837,11 +850,13 @@ def _case_emit(name, ms, bytes_=None, flop=None, **kw):
     print(json.dumps(out), flush=True)
 
 
-def run_case(name, reps, schedule=None):
+def run_case(name, reps, schedule=None, shape=None):
     """One kernel family alone, on a fixed workload (device times of CUDA
     graph replays; the inputs of each are larger than L2, or the timing is
     the flushed one).  schedule: a fixed tile for the grouped case instead
-    of its tuner (so a profiler sees the measured kernel first)."""
+    of its tuner (so a profiler sees the measured kernel first), or for the
+    conv cases instead of the built-in choice; shape: N,H,C,F of the conv
+    cases (3x3, stride 1, pad 1, H x H images)."""
     import torch
 
     import paper_2307_16080_gb300.nk as nk
@@ -873,19 +888,23 @@ def run_case(name, reps, schedule=None):
             _case_emit(f"direct nchw conv ({batch},1,1280,1280) Co=3 3x3", ms, bytes_=b, flop=f,
                        timing="flushed" if batch == 1 else "inputs larger than L2")
     elif name in ("conv", "conv_window", "conv_tap", "conv8"):
-        N = 8 if name == "conv8" else 32
-        sched = {"conv": None, "conv8": None, "conv_window": (128, 64, 576, 1, 1, 1),
+        N, H, C, F = 8 if name == "conv8" else 32, 56, 64, 64
+        if shape is not None:
+            N, H, C, F = shape
+        sched = {"conv": None, "conv8": None, "conv_window": (128, 64, 64 * 9, 1, 1, 1),
                  "conv_tap": (128, 64, 64, 1, 3, 1)}[name]
-        i = torch.randn(N, 56, 56, 64, device="cuda").abs().to(torch.bfloat16)
-        w = nk.nk_conv2d_pack_weights(torch.randn(3, 3, 64, 64, device="cuda") * 0.06)
-        o = torch.empty(N, 56, 56, 64, device="cuda")
+        sched = schedule if schedule is not None else sched
+        i = torch.randn(N, H, H, C, device="cuda").abs().to(torch.bfloat16)
+        w = nk.nk_conv2d_pack_weights(torch.randn(3, 3, C, F, device="cuda") * (2.0 / (9 * C)) ** 0.5)
+        o = torch.empty(N, H, H, F, device="cuda")
         ws = nk.workspace(nk.nk_conv2d_workspace_size(i, w, o, pad=(1, 1, 1, 1), precision="bf16", schedule=sched))
         call = lambda: nk.nk_conv2d_nhwc_hwcf(i, w, o, pad=(1, 1, 1, 1), precision="bf16",  # noqa: E731
                                               schedule=sched, ws=ws)
-        f = 2.0 * N * 56 * 56 * 64 * 9 * 64
-        b = N * 56 * 56 * (64 * 2 + 64 * 4) + 9 * 64 * 64 * 2
-        _case_emit(f"bf16 conv {N}x56x56x64 3x3 ({name})", flushed_time(torch, call), bytes_=b, flop=f,
-                   timing="flushed", warm_ms=graph_time(torch, call, 10, reps))
+        f = 2.0 * N * H * H * F * 9 * C
+        b = N * H * H * (C * 2 + F * 4) + 9 * C * F * 2
+        _case_emit(f"bf16 conv {N}x{H}x{H}x{C} -> {F} 3x3 ({name})", flushed_time(torch, call), bytes_=b, flop=f,
+                   timing="flushed", warm_ms=graph_time(torch, call, 10, reps),
+                   schedule=list(sched) if sched is not None else None)
     elif name == "stack8":
         calls, flop = [], 0.0
         for L in synth.resnet_stack(8):
@@ -981,7 +1000,8 @@ def main():
     ap.add_argument("--case", choices=CASES, help="time one kernel family alone and exit")
     ap.add_argument("--reps", type=int, default=20, help="replays per --case timing")
     ap.add_argument("--schedule", default=None,
-                    help="--case grouped: fixed tile_m,tile_n,tile_k,cluster,stages,split_k instead of tuning")
+                    help="--case grouped / conv*: fixed tile_m,tile_n,tile_k,cluster,stages,split_k")
+    ap.add_argument("--shape", default=None, help="--case conv*: N,H,C,F of a 3x3 stride-1 layer")
     ap.add_argument("--cpu-legs", type=float, default=None, help=argparse.SUPPRESS)
     ap.add_argument("--no-sweep", action="store_true", help="skip the FP8/BF16x3/FP32 sweep")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
@@ -1002,7 +1022,8 @@ def main():
         return
     if args.case:
         run_case(args.case, args.reps,
-                 tuple(int(v) for v in args.schedule.split(",")) if args.schedule else None)
+                 tuple(int(v) for v in args.schedule.split(",")) if args.schedule else None,
+                 tuple(int(v) for v in args.shape.split(",")) if args.shape else None)
         return
 
     import torch
@@ -1105,7 +1126,8 @@ def main():
         rr = resnet_report(torch, synth, dev)
         if rr is not None:
             extra["resnet_stack_bf16"] = rr
-        extra["resnet_chained_forward_bf16"] = chained_forward_report(torch, nk, synth, dev)
+        picks = {b: rr[f"batch{b}"]["model_picks"] for b in (1, 8, 32)} if rr is not None else None
+        extra["resnet_chained_forward_bf16"] = chained_forward_report(torch, nk, synth, dev, picks)
         extra["grouped_conv_resnet_layers"] = grouped_conv_report(torch, nk, synth, dev)
         extra["fp8_peak_measured"] = fp8pk
 

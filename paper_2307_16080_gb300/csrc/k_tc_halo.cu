@@ -360,6 +360,8 @@ __global__ void __launch_bounds__(DB ? kThreadsDB : kThreads, 1) halo_conv_kerne
 #pragma unroll
             for (int e = 0; e < 32; ++e) v[e] = __uint_as_float(r0[e]);
 #pragma unroll
+            // (double-buffered tiles never use whole-width pitches: every
+            // shift stays inside its window row)
             for (int j = 1; j < 4; ++j) {
               if (j >= nst) break;
               const int sh = j * t.dw;
@@ -369,13 +371,19 @@ __global__ void __launch_bounds__(DB ? kThreadsDB : kThreads, 1) halo_conv_kerne
           } else {
           ptx::tmem_ld32(lane_base + (uint32_t)(ch * p.bn + c0), v);
           if (STK) {
-            // output row m = tap-0 row m + tap-kw row m + kw * dw, same warp
+            // output row m = tap-0 row m + tap-kw row m + kw * dw, same warp;
+            // a shift past the window row (whole-width tiles only) reads
+            // right padding and adds nothing
             for (int j = 1; j < nst; ++j) {
               float w[32];
               ptx::tmem_ld32(lane_base + (uint32_t)(j * p.bn + c0), w);
               const int sh = j * t.dw;
+              const bool in_row = x + sh < t.P;
 #pragma unroll
-              for (int e = 0; e < 32; ++e) v[e] += __shfl_down_sync(0xffffffffu, w[e], sh);
+              for (int e = 0; e < 32; ++e) {
+                const float s = __shfl_down_sync(0xffffffffu, w[e], sh);
+                if (in_row) v[e] += s;
+              }
             }
           }
           }
@@ -586,13 +594,23 @@ int halo_tmem_cols(int mch, int bn, int stk, bool db) {
 // Stacked (stk > 1): the window row pitch P is 8, 16 or 32, so window rows
 // are aligned to warps, and every row a valid output reads through the kw
 // shifts (its whole window row) lies inside the first 128 GEMM rows.
-bool choose_halo_tile(const ConvGeom& g, int mch, int max_slot_rows, bool stk, HaloTile* out) {
+//
+// Stacked, one column tile: Q may be the whole output width OW <= P instead
+// of P - (KW-1)*dw when P - pad_left >= W.  A tap whose shift would leave the
+// window row (x + kw*dw >= P) then reads an input column >= W, which is zero
+// padding, so the epilogue leaves it out and the sum is exact.  A 7-wide
+// image fits a pitch of 8 this way (two images per tile instead of one).
+// Only the single-buffered kernel masks those shifts (wrap_ok): in the
+// double-buffered one the mask made the epilogue spill registers.
+bool choose_halo_tile(const ConvGeom& g, int mch, int max_slot_rows, bool stk, bool wrap_ok, HaloTile* out) {
   const int maxrows = mch * 128;
   const int halo_w = (g.kw - 1) * g.dw, halo_h = (g.kh - 1) * g.dh;
   bool found = false;
   int64_t best_tiles = INT64_MAX;
   int best_slot = INT_MAX;
   HaloTile best{};
+  // (Q, P) candidates: P = Q + halo_w, then (stacked) the whole-width tiles
+  std::vector<std::pair<int, int>> qp;
   for (int Q = 1; (stk || Q <= g.ow) && Q + halo_w <= 256; ++Q) {
     const int P = Q + halo_w;
     if (Q > maxrows) break;
@@ -600,6 +618,14 @@ bool choose_halo_tile(const ConvGeom& g, int mch, int max_slot_rows, bool stk, H
       if (P > 32) break;
       continue;
     }
+    qp.push_back({Q, P});
+  }
+  if (stk && wrap_ok)
+    for (int P : {8, 16, 32})
+      if (g.ow <= P && g.ow > P - halo_w && P - g.pl >= g.w) qp.push_back({g.ow, P});
+  for (const auto& c : qp) {
+    const int Q = c.first, P = c.second;
+    const bool wrap = Q + halo_w > P;   // whole-width tile: chosen only for fewer tiles
     for (int R = 1; R <= g.oh && R + halo_h <= 256; ++R) {
       const int WR = R + halo_h;
       const int last = stk ? R * P : (R - 1) * P + Q;   // rows one image's outputs (and their reads) span
@@ -610,7 +636,7 @@ bool choose_halo_tile(const ConvGeom& g, int mch, int max_slot_rows, bool stk, H
       const int slot = (std::max(rows, maxrows + max_offset(g, P, stk)) + 7) / 8 * 8;
       if (slot > max_slot_rows) continue;
       const int64_t tiles = (int64_t)((g.n + NB - 1) / NB) * ((g.oh + R - 1) / R) * ((g.ow + Q - 1) / Q);
-      if (tiles < best_tiles || (tiles == best_tiles && slot < best_slot)) {
+      if (tiles < best_tiles || (!wrap && tiles == best_tiles && slot < best_slot)) {
         best_tiles = tiles;
         best_slot = slot;
         best.Q = Q; best.R = R; best.NB = NB; best.P = P; best.WR = WR;
@@ -637,28 +663,31 @@ struct TileKey {
   ConvGeom g;
   int mch;
   int stk;
+  int wrap_ok;
 };
 std::mutex g_tile_mu;
 std::vector<std::pair<TileKey, std::pair<bool, HaloTile>>> g_tile_cache;
 
-bool cached_halo_tile(const ConvGeom& g, int mch, bool stk, HaloTile* out) {
+bool cached_halo_tile(const ConvGeom& g, int mch, bool stk, bool wrap_ok, HaloTile* out) {
   // The window slot may use at most what is left beside two weight tiles of
   // 256 rows and the barriers; the real budget is checked per schedule.
   const int max_slot_rows = (kMaxSmem - 1024 - kBarBytes) / kRow;
   std::lock_guard<std::mutex> lk(g_tile_mu);
   for (auto& e : g_tile_cache)
-    if (e.first.mch == mch && e.first.stk == (int)stk && std::memcmp(&e.first.g, &g, sizeof g) == 0) {
+    if (e.first.mch == mch && e.first.stk == (int)stk && e.first.wrap_ok == (int)wrap_ok &&
+        std::memcmp(&e.first.g, &g, sizeof g) == 0) {
       *out = e.second.second;
       return e.second.first;
     }
   HaloTile t{};
-  const bool ok = choose_halo_tile(g, mch, max_slot_rows, stk, &t);
+  const bool ok = choose_halo_tile(g, mch, max_slot_rows, stk, wrap_ok, &t);
   if (g_tile_cache.size() > 4096) g_tile_cache.clear();
   TileKey k;
   std::memset(&k, 0, sizeof k);
   k.g = g;
   k.mch = mch;
   k.stk = (int)stk;
+  k.wrap_ok = (int)wrap_ok;
   g_tile_cache.push_back({k, {ok, t}});
   *out = t;
   return ok;
@@ -683,10 +712,10 @@ int halo_ctas(int smem, int tmem_cols) {
 // otherwise they stream through a ring of up to 8 tiles (at least two).  Of
 // the two, the layout that lets more CTAs (independent MMA chains) share an
 // SM wins; on a tie, resident weights.
-bool halo_layout(const ConvGeom& g, int F, const nk_schedule& s, HaloLayout* L, int kind = TC_BF16) {
+bool halo_layout(const ConvGeom& g, int F, const nk_schedule& s, HaloLayout* L, int kind = TC_BF16, int sms = 0) {
   const int mch = chains_of(g, s, kind);
   const bool stk = stacked_schedule(g, s, kind);
-  if (!cached_halo_tile(g, mch, stk, &L->t)) return false;
+  if (!cached_halo_tile(g, mch, stk, stk && !stacked_db(g, s, kind), &L->t)) return false;
   L->t.cblk = cblk_of(kind);
   L->t.cblocks = (g.c + L->t.cblk - 1) / L->t.cblk;
   const int tcols = halo_tmem_cols(mch, s.tile_n, L->t.stk, stacked_db(g, s, kind));
@@ -697,9 +726,13 @@ bool halo_layout(const ConvGeom& g, int F, const nk_schedule& s, HaloLayout* L, 
   const int nkb = (stk ? g.kh : taps_of(g)) * L->t.cblocks;
   const int room = (kMaxSmem - fixed) / b_tile;
   if (room < 2) return false;
-  // streamed ring: deepest ring that keeps the CTA count of a 2-slot ring
+  // streamed ring: deepest ring that keeps the CTA count of a 2-slot ring,
+  // or (sms known, every unit in one wave of one CTA per SM) simply the
+  // deepest: a lone CTA's MMA chain waits on its filter loads otherwise
   int ring = std::min(std::min(room, nkb < 2 ? 2 : nkb), 8);
-  const int want = halo_ctas(fixed + 2 * b_tile, tcols);
+  int want = halo_ctas(fixed + 2 * b_tile, tcols);
+  if (sms > 0 && (int64_t)L->t.tiles_b * L->t.tiles_h * L->t.tiles_w * ((F + s.tile_n - 1) / s.tile_n) <= sms)
+    want = 1;
   while (ring > 2 && halo_ctas(fixed + ring * b_tile, tcols) < want) --ring;
   L->resident = 0;
   L->bslots = ring;
@@ -812,7 +845,7 @@ nk_status tc_halo_conv(const TcConv& c, const nk_schedule& s, cudaStream_t st) {
   const bool f8 = kind == TC_FP8;
   const int esz = f8 ? 1 : 2;
   HaloLayout L;
-  if (!halo_schedule_valid(g, c.F, s, kind) || !halo_layout(g, c.F, s, &L, kind))
+  if (!halo_schedule_valid(g, c.F, s, kind) || !halo_layout(g, c.F, s, &L, kind, sms))
     return fail(NK_ERR_NO_SCHEDULE, "illegal window-conv schedule");
   if ((c.sI_w * esz) % 16 || (c.sI_h * esz) % 16 || (c.sI_n * esz) % 16 || (c.ldw * esz) % 16 ||
       (c.sW_f * esz) % 16 || (reinterpret_cast<uintptr_t>(c.I) & 15) || (reinterpret_cast<uintptr_t>(c.Wt) & 15))

@@ -53,6 +53,12 @@ STACK_CASES = [
     (2, 17, 19, 64, 48, 2, 2, (1, 1), (0, 1, 0, 1)),
     (2, 21, 23, 64, 64, 3, 3, (2, 2), (2, 2, 2, 2)),     # P = 32
     (2, 15, 17, 96, 160, 3, 3, (1, 1), (1, 1, 1, 1)),
+    # whole-width tiles (one column tile, shifts past the window row read
+    # right padding and are left out): 7 and 15 wide, asymmetric pads, dilation
+    (4, 7, 7, 64, 64, 3, 3, (1, 1), (1, 1, 1, 1)),
+    (3, 7, 7, 96, 130, 3, 3, (1, 1), (1, 1, 0, 2)),
+    (2, 15, 15, 64, 48, 3, 3, (1, 1), (1, 1, 1, 1)),
+    (2, 13, 13, 64, 64, 3, 3, (2, 2), (2, 2, 2, 2)),
 ]
 
 

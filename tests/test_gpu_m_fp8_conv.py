@@ -44,6 +44,7 @@ CASES = [
     (2, 10, 12, 256, 96, 3, 3, (1, 1), (1, 1, 1, 1)),    # two N tiles, weights streamed
     (1, 17, 19, 136, 48, 4, 4, (1, 1), (1, 2, 1, 2)),    # KW = 4: N = 256
     (3, 9, 11, 128, 40, 3, 2, (2, 1), (2, 2, 1, 1)),     # KW = 2, row dilation
+    (5, 7, 7, 256, 72, 3, 3, (1, 1), (1, 1, 1, 1)),      # whole-width tiles: 7 wide at pitch 8
 ]
 
 
