@@ -662,8 +662,7 @@ def resnet_report(torch, synth, dev):
         tot["schedules_timed"] = timed
         tot["tuner_timing"] = nt.timing_method()
         tot["stack_graph"] = stack_graph(torch, synth, dev, b, picks, tot["flop"])
-        tot["model_picks"] = [[int(getattr(pk, f)) for f in ("tile_m", "tile_n", "tile_k", "cluster", "stages",
-                                                             "split_k")] for pk in picks]
+        tot["model_picks"] = [[int(v) for v in pk] for pk in picks]   # schedule tuples, one per layer
         out[f"batch{b}"] = tot
     nt.nk_tune_release()
     return out
