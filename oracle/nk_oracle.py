@@ -56,7 +56,9 @@ E4M3_MAX = 448.0              # 1.110b * 2^8 (S.1111.111 is NaN, no infinities)
 def _round_to_precision(x: np.ndarray, frac_bits: int, emin: int) -> np.ndarray:
     """Round finite x (FP64) to a binary format with ``frac_bits`` fraction
     bits and minimum normal exponent ``emin``; round-to-nearest, ties to even
-    (np.rint rounds halves to even).  No overflow handling."""
+    (np.rint rounds halves to even).  Zeros keep their sign; a nonzero value
+    that rounds to zero keeps it too (np.rint(-0.3) is -0.0).  No overflow
+    handling."""
     x = np.asarray(x, dtype=np.float64)
     out = np.zeros_like(x)
     nz = (x != 0) & np.isfinite(x)
@@ -70,6 +72,7 @@ def _round_to_precision(x: np.ndarray, frac_bits: int, emin: int) -> np.ndarray:
     q = np.rint(np.ldexp(x[nz], -quantum_exp))
     out[nz] = np.ldexp(q, quantum_exp)
     out[~np.isfinite(x)] = x[~np.isfinite(x)]
+    out[x == 0] = x[x == 0]                       # a zero keeps its sign (IEEE conversion)
     return out
 
 

@@ -96,6 +96,25 @@ def test_e4m3_matches_torch_cpu_conversion_in_range():
     np.testing.assert_array_equal(O.e4m3_rn_sat(big), [448, 448, 448, -448, 448, -448])
 
 
+def test_conversions_keep_the_sign_of_zero():
+    """IEEE round-to-nearest keeps the sign of a zero, and of a value that
+    rounds to zero; assert_array_equal cannot see it, so compare sign bits
+    against torch's conversions."""
+    x = np.array([-0.0, 0.0, -1e-30, 1e-30, -1e-45, 1e-45, 2.0 ** -10, -2.0 ** -10, -2.0 ** -11, -3e-3, 3e-3],
+                 np.float32)
+    x = np.concatenate([x, _fp32_bit_patterns(20_000)])
+    b = O.bf16_rn(x)
+    tb = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(b, tb)
+    np.testing.assert_array_equal(np.signbit(b), np.signbit(tb))
+    xe = x[np.abs(x) < 464.0]
+    e = O.e4m3_rn_sat(xe)
+    te = torch.from_numpy(xe).to(torch.float8_e4m3fn).to(torch.float64).numpy()
+    np.testing.assert_array_equal(e, te)
+    np.testing.assert_array_equal(np.signbit(e), np.signbit(te))
+    assert np.signbit(O.fp8_quantize(np.array([-0.0], np.float32), np.float32(2.0))[0])
+
+
 def test_bf16x3_split_properties():
     x = synth.outlier_normal(5, 0, (100_000,)).astype(np.float64)
     hi, lo = O.bf16x3_split(x)
