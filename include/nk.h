@@ -229,8 +229,9 @@ typedef struct {
 } nk_gemm_group;
 
 /* Opaque plan: group table, per-group TMA descriptors (A, B^T and, when
- * every group overwrites a 16-byte aligned C with 16-byte aligned rows, C
- * for TMA stores), tile table and the group of every tile (4 bytes per
+ * every group overwrites a 16-byte aligned C whose row stride and row
+ * length N are multiples of 4 floats, C for TMA stores), tile table and the
+ * group of every tile (4 bytes per
  * tile) in device memory, built once on the host side and replayed by one
  * persistent launch.  Creating a plan allocates; running it does not
  * (graph-safe).                                                           */

@@ -254,8 +254,9 @@ __device__ __forceinline__ int conv_row(const ConvTile& c, int tm, int r) {
 // Each warp has its own staging box for the TMA-store epilogue (eight).
 //
 // Grouped launches store through TMA too (c_tma with a C map per group,
-// when every group overwrites a 16-byte aligned C): the store clips each
-// group's ragged edges, and one instruction writes a 32 x 32 block where
+// when every group overwrites a 16-byte aligned C whose rows end on 16-byte
+// boundaries): the store clips each group's ragged rows and columns past the
+// last 16-byte granule, and one instruction writes a 32 x 32 block where
 // per-lane stores touch 32 rows.  On 512 uneven groups (128 x 256 tiles,
 // 4 stages) 0.244 -> 0.234 ms.
 template <int KIND, int CL, bool GROUPED, bool CONV = false, bool PAIR = false, bool WIDE = false, int MCH = 1,
@@ -917,9 +918,12 @@ nk_status tc_gemm(const TcGemm& g, const nk_schedule& s, void* ws, size_t ws_byt
   p.c_vec = cvec ? 1 : 0;
   p.c_vec32 = (splits == 1 && (reinterpret_cast<uintptr_t>(g.C) & 31) == 0 && g.ldc % 8 == 0) ? 1 : 0;
   // TMA-store epilogue: plain overwrite of a 16-byte aligned C in one K slice.
+  // Rows must also end on a 16-byte boundary (N % 4 == 0): a TMA store clips
+  // the innermost dimension only to 16-byte granules, so with N % 4 != 0 and
+  // a padded row stride it wrote the row's padding (caught by canaries).
   p.c_tma = 0;
   if (mch == 1 && splits == 1 && g.beta == 0.f && g.ew.n == 0 && (reinterpret_cast<uintptr_t>(g.C) & 15) == 0 &&
-      (g.ldc * 4) % 16 == 0) {
+      (g.ldc * 4) % 16 == 0 && g.N % 4 == 0) {
     auto fn = encode_fn();
     cuuint64_t dims[2] = {(cuuint64_t)g.N, (cuuint64_t)g.M};
     cuuint64_t strides[1] = {(cuuint64_t)(g.ldc * 4)};
@@ -1339,7 +1343,10 @@ nk_status build_grouped(int G, const nk_gemm_group* groups, int precision, const
     cvec = cvec && ((reinterpret_cast<uintptr_t>(q.C) & 15) == 0) && (q.ldc % 4 == 0);
     cvec32 = cvec32 && ((reinterpret_cast<uintptr_t>(q.C) & 31) == 0) && (q.ldc % 8 == 0);
     // TMA-store epilogue: every group a plain overwrite of a 16-byte aligned C
-    ctma = ctma && fn && !q.accumulate && ((reinterpret_cast<uintptr_t>(q.C) & 15) == 0) && (q.ldc * 4) % 16 == 0;
+    // whose rows end on 16-byte boundaries (a TMA store clips the innermost
+    // dimension to 16-byte granules only)
+    ctma = ctma && fn && !q.accumulate && ((reinterpret_cast<uintptr_t>(q.C) & 15) == 0) && (q.ldc * 4) % 16 == 0 &&
+           q.N % 4 == 0;
     if (ctma) {
       cuuint64_t dims[2] = {(cuuint64_t)q.N, (cuuint64_t)q.M};
       cuuint64_t strides[1] = {(cuuint64_t)(q.ldc * 4)};

@@ -27,14 +27,18 @@ MM = [("f32", None), ("f32", (64, 64, 16, 1, 2, 3)), ("bf16", None), ("bf16", (1
 
 
 @pytest.mark.parametrize("prec,sched", MM)
-def test_matmul_writes_only_its_output(nk, prec, sched):
-    M, N, K = 300, 260, 200
+@pytest.mark.parametrize("N,ldc", [(260, 273), (259, 260), (257, 264), (256, 264)])
+def test_matmul_writes_only_its_output(nk, prec, sched, N, ldc):
+    """Padded rows (the gaps are canaries); ldc a multiple of 4 floats with
+    N % 4 != 0 must not take the TMA-store epilogue, whose clipping works in
+    16-byte granules."""
+    M, K = 300, 200
     A = synth.small_ints(140, 1, (M, K))
     B = synth.small_ints(140, 2, (K, N))
     if prec == "fp8":   # half-integers up to 3.5 with amax 3.5: exact E4M3 codes
         A, B = A / 2, B / 2
         A.flat[0], B.flat[0] = 3.5, 3.5
-    c = Canary((M, N), strides=(N + 13, 1))   # padded rows: gaps between them are canaries too
+    c = Canary((M, N), strides=(ldc, 1))   # padded rows: gaps between them are canaries too
     nk.nk_matmul(dev(A), dev(B), c.t, precision=prec, schedule=sched, bias=dev(np.ones(N, np.float32)))
     nk.nk_sync_status()
     c.check()
