@@ -7,6 +7,8 @@ independent pads, so the dispatcher lands on every kernel family: per-tap
 Entries are small integers (FP32, BF16; BF16 outputs compared after the
 oracle's own rounding) or half-integers with amax 3.5 (E4M3 quantised per
 call: scale 128, exact codes), so every result is exact whatever the order.
+Outputs sit inside canary-filled buffers, so a write past either end of the
+tensor (a ragged last tile) fails too.
 """
 import numpy as np
 import pytest
@@ -14,7 +16,7 @@ import torch
 
 import oracle.nk_oracle as O
 from paper_2307_16080_gb300 import synth
-from tests.gpu_util import DEV
+from tests.gpu_util import DEV, Canary
 
 pytestmark = pytest.mark.gpu
 
@@ -71,7 +73,8 @@ def test_random_convolutions_bitwise(nk, prec, odt):
         R = O.conv2d_nhwc_hwcf(I, W, st, dl, pad)
         if odt == torch.bfloat16:
             R = O.bf16_rn(R)
-        out = torch.full(shape, float("nan"), device=DEV, dtype=odt)
+        can = Canary(shape, odt)   # contiguous NHWC inside sentinels: catches writes past either end
+        out = can.t
         try:
             nk.nk_conv2d_nhwc_hwcf(torch.from_numpy(I).to(DEV), torch.from_numpy(W).to(DEV), out, stride=st,
                                    dilation=dl, pad=pad, precision=prec)
@@ -81,6 +84,7 @@ def test_random_convolutions_bitwise(nk, prec, odt):
                 continue
             raise AssertionError(f"geometry {gi} {GEOMS[gi]}: {e}")
         ran += 1
+        can.check()
         if not np.array_equal(out.float().cpu().numpy(), R):
             bad.append(gi)
     assert not bad, f"{len(bad)} geometries differ, first {[GEOMS[i] for i in bad[:3]]}"
