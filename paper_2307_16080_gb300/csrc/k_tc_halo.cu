@@ -35,13 +35,27 @@
 // one warp and a valid output never reads across a warp.  That makes KH MMAs
 // per 16 channels instead of KH*KW narrow ones.
 //
-//   warp 0      TMA producer: window slots (one per 64-channel block) and
-//               weight tiles (one per tap and channel block).
+// When one column tile spans the output width and P >= W + pad_left, a
+// stacked tile may hold Q = OW columns: a shift past the window row then
+// stands for right padding and the epilogue leaves it out (whole-width
+// tiles; a 7-wide image fits a pitch of 8).
+//
+// Variants (template parameters): DB, two accumulators and eight epilogue
+// warps on one CTA per SM, so a tile's epilogue overlaps the next tile;
+// F8, E4M3 operands in 128-channel blocks (kind::f8f6f4, K = 32 per MMA);
+// RES, the residual ADD + ReLU inline in the store path.  Outputs are FP32
+// or BF16 (rounded once after the whole epilogue).
+//
+//   warp 0      TMA producer: window slots (one per channel block: 64 BF16
+//               or 128 E4M3 channels) and weight tiles (one per tap, or per
+//               kernel row when stacked, and channel block).
 //   warp 1      TMEM allocation; one thread issues tcgen05.mma, M = 128,
-//               N = BN, K = 16, MCH chains x 4 K steps per tap.
-//   warps 2..5  epilogue: tcgen05.ld, bias, beta*O, ReLU, FP32 stores of the
-//               valid rows, overlapped with the next tile through the second
-//               accumulator buffer.
+//               N = BN (stacked: 64*KW), K = 16 (E4M3: 32), MCH chains x 4 K
+//               steps per tap.
+//   warps 2..   epilogue (4 warps, 8 for DB): tcgen05.ld, the tap shuffles
+//               when stacked, bias, beta*O, ReLU, the residual, FP32 or BF16
+//               stores of the valid rows; with two accumulator buffers
+//               overlapped with the next tile's MMAs.
 //
 // Every wait is bounded (tc_ptx.cuh); on expiry the CTA drains its copies and
 // MMAs, frees TMEM and exits, and the host reports NK_ERR_TIMEOUT.
